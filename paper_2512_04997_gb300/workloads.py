@@ -1,0 +1,293 @@
+"""Seeded synthetic workloads shaped like the paper's runs.
+
+This module only draws inputs: particle placements, orientations, random initial fields
+and the parameter sets of the standard workloads. It contains none of the method's
+arithmetic (no equilibrium, collision, solid fraction or contact law), so the CUDA path
+and the FP64 oracle can both be fed from it without sharing any computation.
+
+Conventions: lattice nodes sit at integer coordinates 0..n-1, walls lie halfway at -1/2
+and n-1/2. Particle arrays are per particle with xyz contiguous; the orientation triad is
+``(n, 9)`` = d1, d2, d3 (unit body axes in world components).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 12345
+
+
+def rng(index: int) -> np.random.Generator:
+    """PCG64 generator for workload ``index`` (seed 12345 + index)."""
+    return np.random.Generator(np.random.PCG64(SEED_BASE + int(index)))
+
+
+def random_quaternions(g: np.random.Generator, n: int) -> np.ndarray:
+    """Uniformly random unit quaternions (w, x, y, z), Shoemake's method."""
+    u1, u2, u3 = g.random(n), g.random(n), g.random(n)
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    q = np.stack([a * np.sin(2 * np.pi * u2), a * np.cos(2 * np.pi * u2),
+                  b * np.sin(2 * np.pi * u3), b * np.cos(2 * np.pi * u3)], axis=1)
+    return q[:, [3, 0, 1, 2]]
+
+
+def quaternion_to_triad(q: np.ndarray) -> np.ndarray:
+    """Rows d1, d2, d3 of the rotation that maps world components to body components.
+
+    The body axis d_m, expressed in world coordinates, is column m of the usual
+    body-to-world rotation matrix of the quaternion.
+    """
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    M = np.empty((len(q), 3, 3))
+    M[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    M[:, 0, 1] = 2 * (x * y - w * z)
+    M[:, 0, 2] = 2 * (x * z + w * y)
+    M[:, 1, 0] = 2 * (x * y + w * z)
+    M[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    M[:, 1, 2] = 2 * (y * z - w * x)
+    M[:, 2, 0] = 2 * (x * z - w * y)
+    M[:, 2, 1] = 2 * (y * z + w * x)
+    M[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return np.ascontiguousarray(np.transpose(M, (0, 2, 1)).reshape(len(q), 9))
+
+
+def identity_triads(n: int) -> np.ndarray:
+    return np.tile(np.eye(3).reshape(1, 9), (n, 1))
+
+
+def rsa_spheres(g: np.random.Generator, n: int, radii: np.ndarray, lo, hi, periodic,
+                gap: float = 0.0, max_tries: int = 200000) -> np.ndarray:
+    """Random sequential addition of non-overlapping spheres.
+
+    Centres are drawn uniformly in [lo + R, hi - R] on wall axes and in [lo, hi) on
+    periodic axes; a draw is kept if it is at least R_i + R_j + gap from every kept
+    sphere (minimum image on periodic axes). Raises if ``max_tries`` is exhausted.
+    """
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    L = hi - lo
+    rmax = float(np.max(radii)) if n else 1.0
+    h = 2 * rmax + gap
+    gn = np.maximum(1, np.floor(L / h)).astype(int)
+    gh = L / gn
+    cells: dict = {}
+    pos = np.zeros((n, 3))
+    tries = 0
+    for k in range(n):
+        R = radii[k]
+        while True:
+            tries += 1
+            if tries > max_tries:
+                raise RuntimeError(f"RSA jammed after placing {k} of {n} spheres")
+            p = np.empty(3)
+            for a in range(3):
+                if periodic[a]:
+                    p[a] = lo[a] + g.random() * L[a]
+                else:
+                    p[a] = lo[a] + R + g.random() * (L[a] - 2 * R)
+            c = np.minimum(np.floor((p - lo) / gh).astype(int), gn - 1)
+            ok = True
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        q = c + np.array([dx, dy, dz])
+                        skip = False
+                        for a in range(3):
+                            if q[a] < 0 or q[a] >= gn[a]:
+                                if periodic[a]:
+                                    q[a] %= gn[a]
+                                else:
+                                    skip = True
+                        if skip:
+                            continue
+                        for j in cells.get(tuple(q), ()):
+                            d = p - pos[j]
+                            for a in range(3):
+                                if periodic[a]:
+                                    d[a] -= L[a] * np.round(d[a] / L[a])
+                            if d @ d < (R + radii[j] + gap) ** 2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                pos[k] = p
+                cells.setdefault(tuple(c), []).append(k)
+                break
+    return pos
+
+
+@dataclass
+class Workload:
+    """A lattice/particle problem with its parameters (lattice units)."""
+    name: str
+    nx: int = 0
+    ny: int = 0
+    nz: int = 0
+    box_lo: tuple = (0.0, 0.0, 0.0)
+    box_hi: tuple = (1.0, 1.0, 1.0)
+    periodic: tuple = (1, 1, 1)
+    u_wall: np.ndarray = field(default_factory=lambda: np.zeros((3, 2, 3)))
+    params: dict = field(default_factory=dict)
+    shape: np.ndarray = field(default_factory=lambda: np.zeros(0, dtype=np.int32))
+    radius: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    semi: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    density: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    pos: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    vel: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    omg: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    triad: np.ndarray = field(default_factory=lambda: np.zeros((0, 9)))
+    init_u: np.ndarray | None = None      # (3, ncell) initial velocity field or None
+    steps: int = 1
+    notes: str = ""
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def n(self) -> int:
+        return len(self.shape)
+
+
+def base_params(**kw) -> dict:
+    """Default parameter set (lattice units); keys mirror the C-ABI parameter struct."""
+    p = dict(tau=0.8, fluid_force=(0.0, 0.0, 0.0), storage="f32", voxel="distance",
+             subdiv_n=10, law="linear", n_sub=1, rho_f=1.0, gravity=(0.0, 0.0, 0.0),
+             k_n=1000.0, k_t=1000.0 * 2.0 / 7.0, young=1.0e4, poisson=0.3, restitution=0.7,
+             friction=0.4, skin=0.5, dem_h=0.0, ell_max_iter=60, ell_tol=1e-6)
+    p.update(kw)
+    return p
+
+
+def settling_sphere(steps: int = 2000) -> Workload:
+    """Single sphere settling in a closed box (32x32x64, tau 0.8, R 4, density ratio 2.5,
+    gravity 1e-5 on the particle with analytic buoyancy, subdivision solid fractions)."""
+    w = Workload(name="settling_sphere_32x32x64", nx=32, ny=32, nz=64, periodic=(0, 0, 0))
+    R, rho_p = 4.0, 2.5
+    m = rho_p * 4.0 / 3.0 * math.pi * R ** 3
+    # Linear wall contact lasting at least 20 steps: k_n <= m (pi/20)^2.
+    kn = 0.6 * m * (math.pi / 20.0) ** 2
+    w.params = base_params(tau=0.8, voxel="subdiv", gravity=(0.0, 0.0, -1e-5), k_n=kn,
+                           k_t=kn * 2.0 / 7.0, skin=0.5, dem_h=2 * R + 0.5)
+    w.shape = np.zeros(1, dtype=np.int32)
+    w.radius = np.array([R])
+    w.semi = np.array([[R, R, R]])
+    w.density = np.array([rho_p])
+    w.pos = np.array([[16.0, 16.0, 48.0]])
+    w.vel = np.zeros((1, 3))
+    w.omg = np.zeros((1, 3))
+    w.triad = identity_triads(1)
+    w.steps = steps
+    return w
+
+
+def couette_suspension(nx: int = 256, ny: int = 256, nz: int = 256, n_particles: int = 4000,
+                       radius: float = 6.0, u_wall: float = 0.05, steps: int = 5000,
+                       seed_index: int = 3, storage: str = "f32") -> Workload:
+    """Particle-laden Couette flow: walls at z moving at -/+ u_wall along x, periodic x
+    and y, RSA spheres of equal density with the fluid (no gravity), distance-based solid
+    fractions, 10 DEM substeps, linear contacts lasting >= 20 substeps."""
+    g = rng(seed_index)
+    w = Workload(name=f"couette_suspension_{nx}x{ny}x{nz}_{n_particles}spheres",
+                 nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0))
+    uw = np.zeros((3, 2, 3))
+    uw[2, 0, 0] = -u_wall
+    uw[2, 1, 0] = +u_wall
+    w.u_wall = uw
+    m = 4.0 / 3.0 * math.pi * radius ** 3
+    n_sub = 10
+    kn = 0.45 * (m / 2) * (math.pi / (20.0 / n_sub)) ** 2
+    w.params = base_params(tau=0.8, voxel="distance", n_sub=n_sub, rho_f=1.0, k_n=kn,
+                           k_t=kn * 2.0 / 7.0, skin=0.5, dem_h=2 * radius + 0.5,
+                           storage=storage)
+    radii = np.full(n_particles, radius)
+    lo = (-0.5, -0.5, -0.5 + 1.0)
+    hi = (nx - 0.5, ny - 0.5, nz - 0.5 - 1.0)
+    w.pos = rsa_spheres(g, n_particles, radii, lo, hi, (1, 1, 0), gap=0.1)
+    w.shape = np.zeros(n_particles, dtype=np.int32)
+    w.radius = radii
+    w.semi = np.tile(radii[:, None], (1, 3))
+    w.density = np.ones(n_particles)
+    # Fluid and particles start on the linear wall-driven profile.
+    zc = w.pos[:, 2]
+    w.vel = np.zeros((n_particles, 3))
+    w.vel[:, 0] = -u_wall + 2 * u_wall * (zc + 0.5) / nz
+    w.omg = np.zeros((n_particles, 3))
+    w.triad = identity_triads(n_particles)
+    z = np.arange(nz, dtype=np.float64)
+    prof = -u_wall + 2 * u_wall * (z + 0.5) / nz
+    u = np.zeros((3, nz, ny, nx))
+    u[0] = prof[:, None, None]
+    w.init_u = u.reshape(3, -1)
+    w.steps = steps
+    return w
+
+
+def granular_box(n_particles: int = 100000, box=(120.0, 120.0, 240.0), seed_index: int = 2,
+                 steps: int = 10000) -> Workload:
+    """DEM-only granular box: radii U[0.8, 1.2], jittered cubic lattice of spacing 2.5
+    (sites chosen by a seeded shuffle), walls on all faces, linear law, mu 0.4,
+    restitution 0.7, cell size 2.4 plus skin, gravity along -z.
+
+    The box of the workload description (60x60x120) cannot hold 1e5 such spheres
+    (their volume exceeds the box); it is read as 120x120x240.
+    """
+    g = rng(seed_index)
+    w = Workload(name=f"granular_box_{n_particles}spheres", box_lo=(0.0, 0.0, 0.0),
+                 box_hi=tuple(box), periodic=(0, 0, 0))
+    radii = g.uniform(0.8, 1.2, n_particles)
+    sp = 2.5
+    ns = [int((box[a] - 2 * 1.2) // sp) for a in range(3)]
+    sites = np.stack(np.meshgrid(*[1.2 + sp / 2 + sp * np.arange(ns[a]) for a in range(3)],
+                                 indexing="ij"), axis=-1).reshape(-1, 3)
+    if len(sites) < n_particles:
+        raise ValueError("box too small for the requested particle count")
+    sel = g.permutation(len(sites))[:n_particles]
+    pos = sites[sel] + g.uniform(-0.04, 0.04, (n_particles, 3))
+    rho_p = 1.0
+    m_min = rho_p * 4.0 / 3.0 * math.pi * 0.8 ** 3
+    kn = 0.9 * (m_min / 2) * (math.pi / 20.0) ** 2
+    w.params = base_params(tau=0.8, rho_f=0.0, gravity=(0.0, 0.0, -2e-6), k_n=kn,
+                           k_t=kn * 2.0 / 7.0, restitution=0.7, friction=0.4, skin=0.2,
+                           dem_h=2.4 + 0.2, n_sub=1)
+    w.shape = np.zeros(n_particles, dtype=np.int32)
+    w.radius = radii
+    w.semi = np.tile(radii[:, None], (1, 3))
+    w.density = np.full(n_particles, rho_p)
+    w.pos = pos
+    w.vel = np.zeros((n_particles, 3))
+    w.omg = np.zeros((n_particles, 3))
+    w.triad = identity_triads(n_particles)
+    w.steps = steps
+    return w
+
+
+def random_fields(g: np.random.Generator, nx: int, ny: int, nz: int, amp_u: float = 0.02,
+                  amp_rho: float = 0.01, modes: int = 3):
+    """Smooth random density and velocity fields: a few random Fourier modes."""
+    x, y, z = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    rho = np.ones((nx, ny, nz))
+    u = np.zeros((3, nx, ny, nz))
+    for _ in range(modes):
+        k = g.integers(1, 3, 3)
+        ph = g.random(4) * 2 * np.pi
+        arg = 2 * np.pi * (k[0] * x / nx + k[1] * y / ny + k[2] * z / nz)
+        rho += amp_rho * g.uniform(-1, 1) * np.cos(arg + ph[0])
+        for a in range(3):
+            u[a] += amp_u * g.uniform(-1, 1) * np.cos(arg + ph[1 + a])
+    # to [component][cell] with cell = x + nx*(y + ny*z)
+    rho = np.ascontiguousarray(np.transpose(rho, (2, 1, 0)).reshape(-1))
+    u = np.ascontiguousarray(np.transpose(u, (0, 3, 2, 1)).reshape(3, -1))
+    return rho, u
+
+
+def population_noise(g: np.random.Generator, ncell: int, amp: float = 1e-3) -> np.ndarray:
+    """Uniform noise of shape (19, ncell) used to push populations off equilibrium."""
+    return g.uniform(-amp, amp, (19, ncell))

@@ -1,0 +1,175 @@
+"""Pins of the oracle's PSM coupling and solid fractions (Sec. 2.4).
+
+Each test checks a fact the method fixes independently of how the oracle codes it:
+limits of Eq. (lbePS), conservation of mass and of momentum between fluid and solid,
+exact sample counts in special geometries, solid volumes, Stokes drag, and the sign of
+the hydrodynamic torque on a rotating sphere.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_04997_gb300 import workloads as W
+
+
+def _random_cell(g, oracle):
+    rho = 1.0 + 0.02 * g.uniform(-1, 1)
+    u = 0.05 * g.uniform(-1, 1, 3)
+    return oracle.equilibrium(rho, u) + 1e-3 * g.uniform(-1, 1, 19)
+
+
+def test_psm_zero_weight_is_bgk(oracle):
+    """B = 0: the PSM operator reverts to the plain collision (Sec. 2.4)."""
+    g = W.rng(200)
+    f = _random_cell(g, oracle)
+    plain, _, _ = oracle.cell_collide(f, 0.8)
+    blended, F, M = oracle.cell_collide(f, 0.8, B=[0.0], uk=[[0.01, 0.02, 0.0]], arm=[[1, 0, 0]])
+    assert np.array_equal(plain, blended)
+    assert np.all(F == 0) and np.all(M == 0)
+
+
+def test_psm_full_solid_limit(oracle):
+    """B = 1: f*_i = f_ibar - f^eq_ibar(rho,u) + f^eq_i(rho,u_k), whatever tau is."""
+    g = W.rng(201)
+    f = _random_cell(g, oracle)
+    c, _, opp = oracle.lattice_tables()
+    rho = f.sum()
+    u = (f @ c) / rho
+    uk = np.array([0.02, -0.01, 0.03])
+    expect = f[opp] - oracle.equilibrium(rho, u)[opp] + oracle.equilibrium(rho, uk)
+    for tau in (0.6, 0.8, 1.5):
+        got, _, _ = oracle.cell_collide(f, tau, B=[1.0], uk=[uk], arm=[[0, 0, 0]])
+        assert np.allclose(got, expect, rtol=0, atol=1e-15)
+
+
+def test_psm_conserves_mass_and_momentum(oracle):
+    """Sum f* = sum f, and the momentum the fluid gains is exactly minus the force on the
+    solids of Eq. (forceSF) (action-reaction between fluid and particles)."""
+    g = W.rng(202)
+    c, _, _ = oracle.lattice_tables()
+    for _ in range(20):
+        f = _random_cell(g, oracle)
+        B = g.uniform(0, 1, 2)
+        uk = 0.05 * g.uniform(-1, 1, (2, 3))
+        arm = g.uniform(-3, 3, (2, 3))
+        fs, F, M = oracle.cell_collide(f, g.uniform(0.55, 1.5), B=B, uk=uk, arm=arm)
+        assert abs(fs.sum() - f.sum()) < 1e-15
+        dp = (fs - f) @ c
+        assert np.allclose(dp + F.sum(0), 0.0, atol=1e-16)
+        # torque is the arm times each solid's force
+        for k in range(2):
+            assert np.allclose(M[k], np.cross(arm[k], F[k]), atol=1e-16)
+
+
+def test_subdivision_plane_and_extremes(oracle):
+    """Subdivision (n = 10): a node on the surface of a huge sphere sees half of its
+    samples inside (the surface is a plane at that scale); a node deep inside sees all,
+    a node far outside none; the count is symmetric under rel -> -rel."""
+    R = 1.0e4
+    assert oracle.subdiv_count([-R, 0.0, 0.0], 0, R) == 500
+    assert oracle.subdiv_count([0.0, R, 0.0], 0, R) == 500
+    assert oracle.subdiv_count([0.3, 0.2, -0.1], 0, 4.0) == 1000
+    assert oracle.subdiv_count([7.0, 0.0, 0.0], 0, 4.0) == 0
+    g = W.rng(203)
+    for _ in range(50):
+        rel = g.uniform(-5, 5, 3)
+        assert oracle.subdiv_count(rel, 0, 4.0) == oracle.subdiv_count(-rel, 0, 4.0)
+
+
+def test_distance_method_values(oracle):
+    """Eq. (naiveSolidFrac): beta = 1/2 at a node on the surface, 1 at depth >= R_c,
+    0 beyond R_c outside, linear in between."""
+    Rc = (3.0 / (4.0 * math.pi)) ** (1.0 / 3.0)
+    R = 5.0
+    assert oracle.beta_distance([R, 0, 0], R) == pytest.approx(0.5, abs=1e-15)
+    assert oracle.beta_distance([R - Rc - 1e-9, 0, 0], R) == 1.0
+    assert oracle.beta_distance([R + Rc + 1e-9, 0, 0], R) == 0.0
+    assert oracle.beta_distance([0, R - Rc / 2, 0], R) == pytest.approx(0.75, abs=1e-14)
+
+
+@pytest.mark.parametrize("method,R,tol", [(1, 4.0, 2e-3), (1, 6.0, 1e-3), (0, 4.0, 3e-2),
+                                          (0, 6.0, 1.5e-2)])
+def test_sphere_volume(oracle, method, R, tol):
+    """Summed solid fractions approach the sphere volume 4/3 pi R^3."""
+    n = int(2 * R + 6)
+    s = oracle.Sim(n, n, n, periodic=(1, 1, 1), params=oracle.default_params(voxel=method))
+    c = n / 2 - 0.5
+    s.set_particles([0], [R], [[R, R, R]], [1.0], [[c + 0.23, c - 0.11, c + 0.07]])
+    beta, ids, ns = s.voxelize()
+    assert abs(beta[:, 0].sum() / (4.0 / 3.0 * math.pi * R ** 3) - 1.0) < tol
+    assert np.all((beta >= 0) & (beta <= 1))
+
+
+def test_ellipsoid_volume_any_orientation(oracle):
+    """Subdivision of a rotated prolate ellipsoid (6,2,2): volume 4/3 pi a b c."""
+    g = W.rng(204)
+    tri = W.quaternion_to_triad(W.random_quaternions(g, 3))
+    n = 20
+    for k in range(3):
+        s = oracle.Sim(n, n, n, periodic=(1, 1, 1), params=oracle.default_params(voxel=1))
+        s.set_particles([1], [6.0], [[6, 2, 2]], [1.0], [[9.6, 9.3, 9.8]], triad=tri[k:k + 1])
+        beta, _, _ = s.voxelize()
+        assert abs(beta[:, 0].sum() / (4.0 / 3.0 * math.pi * 24.0) - 1.0) < 3e-3
+
+
+def test_two_solids_per_cell(oracle):
+    """At most two solids per cell (Sec. 3.2.3); with three touching a cell the two with
+    the largest solid fraction are kept and the total is reported."""
+    n = 12
+    s = oracle.Sim(n, n, n, periodic=(1, 1, 1), params=oracle.default_params(voxel=0),
+                   max_particles=3)
+    node = np.array([6.0, 6.0, 6.0])
+    dirs = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    R = 2.0
+    dist = [R + 0.1, R - 0.2, R + 0.3]     # betas ordered: 2nd > 1st > 3rd
+    pos = node - dirs * np.array(dist)[:, None]
+    s.set_particles([0, 0, 0], [R] * 3, [[R] * 3] * 3, [1.0] * 3, pos)
+    beta, ids, ns = s.voxelize()
+    cell = 6 + n * (6 + n * 6)
+    assert ns[cell] == 3
+    assert list(ids[cell]) == [1, 0]
+    assert beta[cell, 0] > beta[cell, 1] > 0
+
+
+def test_stokes_drag_periodic_array(oracle):
+    """A fixed sphere in a periodic box with the fluid driven by a body force. At steady
+    state the drag equals the total force on the fluid (momentum balance), and it is
+    within the low-resolution PSM effective-radius deficit of Stokes drag corrected for a
+    periodic array (Hasimoto 1959: K = 1/(1 - 1.7601 c^(1/3) + c - 1.5593 c^2))."""
+    N, R, tau, f = 16, 2.5, 1.0, 1e-6
+    nu = (tau - 0.5) / 3
+    s = oracle.Sim(N, N, N, periodic=(1, 1, 1),
+                   params=oracle.default_params(tau=tau, voxel=0, fluid_force=(f, 0, 0)))
+    c = N / 2 - 0.5
+    s.set_particles([0], [R], [[R] * 3], [1.0], [[c, c, c]])
+    for _ in range(3000):
+        s.lbm_psm_step()
+    Fh, _, _, _ = s.forces()
+    _, u = s.moments()
+    beta, _, _ = s.voxelize()
+    B = beta[:, 0] * (tau - 0.5) / ((1 - beta[:, 0]) + (tau - 0.5))
+    ftot = f * (1.0 - np.minimum(B, 1.0)).sum()
+    assert abs(Fh[0, 0] / ftot - 1.0) < 0.01
+    phi = 4.0 / 3.0 * math.pi * R ** 3 / N ** 3
+    K = 1.0 / (1 - 1.7601 * phi ** (1 / 3) + phi - 1.5593 * phi ** 2)
+    ratio = Fh[0, 0] / (6 * math.pi * nu * R * u[0].mean() * K)
+    assert 0.75 < ratio < 1.05
+    assert abs(Fh[0, 1]) < 1e-12 and abs(Fh[0, 2]) < 1e-12
+
+
+def test_rotating_sphere_torque(oracle):
+    """A sphere spinning at fixed omega feels a torque opposing the spin, of the order of
+    the Stokes value 8 pi mu R^3 omega. (With the sign of u_k as printed in Sec. 2.4 the
+    torque would drive the spin instead.)"""
+    N, R, tau, w = 16, 2.5, 1.0, 1e-3
+    nu = (tau - 0.5) / 3
+    s = oracle.Sim(N, N, N, periodic=(1, 1, 1), params=oracle.default_params(tau=tau, voxel=1))
+    c = N / 2 - 0.5
+    s.set_particles([0], [R], [[R] * 3], [1.0], [[c, c, c]], omg=[[0, 0, w]])
+    for _ in range(800):
+        s.lbm_psm_step()
+    _, Mh, _, _ = s.forces()
+    ratio = Mh[0, 2] / (-8 * math.pi * nu * R ** 3 * w)
+    assert 0.6 < ratio < 1.1
+    assert abs(Mh[0, 0]) < 1e-10 * abs(Mh[0, 2]) + 1e-15
