@@ -1,0 +1,309 @@
+"""Benchmark of the coupled LBM-PSM-DEM step (one JSON line on rank 0).
+
+Workload: particle-laden Couette flow, D3Q19 PSM lattice 256^3, walls at z moving at
+-/+0.05, periodic x and y, 4000 spheres of radius 6 (solid fraction ~0.22) at seeded RSA
+positions, density ratio 1, distance-based solid fractions, 10 DEM substeps per fluid
+step, linear contacts. A step is one coupled fluid step (all DEM substeps, tile binning,
+the fused PSM collide-stream and the final corrector). Metric: coupled-step MLUPS (cells
+x steps / time), with the PSM kernel's fraction of the measured HBM bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--storage f32|f16|bf16]
+  python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+With N > 1 (torchrun) every rank runs an independent replica of the workload on its own
+GPU (the step does not shard; no collective on the data path) and the value is the
+aggregate over ranks (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS & % HBM roofline, FP32 vs FP16-stored f at stated error"
+BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76}   # 2 x 19 populations per update
+STAGES = ["neighbour_rebuild", "dem_substeps", "tile_binning", "psm_collide_stream", "final_corrector"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def psm_source_hash():
+    h = hashlib.sha256()
+    for f in ("lbm.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2512_04997_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_cell(storage):
+    """DRAM bytes per cell update of the PSM kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "psm_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != psm_source_hash():
+        return None
+    v = d.get("bytes_per_cell", {}).get(storage)
+    return float(v) if v is not None else None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.file = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL,
+                                         start_new_session=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        os.killpg(self.proc.pid, signal.SIGTERM)
+        self.proc.wait()
+        self.file.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.file.name):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(steps):
+    """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
+    slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps."""
+    from oracle import oracle as O
+    from paper_2512_04997_gb300 import workloads as W
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _helpers import oracle_from_workload
+    w = W.couette_suspension(nx=256, ny=256, nz=32, n_particles=500)
+    o = oracle_from_workload(O, w)
+    o.step(1)   # warm
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = w.ncell * steps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} coupled steps of a 256x256x32 slab of the workload "
+                      f"(500 spheres, same solid fraction), FP64, single thread",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    steps = max(1, min(args.steps, 8))
+    warm = max(0, min(args.warmup, 1))
+    from oracle import oracle as O  # noqa: F401  (built on first use)
+    if warm:
+        oracle_sample(1)
+    res = oracle_sample(steps)
+    line = {"metric": METRIC, "value": res["value"], "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * res["seconds"] / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "couette_suspension_256x256x32_500spheres (slab sample of "
+                                   "couette_suspension_256x256x256_4000spheres)", "n_sub": 10},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
+                             "value": res["value"], "unit": "MLUPS"},
+            "e2e": {"value": res["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist = td
+    hbm, peak_kind = peaks()
+    w = W.couette_suspension(storage=args.storage)
+    N = w.ncell
+    sim = ledds.from_workload(w, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (graph capture happens here)
+    sim.step(args.warmup)
+    barrier()
+    clocks = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = N * args.steps * world / (ms * 1e-3) / 1e6
+    st = sim.status()
+
+    # profiled pass: CUDA events around every stage of each step (eager launches)
+    sim.set_profiling(True)
+    sim.step(args.steps)
+    stage_ms, psteps, plaunch = sim.read_profile()
+    sim.set_profiling(False)
+    psm_ms = stage_ms[3] / psteps
+    bpc = BYTES_PER_CELL[args.storage]
+    achieved = N * bpc / (psm_ms * 1e-3) / 1e9
+    tpc = traffic_per_cell(args.storage)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": (tpc * N if tpc is not None else None),
+                "kernel": "k_psm (fused PSM collide-stream, solid fractions, force reduction)",
+                "algorithmic_bytes_per_launch": N * bpc, "peak_kind": peak_kind,
+                "avg_launch_ms": psm_ms}
+
+    # end to end through the C-ABI: particle kinematics in from pinned host memory, one
+    # step, kinematics out to pinned host memory, every step
+    n = w.n
+    h_in = torch.empty(18 * n, dtype=torch.float64, pin_memory=True)
+    h_out = torch.empty(18 * n, dtype=torch.float64, pin_memory=True)
+    sim.step(1)
+    ledds.check("ledds_read_particles", ledds.lib().ledds_read_particles(sim.h, h_in.data_ptr(), 0))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ledds.check("ledds_write_kinematics", ledds.lib().ledds_write_kinematics(sim.h, h_in.data_ptr(), 0))
+        sim.step(1)
+        ledds.check("ledds_read_particles", ledds.lib().ledds_read_particles(sim.h, h_out.data_ptr(), 0))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 18 * 8 * n, "d2h_bytes_per_step": 18 * 8 * n,
+           "api": "ledds_write_kinematics(host) + ledds_step(1) + ledds_read_particles(host)"}
+
+    variants = {}
+    if not args.no_variants and args.storage == "f32":
+        # reduced-precision storage: same workload and steps; field error against FP32
+        ref = ledds.from_workload(w, device=f"cuda:{local}")
+        ref.step(args.warmup + args.steps)
+        _, u_ref = ref.fields()
+        del ref
+        for sto in ("f16", "bf16"):
+            v = ledds.from_workload(w, device=f"cuda:{local}", storage=sto)
+            v.step(args.warmup)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            v.step(args.steps)
+            a1.record(stream)
+            a1.synchronize()
+            vms = a0.elapsed_time(a1)
+            _, u_v = v.fields()
+            err = float((u_v - u_ref).abs().max() / u_ref.abs().max())
+            v.set_profiling(True)
+            v.step(args.steps)
+            sm_, ps_, _ = v.read_profile()
+            pms = sm_[3] / ps_
+            ach = N * BYTES_PER_CELL[sto] / (pms * 1e-3) / 1e9
+            variants[sto] = {"value": N * args.steps / (vms * 1e-3) / 1e6, "unit": "MLUPS",
+                             "speedup_vs_f32": (N * args.steps / (vms * 1e-3) / 1e6) / value * world,
+                             "field_error_vs_f32": err,
+                             "roofline": {"achieved": ach, "frac": ach / hbm, "unit": "GB/s"}}
+            del v
+            torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(2)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": w.name, "cells": N, "particles": w.n,
+                           "storage": args.storage, "n_sub": w.params["n_sub"],
+                           "tau": w.params["tau"], "voxel": w.params["voxel"],
+                           "l2": "inputs larger than L2 (populations 2 x 19 x 16.8M values)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": st["launches_per_step"] * args.steps,
+                "clocks": clk, "stages_ms_per_step": {k: v / psteps for k, v in zip(STAGES, stage_ms)},
+                "status": {k: st[k] for k in ("tile_overflow", "cand_overflow", "skin_violation",
+                                              "nan_detected", "solids_overflow")},
+                "variants": variants}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,7 +153,7 @@ or_sim* or_create(int nx, int ny, int nz, const double box_lo[3], const double b
     s->chist = (double*)xcalloc(3 * s->contcap, sizeof(double));
     /* DEM grid (Sec. 3.2.1): spacing >= the requested h, integer cells per axis. */
     for (int a = 0; a < 3; ++a) {
-        int g = (int)floor(s->L[a] / p->dem_h);
+        int g = p->dem_h > 0.0 ? (int)floor(s->L[a] / p->dem_h) : 1;
         if (g < 1) g = 1;
         s->gn[a] = g;
         s->gh[a] = s->L[a] / g;
@@ -1297,7 +1297,7 @@ void or_step(or_sim* s, int nsteps) {
     int nsub = s->p.n_sub > 0 ? s->p.n_sub : 1;
     double dt = 1.0 / nsub;
     for (int st = 0; st < nsteps; ++st) {
-        for (int sub = 1; sub <= nsub; ++sub) {
+        for (int sub = 1; sub <= nsub && s->n > 0; ++sub) {
             predict(s, dt);
             or_contact_forces(s, dt);
             if (sub < nsub || s->ncell == 0) correct(s, dt, s->Fh_prev, s->Mh_prev);

@@ -1,0 +1,917 @@
+// api.cu -- C ABI of the LEDDS GB300 library (declared in include/ledds.h).
+//
+// Host-side orchestration: workspace layout (the library allocates no device memory),
+// parameter validation, particle upload, and the coupled step of the flowchart of
+// Sec. 3.2 enqueued as kernels and replayed as CUDA graphs (one graph per starting
+// buffer parity for one step and for two steps, so buffers return to their roles).
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace ledds {
+cudaError_t launch_init(const LbmArgs&, int, const float*, const float*, const float*, cudaStream_t);
+cudaError_t launch_read(const LbmArgs&, int, float*, float*, float*, int, cudaStream_t);
+cudaError_t launch_rebase(const LbmArgs&, int, const float (*)[2][3], cudaStream_t);
+cudaError_t launch_bin(const LbmArgs&, int, int*, int*, cudaStream_t);
+cudaError_t launch_psm(const LbmArgs&, int, cudaStream_t);
+cudaError_t launch_voxelize(const LbmArgs&, float*, int*, int*, cudaStream_t);
+cudaError_t launch_rebuild(const DemArgs&, int, int, uint32_t*, cudaStream_t, int*);
+cudaError_t launch_predict_first(const DemArgs&, cudaStream_t);
+cudaError_t launch_substep(const DemArgs&, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_final(const DemArgs&, int, int, cudaStream_t);
+cudaError_t launch_pairs(const DemArgs&, int, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
+                         int, cudaStream_t);
+cudaError_t launch_scan(const uint32_t*, int, uint32_t*, uint32_t*, cudaStream_t);
+}  // namespace ledds
+
+using namespace ledds;
+
+static const double kPi = 3.14159265358979323846;
+enum { NSTAGE = 5 };
+
+struct ledds_sim_s {
+    ledds_dims d;
+    ledds_params p;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    // lattice
+    bool lattice = false;
+    long long N = 0;
+    int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
+    void* pop[2] = {nullptr, nullptr};
+    int* tile_count = nullptr;
+    int* tile_ids = nullptr;
+    int tile_cap = 0;
+    // particles
+    DevParticles P{};
+    int ccap = 0;
+    double lo[3], hi[3], L[3];
+    int gn[3] = {1, 1, 1};
+    double gh[3] = {1, 1, 1};
+    int G = 1;
+    uint32_t *keys = nullptr, *cell_count = nullptr, *cell_start = nullptr, *scan_partial = nullptr;
+    uint32_t *pair_cnt = nullptr, *pair_off = nullptr;
+    int *rank = nullptr, *sorted = nullptr;
+    int* cand[2] = {nullptr, nullptr};
+    int* ncand[2] = {nullptr, nullptr};
+    double* hist[2] = {nullptr, nullptr};
+    double* whist = nullptr;
+    DevStatus* status = nullptr;
+    // state
+    double uw[3][2][3];
+    int parity = 0;          // pop[parity], cand[parity] hold the current data
+    long long steps = 0;
+    // graphs
+    cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
+    int launches_per_step = 0;
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev[NSTAGE + 1];
+    bool ev_made = false;
+    double prof_ms[NSTAGE];
+    long long prof_steps = 0, prof_launches = 0;
+};
+
+// ------------------------------------------------------------------------------------
+// Workspace layout
+// ------------------------------------------------------------------------------------
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static int check_args(const ledds_dims* d, const ledds_params* p) {
+    if (!d || !p) return LEDDS_ERR_INVALID_ARG;
+    if (d->nx < 0 || d->ny < 0 || d->nz < 0) return LEDDS_ERR_INVALID_ARG;
+    bool lat = d->nx > 0 || d->ny > 0 || d->nz > 0;
+    if (lat && (d->nx <= 0 || d->ny <= 0 || d->nz <= 0)) return LEDDS_ERR_INVALID_ARG;
+    // populations are addressed with 32-bit element offsets
+    if (lat && 20.0 * (double)d->nx * d->ny * d->nz >= 2147483647.0) return LEDDS_ERR_INVALID_ARG;
+    if (!lat && d->max_particles <= 0) return LEDDS_ERR_INVALID_ARG;
+    if (d->max_particles < 0) return LEDDS_ERR_INVALID_ARG;
+    if (!(p->tau > 0.5)) return LEDDS_ERR_INVALID_ARG;
+    if (p->storage < 0 || p->storage > 2) return LEDDS_ERR_INVALID_ARG;
+    if (p->voxel < 0 || p->voxel > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->subdiv_n < 1 || p->subdiv_n > 16) return LEDDS_ERR_INVALID_ARG;
+    if (p->law < 0 || p->law > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->n_sub < 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->storage_scale_log2 < -30 || p->storage_scale_log2 > 30) return LEDDS_ERR_INVALID_ARG;
+    if (d->cand_cap < 0 || d->cand_cap > MAX_CAND_CAP) return LEDDS_ERR_INVALID_ARG;
+    if (d->tile_cap < 0 || d->tile_cap > MAX_TILE_CAP) return LEDDS_ERR_INVALID_ARG;
+    if (d->max_particles > 0 && !(p->dem_h > 0.0)) return LEDDS_ERR_INVALID_ARG;
+    if (p->skin < 0.0) return LEDDS_ERR_INVALID_ARG;
+    if (!lat) {
+        for (int a = 0; a < 3; ++a)
+            if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
+    }
+    return LEDDS_OK;
+}
+
+static void domain(const ledds_dims* d, double lo[3], double hi[3], double L[3]) {
+    bool lat = d->nx > 0;
+    int n3[3] = {d->nx, d->ny, d->nz};
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = lat ? -0.5 : d->box_lo[a];
+        hi[a] = lat ? n3[a] - 0.5 : d->box_hi[a];
+        L[a] = hi[a] - lo[a];
+    }
+}
+
+static void grid_of(const ledds_dims* d, const ledds_params* p, int gn[3], double gh[3], int* G) {
+    double lo[3], hi[3], L[3];
+    domain(d, lo, hi, L);
+    *G = 1;
+    for (int a = 0; a < 3; ++a) {
+        int g = p->dem_h > 0 ? (int)floor(L[a] / p->dem_h) : 1;
+        if (g < 1) g = 1;
+        gn[a] = g;
+        gh[a] = L[a] / g;
+        *G *= g;
+    }
+}
+
+// Lays out every device array; with base == nullptr only computes the size.
+static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p, char* base) {
+    Carver c{base};
+    long long N = (long long)d->nx * d->ny * d->nz;
+    size_t sb = storage_bytes(p->storage);
+    int ntx = (d->nx + TILE_X - 1) / TILE_X, nty = (d->ny + TILE_Y - 1) / TILE_Y,
+        ntz = (d->nz + TILE_Z - 1) / TILE_Z;
+    int ntiles = N > 0 ? ntx * nty * ntz : 0;
+    int tcap = d->tile_cap > 0 ? d->tile_cap : 64;
+    int cap = d->max_particles > 0 ? d->max_particles : 0;
+    int ccap = d->cand_cap > 0 ? d->cand_cap : 32;
+    int gn[3];
+    double gh[3];
+    int G;
+    grid_of(d, p, gn, gh, &G);
+    int capc = cap > 0 ? cap : 1;
+    void* pop0 = c.take<char>((size_t)N * 19 * sb);
+    void* pop1 = c.take<char>((size_t)N * 19 * sb);
+    int* tcount = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1));
+    int* tids = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1) * tcap);
+    double* st0 = c.take<double>(18 * (size_t)capc);
+    double* st1 = c.take<double>(18 * (size_t)capc);
+    double* acc = c.take<double>(3 * (size_t)capc);
+    double* alpha = c.take<double>(3 * (size_t)capc);
+    double* Fc = c.take<double>(3 * (size_t)capc);
+    double* Mc = c.take<double>(3 * (size_t)capc);
+    double* Fh = c.take<double>(6 * (size_t)capc);  // Fh then Mh, contiguous
+    double* Fhp = c.take<double>(6 * (size_t)capc);
+    double* pb = c.take<double>(3 * (size_t)capc);
+    double* radius = c.take<double>((size_t)capc);
+    double* semi = c.take<double>(3 * (size_t)capc);
+    double* bound = c.take<double>((size_t)capc);
+    double* mass = c.take<double>((size_t)capc);
+    double* inertia = c.take<double>(3 * (size_t)capc);
+    double* gfac = c.take<double>((size_t)capc);
+    int* shape = c.take<int>((size_t)capc);
+    uint32_t* keys = c.take<uint32_t>((size_t)capc);
+    int* rank = c.take<int>((size_t)capc);
+    int* sorted = c.take<int>((size_t)capc);
+    uint32_t* ccount = c.take<uint32_t>((size_t)G + 1);
+    uint32_t* cstart = c.take<uint32_t>((size_t)G + 1);
+    uint32_t* partial = c.take<uint32_t>(4096);
+    uint32_t* pcnt = c.take<uint32_t>((size_t)capc);
+    uint32_t* poff = c.take<uint32_t>((size_t)capc + 1);
+    int* cand0 = c.take<int>((size_t)capc * ccap);
+    int* cand1 = c.take<int>((size_t)capc * ccap);
+    int* nc0 = c.take<int>((size_t)capc);
+    int* nc1 = c.take<int>((size_t)capc);
+    double* h0 = c.take<double>((size_t)capc * ccap * 3);
+    double* h1 = c.take<double>((size_t)capc * ccap * 3);
+    double* wh = c.take<double>((size_t)capc * 18);
+    DevStatus* status = c.take<DevStatus>(1);
+    size_t total = c.off + 256;
+    if (s && base) {
+        s->N = N;
+        s->lattice = N > 0;
+        s->ntx = ntx;
+        s->nty = nty;
+        s->ntz = ntz;
+        s->ntiles = ntiles;
+        s->tile_cap = tcap;
+        s->pop[0] = pop0;
+        s->pop[1] = pop1;
+        s->tile_count = tcount;
+        s->tile_ids = tids;
+        s->ccap = ccap;
+        DevParticles& P = s->P;
+        P.n = 0;
+        P.cap = capc;
+        P.st[0] = st0;
+        P.st[1] = st1;
+        P.acc = acc;
+        P.alpha = alpha;
+        P.Fc = Fc;
+        P.Mc = Mc;
+        P.Fh = Fh;
+        P.Mh = Fh + 3 * (size_t)capc;
+        P.Fhp = Fhp;
+        P.Mhp = Fhp + 3 * (size_t)capc;
+        P.pos_build = pb;
+        P.radius = radius;
+        P.semi = semi;
+        P.bound = bound;
+        P.mass = mass;
+        P.inertia = inertia;
+        P.gfac = gfac;
+        P.shape = shape;
+        s->keys = keys;
+        s->rank = rank;
+        s->sorted = sorted;
+        s->cell_count = ccount;
+        s->cell_start = cstart;
+        s->scan_partial = partial;
+        s->pair_cnt = pcnt;
+        s->pair_off = poff;
+        s->cand[0] = cand0;
+        s->cand[1] = cand1;
+        s->ncand[0] = nc0;
+        s->ncand[1] = nc1;
+        s->hist[0] = h0;
+        s->hist[1] = h1;
+        s->whist = wh;
+        s->status = status;
+        for (int a = 0; a < 3; ++a) {
+            s->gn[a] = gn[a];
+            s->gh[a] = gh[a];
+        }
+        s->G = G;
+    }
+    return total;
+}
+
+static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
+    LbmArgs a{};
+    a.nx = s->d.nx;
+    a.ny = s->d.ny;
+    a.nz = s->d.nz;
+    a.N = s->N;
+    for (int q = 0; q < 3; ++q) a.per[q] = s->d.periodic[q];
+    for (int q = 0; q < 3; ++q)
+        for (int e = 0; e < 2; ++e)
+            for (int c = 0; c < 3; ++c) a.uw[q][e][c] = (float)s->uw[q][e][c];
+    a.tau = (float)s->p.tau;
+    a.omega = (float)(1.0 / s->p.tau);
+    for (int q = 0; q < 3; ++q) a.F[q] = (float)s->p.fluid_force[q];
+    a.has_force = (s->p.fluid_force[0] != 0 || s->p.fluid_force[1] != 0 || s->p.fluid_force[2] != 0);
+    a.guo_pref = (float)(1.0 - 0.5 / s->p.tau);
+    double sc = s->p.storage == LEDDS_STORE_F16 ? ldexp(1.0, s->p.storage_scale_log2) : 1.0;
+    a.scale = (float)sc;
+    a.inv_scale = (float)(1.0 / sc);
+    a.pop_in = s->pop[in];
+    a.pop_out = s->pop[out];
+    for (int i = 0; i < 19; ++i) {
+        a.pN[i] = (int)(i * s->N);
+        a.off[i] = CX(i) + s->d.nx * (CY(i) + s->d.ny * CZ(i));
+        if (a.off[i] & 1) a.off_odd |= 1u << i;
+    }
+    a.ntx = s->ntx;
+    a.nty = s->nty;
+    a.ntz = s->ntz;
+    a.tile_cap = s->tile_cap;
+    a.tile_count = s->tile_count;
+    a.tile_ids = s->tile_ids;
+    a.st = s->P.st[pst];
+    a.pcap = s->P.cap;
+    a.radius = s->P.radius;
+    a.semi = s->P.semi;
+    a.bound = s->P.bound;
+    a.shape = s->P.shape;
+    a.Fh = s->P.Fh;
+    a.Mh = s->P.Mh;
+    a.voxel = s->p.voxel;
+    a.subdiv_n = s->p.subdiv_n;
+    a.Rc = (float)cbrt(3.0 / (4.0 * kPi));
+    a.status = s->status;
+    return a;
+}
+
+static DemArgs dem_args(const ledds_sim_s* s) {
+    DemArgs A{};
+    A.P = s->P;
+    for (int a = 0; a < 3; ++a) {
+        A.lo[a] = s->lo[a];
+        A.hi[a] = s->hi[a];
+        A.L[a] = s->L[a];
+        A.per[a] = s->d.periodic[a];
+        A.gn[a] = s->gn[a];
+        A.gh[a] = s->gh[a];
+        A.gravity[a] = s->p.gravity[a];
+    }
+    memcpy(A.uw, s->uw, sizeof(A.uw));
+    A.G = s->G;
+    A.dt = 1.0 / s->p.n_sub;
+    A.law = s->p.law;
+    A.k_n = s->p.k_n;
+    A.k_t = s->p.k_t;
+    double eps = s->p.restitution;
+    double beta = 0.0;
+    if (eps > 0.0 && eps < 1.0) {
+        double le = log(eps);
+        beta = le / sqrt(le * le + kPi * kPi);
+    } else if (eps <= 0.0) {
+        beta = -1.0;
+    }
+    A.beta = beta;
+    double E = s->p.young, nu = s->p.poisson;
+    A.Ystar = 1.0 / ((1.0 - nu * nu) / E + (1.0 - nu * nu) / E);
+    A.Gstar = 1.0 / (2.0 * (2.0 - nu) * (1.0 + nu) / E + 2.0 * (2.0 - nu) * (1.0 + nu) / E);
+    A.mu = s->p.friction;
+    A.skin = s->p.skin;
+    A.ell_max_iter = s->p.ell_max_iter;
+    A.ell_tol = s->p.ell_tol;
+    A.ccap = s->ccap;
+    A.keys = s->keys;
+    A.rank = s->rank;
+    A.sorted = s->sorted;
+    A.cell_count = s->cell_count;
+    A.cell_start = s->cell_start;
+    for (int b = 0; b < 2; ++b) {
+        A.cand[b] = s->cand[b];
+        A.ncand[b] = s->ncand[b];
+        A.hist[b] = s->hist[b];
+    }
+    A.whist = s->whist;
+    A.status = s->status;
+    return A;
+}
+
+static void drop_graphs(ledds_sim_s* s) {
+    for (int q = 0; q < 2; ++q) {
+        if (s->g1[q]) cudaGraphExecDestroy(s->g1[q]);
+        if (s->g2[q]) cudaGraphExecDestroy(s->g2[q]);
+        s->g1[q] = s->g2[q] = nullptr;
+    }
+}
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return e_;       \
+    } while (0)
+
+// The coupled step, flowchart order of Sec. 3.2, starting from buffer parity p.
+// ev (optional) receives NSTAGE+1 events bracketing the stages.
+static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* launches,
+                                cudaEvent_t* ev) {
+    const int n = s->P.n;
+    const int nsub = s->p.n_sub;
+    const int last = (nsub - 1) & 1;
+    DemArgs A = dem_args(s);
+    if (ev) CK(cudaEventRecord(ev[0], st));
+    if (n > 0) {
+        // particle/grid stage: neighbour rebuild (keys, counting sort, candidates)
+        CK(launch_rebuild(A, p, p ^ 1, s->scan_partial, st, launches));
+    }
+    if (ev) CK(cudaEventRecord(ev[1], st));
+    if (n > 0) {
+        CK(launch_predict_first(A, st));
+        *launches += 1;
+        for (int sub = 1; sub < nsub; ++sub) {
+            CK(launch_substep(A, (sub - 1) & 1, sub & 1, p ^ 1, 1, 1, st));
+            *launches += 2;
+        }
+        CK(launch_substep(A, last, last, p ^ 1, 0, 0, st));
+        *launches += 1;
+    }
+    if (ev) CK(cudaEventRecord(ev[2], st));
+    if (s->lattice) {
+        LbmArgs la = lbm_args(s, p, p ^ 1, last);
+        CK(cudaMemsetAsync(s->tile_count, 0, sizeof(int) * (size_t)s->ntiles, st));
+        if (n > 0) {
+            CK(cudaMemsetAsync(s->P.Fh, 0, sizeof(double) * 6 * (size_t)s->P.cap, st));
+            CK(launch_bin(la, n, s->tile_count, s->tile_ids, st));
+            *launches += 1;
+        }
+        if (ev) CK(cudaEventRecord(ev[3], st));
+        CK(launch_psm(la, s->p.storage, st));
+        *launches += 1;
+    } else if (ev) {
+        CK(cudaEventRecord(ev[3], st));
+    }
+    if (ev) CK(cudaEventRecord(ev[4], st));
+    if (n > 0) {
+        CK(launch_final(A, last, s->lattice ? 1 : 0, st));
+        *launches += 1;
+    }
+    if (ev) CK(cudaEventRecord(ev[5], st));
+    return cudaSuccess;
+}
+
+static cudaError_t capture(ledds_sim_s* s, int p, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    int launches = 0;
+    CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < nsteps && e == cudaSuccess; ++q) e = enqueue_step(s, p ^ (q & 1), s->cap_stream, &launches, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    s->launches_per_step = launches / nsteps;
+    return e;
+}
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+int ledds_version(void) { return 1; }
+
+const char* ledds_strerror(int code) {
+    switch (code) {
+        case LEDDS_OK: return "ok";
+        case LEDDS_ERR_INVALID_ARG: return "invalid argument";
+        case LEDDS_ERR_CAPACITY: return "capacity exceeded";
+        case LEDDS_ERR_NAN: return "non-finite values detected";
+        case LEDDS_ERR_TIMEOUT: return "device wait timed out";
+        case LEDDS_ERR_CUDA: return "CUDA runtime error";
+        case LEDDS_ERR_STATE: return "invalid state for this call";
+        default: return "unknown error";
+    }
+}
+
+int ledds_params_default(ledds_params* p) {
+    if (!p) return LEDDS_ERR_INVALID_ARG;
+    memset(p, 0, sizeof(*p));
+    p->tau = 0.8;
+    p->storage = LEDDS_STORE_F32;
+    p->storage_scale_log2 = 10;
+    p->voxel = LEDDS_VOXEL_DISTANCE;
+    p->subdiv_n = 10;
+    p->law = LEDDS_LAW_LINEAR;
+    p->n_sub = 1;
+    p->rho_f = 1.0;
+    p->k_n = 1000.0;
+    p->k_t = 1000.0 * 2.0 / 7.0;
+    p->young = 1.0e4;
+    p->poisson = 0.3;
+    p->restitution = 0.7;
+    p->friction = 0.4;
+    p->skin = 0.5;
+    p->dem_h = 0.0;
+    p->ell_max_iter = 60;
+    p->ell_tol = 1e-6;
+    return LEDDS_OK;
+}
+
+int ledds_workspace_size(const ledds_dims* d, const ledds_params* p, size_t* bytes) {
+    int rc = check_args(d, p);
+    if (rc != LEDDS_OK) return rc;
+    if (!bytes) return LEDDS_ERR_INVALID_ARG;
+    *bytes = layout(nullptr, d, p, nullptr);
+    return LEDDS_OK;
+}
+
+int ledds_create(const ledds_dims* d, const ledds_params* p, void* d_workspace, size_t bytes,
+                 void* stream, ledds_sim_t* out) {
+    int rc = check_args(d, p);
+    if (rc != LEDDS_OK) return rc;
+    if (!out || !d_workspace || ((uintptr_t)d_workspace & 255)) return LEDDS_ERR_INVALID_ARG;
+    size_t need = layout(nullptr, d, p, nullptr);
+    if (bytes < need) return LEDDS_ERR_INVALID_ARG;
+    ledds_sim_s* s = new ledds_sim_s();
+    s->d = *d;
+    s->p = *p;
+    s->stream = (cudaStream_t)stream;
+    s->ws = (char*)d_workspace;
+    s->ws_bytes = bytes;
+    memset(s->uw, 0, sizeof(s->uw));
+    domain(d, s->lo, s->hi, s->L);
+    layout(s, d, p, s->ws);
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return LEDDS_ERR_CUDA;
+    }
+    cudaError_t e = cudaMemsetAsync(s->ws, 0, need - 256, s->stream);
+    if (e == cudaSuccess && s->lattice) {
+        LbmArgs a = lbm_args(s, 0, 0, 0);
+        e = launch_init(a, s->p.storage, nullptr, nullptr, nullptr, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s->cap_stream);
+        delete s;
+        return LEDDS_ERR_CUDA;
+    }
+    *out = s;
+    return LEDDS_OK;
+}
+
+int ledds_destroy(ledds_sim_t s) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    drop_graphs(s);
+    if (s->ev_made)
+        for (int q = 0; q <= NSTAGE; ++q) cudaEventDestroy(s->ev[q]);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    delete s;
+    return LEDDS_OK;
+}
+
+int ledds_set_wall_velocity(ledds_sim_t s, int axis, int side, const double u[3]) {
+    if (!s || !u || axis < 0 || axis > 2 || side < 0 || side > 1) return LEDDS_ERR_INVALID_ARG;
+    if (s->d.periodic[axis]) return LEDDS_ERR_INVALID_ARG;
+    float old[3][2][3];
+    for (int q = 0; q < 3; ++q)
+        for (int e = 0; e < 2; ++e)
+            for (int c = 0; c < 3; ++c) old[q][e][c] = (float)s->uw[q][e][c];
+    for (int c = 0; c < 3; ++c) s->uw[axis][side][c] = u[c];
+    drop_graphs(s);
+    if (s->lattice) {
+        // the current pre-collision populations stay as they are
+        LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+        if (launch_rebase(a, s->p.storage, old, s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+    }
+    return LEDDS_OK;
+}
+
+int ledds_set_forcing(ledds_sim_t s, const double gravity[3], const double fluid_force[3]) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (gravity)
+        for (int c = 0; c < 3; ++c) s->p.gravity[c] = gravity[c];
+    if (fluid_force)
+        for (int c = 0; c < 3; ++c) s->p.fluid_force[c] = fluid_force[c];
+    drop_graphs(s);
+    return LEDDS_OK;
+}
+
+int ledds_init_fluid(ledds_sim_t s, const float* d_rho, const float* d_u) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (!s->lattice) return LEDDS_ERR_STATE;
+    LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+    return launch_init(a, s->p.storage, d_rho, d_u, nullptr, s->stream) == cudaSuccess ? LEDDS_OK
+                                                                                       : LEDDS_ERR_CUDA;
+}
+
+int ledds_init_populations(ledds_sim_t s, const float* d_f) {
+    if (!s || !d_f) return LEDDS_ERR_INVALID_ARG;
+    if (!s->lattice) return LEDDS_ERR_STATE;
+    LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+    return launch_init(a, s->p.storage, nullptr, nullptr, d_f, s->stream) == cudaSuccess ? LEDDS_OK
+                                                                                       : LEDDS_ERR_CUDA;
+}
+
+static int upload_rows(ledds_sim_t s, double* dst, const double* src, int rows, int n, int on_device) {
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(double) * s->P.cap, src, sizeof(double) * n,
+                                      sizeof(double) * n, rows, kind, s->stream);
+    return e == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
+}
+
+int ledds_set_particles(ledds_sim_t s, int n, const ledds_particle* h) {
+    if (!s || n < 0 || n > s->d.max_particles || (n > 0 && !h)) return LEDDS_ERR_INVALID_ARG;
+    std::vector<double> st(18 * (size_t)(n > 0 ? n : 1)), radius(n + 1), semi(3 * (size_t)n + 3), bound(n + 1),
+        mass(n + 1), inertia(3 * (size_t)n + 3), gfac(n + 1), acc(3 * (size_t)n + 3);
+    std::vector<int> shape(n + 1);
+    double bmax = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const ledds_particle& q = h[k];
+        if (q.shape != LEDDS_SPHERE && q.shape != LEDDS_ELLIPSOID) return LEDDS_ERR_INVALID_ARG;
+        if (!(q.density > 0.0)) return LEDDS_ERR_INVALID_ARG;
+        double V, m, I[3], b;
+        if (q.shape == LEDDS_SPHERE) {
+            double R = q.radius;
+            if (!(R > 0.0)) return LEDDS_ERR_INVALID_ARG;
+            V = 4.0 / 3.0 * kPi * R * R * R;
+            m = q.density * V;
+            for (int a = 0; a < 3; ++a) I[a] = 2.0 * m * R * R / 5.0;
+            radius[k] = R;
+            b = R;
+            for (int a = 0; a < 3; ++a) semi[a * (size_t)n + k] = R;
+        } else {
+            double A = q.semi[0], B = q.semi[1], C = q.semi[2];
+            if (!(A > 0.0 && B > 0.0 && C > 0.0)) return LEDDS_ERR_INVALID_ARG;
+            V = 4.0 / 3.0 * kPi * A * B * C;
+            m = q.density * V;
+            I[0] = m * (B * B + C * C) / 5.0;
+            I[1] = m * (A * A + C * C) / 5.0;
+            I[2] = m * (A * A + B * B) / 5.0;
+            b = fmax(A, fmax(B, C));
+            radius[k] = b;
+            for (int a = 0; a < 3; ++a) semi[a * (size_t)n + k] = q.semi[a];
+        }
+        // orthonormal triad
+        const double* t = q.triad;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double dd = t[3 * i] * t[3 * j] + t[3 * i + 1] * t[3 * j + 1] + t[3 * i + 2] * t[3 * j + 2];
+                if (fabs(dd - (i == j ? 1.0 : 0.0)) > 1e-6) return LEDDS_ERR_INVALID_ARG;
+            }
+        bound[k] = b;
+        bmax = fmax(bmax, b);
+        mass[k] = m;
+        for (int a = 0; a < 3; ++a) inertia[a * (size_t)n + k] = I[a];
+        gfac[k] = 1.0 - s->p.rho_f / q.density;
+        shape[k] = q.shape;
+        for (int a = 0; a < 3; ++a) {
+            st[(SP + a) * (size_t)n + k] = q.pos[a];
+            st[(SV + a) * (size_t)n + k] = q.vel[a];
+            st[(SW + a) * (size_t)n + k] = q.omg[a];
+            acc[a * (size_t)n + k] = s->p.gravity[a] * gfac[k];
+        }
+        for (int m9 = 0; m9 < 9; ++m9) st[(ST + m9) * (size_t)n + k] = t[m9];
+    }
+    // The candidate search covers the 27 neighbouring cells, so a cell must be at least
+    // as wide as the largest interaction range; periodic boxes must exceed twice it.
+    double range = 2.0 * bmax + s->p.skin;
+    for (int a = 0; a < 3; ++a) {
+        if (n > 0 && s->gh[a] < range) return LEDDS_ERR_INVALID_ARG;
+        if (n > 0 && s->d.periodic[a] && s->L[a] <= 2.0 * range) return LEDDS_ERR_INVALID_ARG;
+    }
+    if (s->lattice && n > 0) {
+        int n3[3] = {s->d.nx, s->d.ny, s->d.nz};
+        double reach = bmax + 1.0 + (cbrt(3.0 / (4.0 * kPi)));
+        for (int a = 0; a < 3; ++a)
+            if (s->d.periodic[a] && 2.0 * reach + 2.0 >= n3[a]) return LEDDS_ERR_INVALID_ARG;
+    }
+    s->P.n = n;
+    drop_graphs(s);
+    if (n > 0) {
+        int rc;
+        if ((rc = upload_rows(s, s->P.st[0], st.data(), 18, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.st[1], st.data(), 18, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.radius, radius.data(), 1, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.semi, semi.data(), 3, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.bound, bound.data(), 1, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.mass, mass.data(), 1, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.inertia, inertia.data(), 3, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.gfac, gfac.data(), 1, n, 0)) != LEDDS_OK) return rc;
+        if ((rc = upload_rows(s, s->P.acc, acc.data(), 3, n, 0)) != LEDDS_OK) return rc;
+        if (cudaMemcpyAsync(s->P.shape, shape.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                            s->stream) != cudaSuccess)
+            return LEDDS_ERR_CUDA;
+    }
+    size_t c3 = sizeof(double) * 3 * (size_t)s->P.cap;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->P.alpha, 0, c3, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->P.Fc, 0, c3, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->P.Mc, 0, c3, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->P.Fh, 0, 2 * c3, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->P.Fhp, 0, 2 * c3, s->stream);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMemsetAsync(s->ncand[b], 0, sizeof(int) * s->P.cap, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->whist, 0, sizeof(double) * 18 * (size_t)s->P.cap, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
+}
+
+int ledds_write_kinematics(ledds_sim_t s, const double* state, int on_device) {
+    if (!s || !state) return LEDDS_ERR_INVALID_ARG;
+    if (s->P.n == 0) return LEDDS_OK;
+    int rc = upload_rows(s, s->P.st[0], state, 18, s->P.n, on_device);
+    if (rc == LEDDS_OK && !on_device && cudaStreamSynchronize(s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+    return rc;
+}
+
+int ledds_step(ledds_sim_t s, int n_steps) {
+    if (!s || n_steps < 0) return LEDDS_ERR_INVALID_ARG;
+    if (s->profiling) {
+        if (!s->ev_made) {
+            for (int q = 0; q <= NSTAGE; ++q)
+                if (cudaEventCreate(&s->ev[q]) != cudaSuccess) return LEDDS_ERR_CUDA;
+            s->ev_made = true;
+        }
+        for (int k = 0; k < n_steps; ++k) {
+            int launches = 0;
+            if (enqueue_step(s, s->parity, s->stream, &launches, s->ev) != cudaSuccess) return LEDDS_ERR_CUDA;
+            if (cudaEventSynchronize(s->ev[NSTAGE]) != cudaSuccess) return LEDDS_ERR_CUDA;
+            for (int q = 0; q < NSTAGE; ++q) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, s->ev[q], s->ev[q + 1]);
+                s->prof_ms[q] += ms;
+            }
+            s->prof_steps++;
+            s->prof_launches += launches;
+            s->launches_per_step = launches;
+            s->parity ^= 1;
+            s->steps++;
+        }
+        return LEDDS_OK;
+    }
+    int left = n_steps;
+    while (left > 0) {
+        int p = s->parity;
+        if (left >= 2) {
+            if (!s->g2[p] && capture(s, p, 2, &s->g2[p]) != cudaSuccess) return LEDDS_ERR_CUDA;
+            if (cudaGraphLaunch(s->g2[p], s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+            left -= 2;
+            s->steps += 2;
+        } else {
+            if (!s->g1[p] && capture(s, p, 1, &s->g1[p]) != cudaSuccess) return LEDDS_ERR_CUDA;
+            if (cudaGraphLaunch(s->g1[p], s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+            left -= 1;
+            s->steps += 1;
+            s->parity ^= 1;
+        }
+    }
+    return LEDDS_OK;
+}
+
+int ledds_sync(ledds_sim_t s) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
+}
+
+int ledds_get_status(ledds_sim_t s, ledds_status* st) {
+    if (!s || !st) return LEDDS_ERR_INVALID_ARG;
+    DevStatus h;
+    if (cudaMemcpyAsync(&h, s->status, sizeof(h), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    st->steps = s->steps;
+    st->tile_overflow = h.tile_overflow;
+    st->cand_overflow = h.cand_overflow;
+    st->solids_overflow = h.solids_overflow;
+    st->skin_violation = h.skin_violation;
+    st->ell_nonconverged = h.ell_nonconverged;
+    st->nan_detected = h.nan_detected;
+    st->n_particles = s->P.n;
+    st->launches_per_step = s->launches_per_step;
+    if (h.nan_detected) return LEDDS_ERR_NAN;
+    if (h.tile_overflow || h.cand_overflow) return LEDDS_ERR_CAPACITY;
+    return LEDDS_OK;
+}
+
+int ledds_read_fields(ledds_sim_t s, float* d_rho, float* d_u) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (!s->lattice) return LEDDS_ERR_STATE;
+    LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+    return launch_read(a, s->p.storage, d_rho, d_u, nullptr, 0, s->stream) == cudaSuccess ? LEDDS_OK
+                                                                                       : LEDDS_ERR_CUDA;
+}
+
+int ledds_read_populations(ledds_sim_t s, float* d_f, int which) {
+    if (!s || !d_f || which < 0 || which > 1) return LEDDS_ERR_INVALID_ARG;
+    if (!s->lattice) return LEDDS_ERR_STATE;
+    LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+    return launch_read(a, s->p.storage, nullptr, nullptr, d_f, which, s->stream) == cudaSuccess
+               ? LEDDS_OK
+               : LEDDS_ERR_CUDA;
+}
+
+int ledds_read_particles(ledds_sim_t s, double* state, int on_device) {
+    if (!s || !state) return LEDDS_ERR_INVALID_ARG;
+    int n = s->P.n;
+    if (n == 0) return LEDDS_OK;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpy2DAsync(state, sizeof(double) * n, s->P.st[0], sizeof(double) * s->P.cap,
+                                      sizeof(double) * n, 18, kind, s->stream);
+    if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
+}
+
+int ledds_read_forces(ledds_sim_t s, double* d_Fh, double* d_Mh, double* d_Fc, double* d_Mc) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    int n = s->P.n;
+    if (n == 0) return LEDDS_OK;
+    double* src[4] = {s->P.Fh, s->P.Mh, s->P.Fc, s->P.Mc};
+    double* dst[4] = {d_Fh, d_Mh, d_Fc, d_Mc};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        if (cudaMemcpy2DAsync(dst[q], sizeof(double) * n, src[q], sizeof(double) * s->P.cap,
+                              sizeof(double) * n, 3, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+            return LEDDS_ERR_CUDA;
+    }
+    return LEDDS_OK;
+}
+
+int ledds_read_pairs(ledds_sim_t s, uint64_t* d_keys, int cap, int* n_out) {
+    if (!s || !n_out || cap < 0 || (cap > 0 && !d_keys)) return LEDDS_ERR_INVALID_ARG;
+    *n_out = 0;
+    if (s->P.n == 0) return LEDDS_OK;
+    DemArgs A = dem_args(s);
+    if (launch_pairs(A, s->parity, s->pair_cnt, s->pair_off, s->scan_partial,
+                     (unsigned long long*)d_keys, cap, s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    uint32_t tot = 0;
+    if (cudaMemcpyAsync(&tot, s->pair_off + s->P.n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    *n_out = (int)tot;
+    return LEDDS_OK;
+}
+
+int ledds_read_cell_keys(ledds_sim_t s, uint32_t* d_keys, int32_t* d_sorted_ids, int grid_n[3]) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    int n = s->P.n;
+    if (grid_n)
+        for (int a = 0; a < 3; ++a) grid_n[a] = s->gn[a];
+    if (n == 0) return LEDDS_OK;
+    if (d_keys && cudaMemcpyAsync(d_keys, s->keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    if (d_sorted_ids &&
+        cudaMemcpyAsync(d_sorted_ids, s->sorted, sizeof(int) * n, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    return cudaStreamSynchronize(s->stream) == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
+}
+
+int ledds_voxelize(ledds_sim_t s, float* d_beta, int32_t* d_ids, int32_t* d_nsolid) {
+    if (!s || !d_beta || !d_ids || !d_nsolid) return LEDDS_ERR_INVALID_ARG;
+    if (!s->lattice) return LEDDS_ERR_STATE;
+    LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
+    if (cudaMemsetAsync(s->tile_count, 0, sizeof(int) * (size_t)s->ntiles, s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    if (launch_bin(a, s->P.n, s->tile_count, s->tile_ids, s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+    if (launch_voxelize(a, d_beta, d_ids, d_nsolid, s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+    return LEDDS_OK;
+}
+
+int ledds_set_profiling(ledds_sim_t s, int on) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    s->profiling = on != 0;
+    return LEDDS_OK;
+}
+
+int ledds_read_profile(ledds_sim_t s, double ms[5], long long* steps, long long* launches) {
+    if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (ms)
+        for (int q = 0; q < NSTAGE; ++q) ms[q] = s->prof_ms[q];
+    if (steps) *steps = s->prof_steps;
+    if (launches) *launches = s->prof_launches;
+    for (int q = 0; q < NSTAGE; ++q) s->prof_ms[q] = 0.0;
+    s->prof_steps = s->prof_launches = 0;
+    return LEDDS_OK;
+}
+
+// Checkpoint: a small header with the host-side state, then the whole workspace image.
+struct CkptHeader {
+    char magic[8];
+    int version;
+    ledds_dims d;
+    ledds_params p;
+    int n, parity;
+    long long steps;
+    double uw[3][2][3];
+    size_t ws_used;
+};
+
+int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes) {
+    if (!s || !bytes) return LEDDS_ERR_INVALID_ARG;
+    size_t used = layout(nullptr, &s->d, &s->p, nullptr) - 256;
+    size_t need = sizeof(CkptHeader) + used;
+    if (!h_buf) {
+        *bytes = need;
+        return LEDDS_OK;
+    }
+    if (*bytes < need) return LEDDS_ERR_INVALID_ARG;
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LEDDSCK1", 8);
+    hd.version = 1;
+    hd.d = s->d;
+    hd.p = s->p;
+    hd.n = s->P.n;
+    hd.parity = s->parity;
+    hd.steps = s->steps;
+    memcpy(hd.uw, s->uw, sizeof(hd.uw));
+    hd.ws_used = used;
+    memcpy(h_buf, &hd, sizeof(hd));
+    if (cudaMemcpyAsync((char*)h_buf + sizeof(hd), s->ws, used, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    *bytes = need;
+    return LEDDS_OK;
+}
+
+int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
+    if (!s || !h_buf || bytes < sizeof(CkptHeader)) return LEDDS_ERR_INVALID_ARG;
+    CkptHeader hd;
+    memcpy(&hd, h_buf, sizeof(hd));
+    size_t used = layout(nullptr, &s->d, &s->p, nullptr) - 256;
+    if (memcmp(hd.magic, "LEDDSCK1", 8) != 0 || hd.ws_used != used || bytes < sizeof(hd) + used ||
+        memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0 || hd.p.storage != s->p.storage)
+        return LEDDS_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(s->ws, (const char*)h_buf + sizeof(hd), used, cudaMemcpyHostToDevice, s->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return LEDDS_ERR_CUDA;
+    s->p = hd.p;
+    s->P.n = hd.n;
+    s->parity = hd.parity;
+    s->steps = hd.steps;
+    memcpy(s->uw, hd.uw, sizeof(hd.uw));
+    drop_graphs(s);
+    return LEDDS_OK;
+}
+
+}  // extern "C"

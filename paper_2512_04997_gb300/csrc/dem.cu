@@ -1,0 +1,844 @@
+// dem.cu -- DEM kernels of the coupled step (Secs. 2.1, 2.2, 3.2.1, 3.2.2; App. A).
+//
+// Compiled with -fmad=false: every FP64 expression rounds exactly as written, so the
+// contact predicate, the cell keys and the integrator evaluate the documented operation
+// order.
+//
+// Design: the cell list is rebuilt once per fluid step by a counting sort on the cell
+// key (one radix digit wide enough for the whole key). Each particle then gathers, from
+// the 27 neighbouring cells, every particle within the sum of bounding radii plus a
+// skin into a sorted candidate list; contact pairs during the substeps are a subset of
+// it while no particle moves more than skin/2 (checked, see skin_violation). A warp per
+// particle evaluates its candidate pairs, one per lane, and sums them by a fixed
+// butterfly; a pair is always evaluated in canonical order (lower id first), so both
+// members compute bit-identical forces and tangential histories and the per-particle
+// sums of Table 1 need neither atomics nor a second sort.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace ledds {
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double o[3]) {
+    double x = a[1] * b[2] - a[2] * b[1];
+    double y = a[2] * b[0] - a[0] * b[2];
+    double z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+}
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__device__ __forceinline__ double norm3(const double a[3]) { return sqrt(dot3(a, a)); }
+
+__device__ __forceinline__ double stv(const DemArgs& A, const double* st, int comp, int k) {
+    return st[(long long)comp * A.P.cap + k];
+}
+__device__ __forceinline__ void ld3(const DemArgs& A, const double* st, int comp, int k, double o[3]) {
+    for (int a = 0; a < 3; ++a) o[a] = st[(long long)(comp + a) * A.P.cap + k];
+}
+
+__device__ __forceinline__ double min_image(const DemArgs& A, int a, double d) {
+    if (A.per[a]) {
+        if (d > 0.5 * A.L[a]) d -= A.L[a];
+        else if (d < -0.5 * A.L[a]) d += A.L[a];
+    }
+    return d;
+}
+
+// ------------------------------------------------------------------------------------
+// Exclusive scan of uint32 (n <= 4096*4096): out[0..n], out[n] = total.
+// ------------------------------------------------------------------------------------
+constexpr int SCAN_THREADS = 1024, SCAN_ITEMS = 4, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t prefix = warp ? warp_sums[warp - 1] : 0u;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    uint32_t r = prefix + x - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_reduce(const uint32_t* in, int n, uint32_t* partial) {
+    long long base = (long long)blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        long long i = base + (long long)threadIdx.x * SCAN_ITEMS + q;
+        if (i < n) s += in[i];
+    }
+    uint32_t tot;
+    block_exclusive_scan(s, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_partials(uint32_t* partial, int nb) {
+    uint32_t v[SCAN_ITEMS], s = 0;
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        int i = threadIdx.x * SCAN_ITEMS + q;
+        v[q] = i < nb ? partial[i] : 0u;
+        s += v[q];
+    }
+    uint32_t run = block_exclusive_scan(s, nullptr);
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        int i = threadIdx.x * SCAN_ITEMS + q;
+        if (i < nb) partial[i] = run;
+        run += v[q];
+    }
+}
+
+__global__ void k_scan_apply(const uint32_t* in, int n, const uint32_t* partial, uint32_t* out) {
+    long long base = (long long)blockIdx.x * SCAN_TILE;
+    uint32_t v[SCAN_ITEMS], s = 0;
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        long long i = base + (long long)threadIdx.x * SCAN_ITEMS + q;
+        v[q] = i < n ? in[i] : 0u;
+        s += v[q];
+    }
+    uint32_t tot;
+    uint32_t run = block_exclusive_scan(s, &tot) + partial[blockIdx.x];
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        long long i = base + (long long)threadIdx.x * SCAN_ITEMS + q;
+        if (i < n) out[i] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
+}
+
+cudaError_t launch_scan(const uint32_t* in, int n, uint32_t* out, uint32_t* partial, cudaStream_t s) {
+    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb < 1) nb = 1;
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, s>>>(in, n, partial);
+    k_scan_partials<<<1, SCAN_THREADS, 0, s>>>(partial, nb);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, s>>>(in, n, partial, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Neighbour structure (Sec. 3.2.1): keys, counting sort, candidate lists
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cell_key(const DemArgs& A, const double r[3], int c[3]) {
+    for (int a = 0; a < 3; ++a) {
+        double q = floor((r[a] - A.lo[a]) / A.gh[a]);
+        int v = (int)q;
+        if (q < 0) v = 0;
+        if (q > A.gn[a] - 1) v = A.gn[a] - 1;
+        c[a] = v;
+    }
+    return (uint32_t)(c[0] + A.gn[0] * (c[1] + A.gn[1] * c[2]));
+}
+
+__global__ void k_keys(DemArgs A) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3];
+    ld3(A, A.P.st[0], SP, k, r);
+    int c[3];
+    uint32_t key = cell_key(A, r, c);
+    A.keys[k] = key;
+    A.rank[k] = (int)atomicAdd(&A.cell_count[key], 1u);
+    for (int a = 0; a < 3; ++a) A.P.pos_build[(long long)a * A.P.cap + k] = r[a];
+}
+
+__global__ void k_scatter(DemArgs A) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    A.sorted[A.cell_start[A.keys[k]] + A.rank[k]] = k;
+}
+
+// ids inside each cell in ascending order, so the sorted (key, id) list is unique
+__global__ void k_segsort(DemArgs A) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= A.G) return;
+    int b = (int)A.cell_start[c], e = (int)A.cell_start[c + 1];
+    for (int i = b + 1; i < e; ++i) {
+        int v = A.sorted[i];
+        int j = i - 1;
+        while (j >= b && A.sorted[j] > v) {
+            A.sorted[j + 1] = A.sorted[j];
+            --j;
+        }
+        A.sorted[j + 1] = v;
+    }
+}
+
+// Candidate list of particle i (ascending ids) and its tangential history carried over
+// from the previous list by a merge join (Sec. 3.2.2: look-up in the previous sorted list).
+__global__ void k_candidates(DemArgs A, int ob, int nbuf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.P.n) return;
+    const double* st = A.P.st[0];
+    double ri[3];
+    ld3(A, st, SP, i, ri);
+    const double bi = A.P.bound[i];
+    int c[3];
+    cell_key(A, ri, c);
+    int lst[MAX_CAND_CAP];
+    int cnt = 0, over = 0;
+    int visited[27];
+    int nvis = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    if (q[a] < 0 || q[a] >= A.gn[a]) {
+                        if (A.per[a]) q[a] = (q[a] + A.gn[a]) % A.gn[a];
+                        else ok = false;
+                    }
+                }
+                if (!ok) continue;
+                int h = q[0] + A.gn[0] * (q[1] + A.gn[1] * q[2]);
+                bool dup = false;
+                for (int m = 0; m < nvis; ++m) dup |= visited[m] == h;
+                if (dup) continue;
+                visited[nvis++] = h;
+                for (uint32_t s = A.cell_start[h]; s < A.cell_start[h + 1]; ++s) {
+                    int j = A.sorted[s];
+                    if (j == i) continue;
+                    double d[3];
+                    for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
+                    double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    double lim = bi + A.P.bound[j] + A.skin;
+                    if (d2 < lim * lim) {
+                        if (cnt < A.ccap) lst[cnt++] = j;
+                        else over = 1;
+                    }
+                }
+            }
+    if (over) atomicAdd(&A.status->cand_overflow, 1);
+    for (int m = 1; m < cnt; ++m) {
+        int v = lst[m], j = m - 1;
+        while (j >= 0 && lst[j] > v) {
+            lst[j + 1] = lst[j];
+            --j;
+        }
+        lst[j + 1] = v;
+    }
+    const int* oc = A.cand[ob] + (long long)i * A.ccap;
+    const double* oh = A.hist[ob] + (long long)i * A.ccap * 3;
+    int* nc = A.cand[nbuf] + (long long)i * A.ccap;
+    double* nh = A.hist[nbuf] + (long long)i * A.ccap * 3;
+    int nold = A.ncand[ob][i], p = 0;
+    for (int m = 0; m < cnt; ++m) {
+        int j = lst[m];
+        while (p < nold && oc[p] < j) ++p;
+        bool found = p < nold && oc[p] == j;
+        nc[m] = j;
+        for (int a = 0; a < 3; ++a) nh[3 * m + a] = found ? oh[3 * p + a] : 0.0;
+    }
+    A.ncand[nbuf][i] = cnt;
+}
+
+// ------------------------------------------------------------------------------------
+// Contact geometry
+// ------------------------------------------------------------------------------------
+struct Geo {
+    double delta;
+    double en[3];              // unit normal from b to a
+    double rca[3], rcb[3];     // arms from the centres to the contact point
+    double Ra, Rb;             // radii (spheres) / curvature radii (ellipsoids)
+    bool sphere;
+};
+
+__device__ __forceinline__ void tri_of(const DemArgs& A, const double* st, int k, double R[9]) {
+    for (int m = 0; m < 9; ++m) R[m] = st[(long long)(ST + m) * A.P.cap + k];
+}
+__device__ __forceinline__ void to_body(const double R[9], const double v[3], double o[3]) {
+    for (int m = 0; m < 3; ++m) o[m] = R[3 * m] * v[0] + R[3 * m + 1] * v[1] + R[3 * m + 2] * v[2];
+}
+__device__ __forceinline__ void to_world(const double R[9], const double b[3], double o[3]) {
+    for (int a = 0; a < 3; ++a) o[a] = b[0] * R[a] + b[1] * R[3 + a] + b[2] * R[6 + a];
+}
+
+// normal, curvature radius of Eq. (local-curvature), osculating centre at surface point p
+__device__ void osc(const double r[3], const double R[9], const double s[3], const double p[3],
+                    double* rho, double o[3]) {
+    double rel[3] = {p[0] - r[0], p[1] - r[1], p[2] - r[2]};
+    double pb[3], nb[3], n[3];
+    to_body(R, rel, pb);
+    for (int m = 0; m < 3; ++m) nb[m] = pb[m] / (s[m] * s[m]);
+    double nn = norm3(nb);
+    for (int m = 0; m < 3; ++m) nb[m] /= nn;
+    to_world(R, nb, n);
+    double a = s[0], b = s[1], c = s[2];
+    *rho = b * c * pb[0] * pb[0] / (a * a * a) + a * c * pb[1] * pb[1] / (b * b * b) +
+           a * b * pb[2] * pb[2] / (c * c * c);
+    for (int m = 0; m < 3; ++m) o[m] = p[m] - (*rho) * n[m];
+}
+
+// far intersection (largest parameter) of the line origin + t dir with the ellipsoid
+__device__ bool hit(const double r[3], const double R[9], const double s[3], const double org[3],
+                    const double dir[3], double* t) {
+    double rel[3] = {org[0] - r[0], org[1] - r[1], org[2] - r[2]};
+    double q[3], w[3];
+    to_body(R, rel, q);
+    to_body(R, dir, w);
+    double Aq = 0, Bq = 0, Cq = -1.0;
+    for (int m = 0; m < 3; ++m) {
+        Aq += (w[m] / s[m]) * (w[m] / s[m]);
+        Bq += q[m] * w[m] / (s[m] * s[m]);
+        Cq += (q[m] / s[m]) * (q[m] / s[m]);
+    }
+    double disc = Bq * Bq - Aq * Cq;
+    if (disc < 0.0 || Aq <= 0.0) return false;
+    *t = (-Bq + sqrt(disc)) / Aq;
+    return true;
+}
+
+// Common-normal iteration with osculating spheres (Sec. 2.1): start on the centre line;
+// move each point half way towards the intersection of its ellipsoid with the line
+// joining the osculating centres and project it back along the ray from its centre;
+// stop when both undamped steps fall below tol * smallest semi-axis.
+__device__ bool ell_geo(const DemArgs& A, const double ra[3], const double Ra_[9],
+                        const double sa[3], const double rb[3], const double Rb_[9],
+                        const double sb[3], Geo& g) {
+    double d[3] = {rb[0] - ra[0], rb[1] - ra[1], rb[2] - ra[2]};
+    double dn = norm3(d);
+    if (dn <= 0.0) return false;
+    double u[3] = {d[0] / dn, d[1] / dn, d[2] / dn};
+    double mu[3] = {-u[0], -u[1], -u[2]};
+    double t, pa[3], pb[3];
+    if (!hit(ra, Ra_, sa, ra, u, &t)) return false;
+    for (int a = 0; a < 3; ++a) pa[a] = ra[a] + t * u[a];
+    if (!hit(rb, Rb_, sb, rb, mu, &t)) return false;
+    for (int a = 0; a < 3; ++a) pb[a] = rb[a] + t * mu[a];
+    double smin = sa[0];
+    for (int m = 0; m < 3; ++m) {
+        smin = fmin(smin, sa[m]);
+        smin = fmin(smin, sb[m]);
+    }
+    bool conv = false;
+    double oa[3], ob[3], rhoa, rhob;
+    for (int it = 0; it < A.ell_max_iter; ++it) {
+        osc(ra, Ra_, sa, pa, &rhoa, oa);
+        osc(rb, Rb_, sb, pb, &rhob, ob);
+        double w[3] = {ob[0] - oa[0], ob[1] - oa[1], ob[2] - oa[2]};
+        double wn = norm3(w);
+        if (wn <= 0.0) break;
+        for (int a = 0; a < 3; ++a) w[a] /= wn;
+        double mw[3] = {-w[0], -w[1], -w[2]};
+        double ta, tb;
+        if (!hit(ra, Ra_, sa, oa, w, &ta)) break;
+        if (!hit(rb, Rb_, sb, ob, mw, &tb)) break;
+        double da[3], db[3];
+        for (int a = 0; a < 3; ++a) {
+            da[a] = (oa[a] + ta * w[a]) - pa[a];
+            db[a] = (ob[a] + tb * mw[a]) - pb[a];
+        }
+        double mv = fmax(norm3(da), norm3(db));
+        double qa[3], qb[3];
+        for (int a = 0; a < 3; ++a) {
+            qa[a] = (pa[a] + 0.5 * da[a]) - ra[a];
+            qb[a] = (pb[a] + 0.5 * db[a]) - rb[a];
+        }
+        double qan = norm3(qa), qbn = norm3(qb);
+        for (int a = 0; a < 3; ++a) {
+            qa[a] /= qan;
+            qb[a] /= qbn;
+        }
+        if (!hit(ra, Ra_, sa, ra, qa, &ta)) break;
+        if (!hit(rb, Rb_, sb, rb, qb, &tb)) break;
+        for (int a = 0; a < 3; ++a) {
+            pa[a] = ra[a] + ta * qa[a];
+            pb[a] = rb[a] + tb * qb[a];
+        }
+        if (mv < A.ell_tol * smin) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) atomicAdd(&A.status->ell_nonconverged, 1);
+    osc(ra, Ra_, sa, pa, &rhoa, oa);
+    osc(rb, Rb_, sb, pb, &rhob, ob);
+    double gv[3] = {oa[0] - ob[0], oa[1] - ob[1], oa[2] - ob[2]};
+    double gn = norm3(gv);
+    g.delta = rhoa + rhob - gn;
+    for (int a = 0; a < 3; ++a) {
+        g.en[a] = gv[a] / gn;
+        double cp = 0.5 * (pa[a] + pb[a]);
+        g.rca[a] = cp - ra[a];
+        g.rcb[a] = cp - rb[a];
+    }
+    g.Ra = rhoa;
+    g.Rb = rhob;
+    g.sphere = false;
+    return true;
+}
+
+// Geometry of the canonical pair (a < b) from state buffer st; false if no contact.
+__device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& g) {
+    double dd[3];
+    for (int c = 0; c < 3; ++c) dd[c] = min_image(A, c, stv(A, st, SP + c, a) - stv(A, st, SP + c, b));
+    const int sha = A.P.shape[a], shb = A.P.shape[b];
+    if (sha == LEDDS_SPHERE && shb == LEDDS_SPHERE) {
+        double d2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+        double dist = sqrt(d2);
+        double Ra = A.P.radius[a], Rb = A.P.radius[b];
+        g.delta = (Ra + Rb) - dist;
+        if (!(g.delta > 0.0)) return false;
+        for (int c = 0; c < 3; ++c) {
+            g.en[c] = dd[c] / dist;
+            g.rca[c] = -Ra * g.en[c];
+            g.rcb[c] = Rb * g.en[c];
+        }
+        g.Ra = Ra;
+        g.Rb = Rb;
+        g.sphere = true;
+        return true;
+    }
+    double dist = norm3(dd);
+    if (!((A.P.bound[a] + A.P.bound[b]) - dist > 0.0)) return false;
+    double ra[3], rb[3], Ra_[9], Rb_[9], sa[3], sb[3];
+    for (int c = 0; c < 3; ++c) {
+        ra[c] = stv(A, st, SP + c, a);
+        rb[c] = ra[c] - dd[c];
+        sa[c] = A.P.semi[(long long)c * A.P.cap + a];
+        sb[c] = A.P.semi[(long long)c * A.P.cap + b];
+    }
+    tri_of(A, st, a, Ra_);
+    tri_of(A, st, b, Rb_);
+    if (!ell_geo(A, ra, Ra_, sa, rb, Rb_, sb, g)) return false;
+    return g.delta > 0.0;
+}
+
+// Particle-wall geometry, face = 2*axis + side: a static plane with inward normal at the
+// halfway position, surface velocity u_w; infinite mass and radius.
+__device__ bool wall_geo(const DemArgs& A, const double* st, int k, int face, Geo& g) {
+    int a = face >> 1, side = face & 1;
+    double nrm[3] = {0.0, 0.0, 0.0};
+    nrm[a] = side == 0 ? 1.0 : -1.0;
+    double r[3];
+    ld3(A, st, SP, k, r);
+    if (A.P.shape[k] == LEDDS_SPHERE) {
+        double R = A.P.radius[k];
+        double dist = side == 0 ? r[a] - A.lo[a] : A.hi[a] - r[a];
+        g.delta = R - dist;
+        if (!(g.delta > 0.0)) return false;
+        for (int c = 0; c < 3; ++c) {
+            g.en[c] = nrm[c];
+            g.rca[c] = -R * nrm[c];
+            g.rcb[c] = 0.0;
+        }
+        g.Ra = R;
+        g.sphere = true;
+        return true;
+    }
+    double R9[9], s[3];
+    tri_of(A, st, k, R9);
+    for (int c = 0; c < 3; ++c) s[c] = A.P.semi[(long long)c * A.P.cap + k];
+    double nb[3], pb[3], pw[3], p[3];
+    to_body(R9, nrm, nb);
+    double den = sqrt(s[0] * s[0] * nb[0] * nb[0] + s[1] * s[1] * nb[1] * nb[1] + s[2] * s[2] * nb[2] * nb[2]);
+    for (int m = 0; m < 3; ++m) pb[m] = -s[m] * s[m] * nb[m] / den;
+    to_world(R9, pb, pw);
+    for (int c = 0; c < 3; ++c) p[c] = r[c] + pw[c];
+    double sd = side == 0 ? p[a] - A.lo[a] : A.hi[a] - p[a];
+    g.delta = -sd;
+    if (!(g.delta > 0.0)) return false;
+    double rho, o[3];
+    osc(r, R9, s, p, &rho, o);
+    for (int c = 0; c < 3; ++c) {
+        g.en[c] = nrm[c];
+        g.rca[c] = (p[c] + 0.5 * g.delta * nrm[c]) - r[c];
+        g.rcb[c] = 0.0;
+    }
+    g.Ra = rho;
+    g.sphere = false;
+    return true;
+}
+
+// ------------------------------------------------------------------------------------
+// Spring-dashpot force on a (Eqs. spring_dashpot_easy, fnScal, trangential-history,
+// coulombCoeff; App. A for the Hertz coefficients). h: tangential displacement of the
+// canonical pair, updated in place. Ft receives the tangential part.
+// ------------------------------------------------------------------------------------
+__device__ void spring_dashpot(const DemArgs& A, const Geo& g, double Rstar, double mstar,
+                               const double va[3], const double wa[3], const double vb[3],
+                               const double wb[3], double h[3], double F[3], double Ft[3]) {
+    double kn, kt, gn, gt;
+    if (A.law == LEDDS_LAW_LINEAR) {
+        kn = A.k_n;
+        kt = A.k_t;
+        gn = -2.0 * A.beta * sqrt(kn * mstar);
+        gt = -2.0 * A.beta * sqrt(kt * mstar);
+    } else {
+        double sq = sqrt(Rstar * g.delta);
+        kn = 4.0 / 3.0 * A.Ystar * sq;
+        kt = 8.0 * A.Gstar * sq;
+        double Sn = 2.0 * A.Ystar * sq;
+        double St = 8.0 * A.Gstar * sq;
+        gn = -2.0 * sqrt(5.0 / 6.0) * A.beta * sqrt(Sn * mstar);
+        gt = -2.0 * sqrt(5.0 / 6.0) * A.beta * sqrt(St * mstar);
+    }
+    double ca[3], cb[3], vrel[3];
+    cross3(wa, g.rca, ca);
+    cross3(wb, g.rcb, cb);
+    for (int c = 0; c < 3; ++c) vrel[c] = (va[c] + ca[c]) - (vb[c] + cb[c]);
+    double vn = dot3(vrel, g.en);
+    double vt[3];
+    for (int c = 0; c < 3; ++c) vt[c] = vrel[c] - vn * g.en[c];
+    double fn = kn * g.delta - gn * vn;
+    double hn = dot3(h, g.en);
+    double hp[3];
+    for (int c = 0; c < 3; ++c) hp[c] = h[c] - hn * g.en[c];
+    double lh = norm3(h), lp = norm3(hp);
+    if (lp > 0.0)
+        for (int c = 0; c < 3; ++c) hp[c] *= lh / lp;
+    for (int c = 0; c < 3; ++c) h[c] = hp[c] + vt[c] * A.dt;
+    for (int c = 0; c < 3; ++c) Ft[c] = -kt * h[c] - gt * vt[c];
+    double lft = norm3(Ft), lfn = fabs(fn);
+    if (lft > A.mu * lfn) {
+        double sc = lft > 0.0 ? A.mu * lfn / lft : 0.0;
+        for (int c = 0; c < 3; ++c) Ft[c] *= sc;
+        if (kt > 0.0)
+            for (int c = 0; c < 3; ++c) h[c] = -(Ft[c] + gt * vt[c]) / kt;
+    }
+    for (int c = 0; c < 3; ++c) F[c] = fn * g.en[c] + Ft[c];
+}
+
+// Contribution of candidate slot m of particle i (state buffer st): the canonical pair
+// force is applied with the sign of i's membership; the slot's tangential history is
+// updated (and reset when the pair is not in contact).
+__device__ void pair_contrib(const DemArgs& A, const double* st, int cb, int i, int m, double F[3],
+                             double M[3]) {
+    const int j = A.cand[cb][(long long)i * A.ccap + m];
+    double* hl = A.hist[cb] + ((long long)i * A.ccap + m) * 3;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    Geo g;
+    if (!pair_geo(A, st, a, b, g)) {
+        hl[0] = hl[1] = hl[2] = 0.0;
+        return;
+    }
+    double va[3], wa[3], vb[3], wb[3], h[3], Fp[3], Ft[3];
+    ld3(A, st, SV, a, va);
+    ld3(A, st, SW, a, wa);
+    ld3(A, st, SV, b, vb);
+    ld3(A, st, SW, b, wb);
+    for (int c = 0; c < 3; ++c) h[c] = hl[c];
+    double Rstar = 1.0 / (1.0 / g.Ra + 1.0 / g.Rb);
+    double mstar = 1.0 / (1.0 / A.P.mass[a] + 1.0 / A.P.mass[b]);
+    spring_dashpot(A, g, Rstar, mstar, va, wa, vb, wb, h, Fp, Ft);
+    for (int c = 0; c < 3; ++c) hl[c] = h[c];
+    double Mi[3];
+    if (g.sphere) {
+        // Sec. 2.1: M = -R e_n x F_t for both members
+        double mr[3];
+        cross3(g.en, Ft, mr);
+        double Ri = i == a ? g.Ra : g.Rb;
+        for (int c = 0; c < 3; ++c) Mi[c] = -Ri * mr[c];
+    } else if (i == a) {
+        cross3(g.rca, Fp, Mi);  // Eq. (torque)
+    } else {
+        double mF[3] = {-Fp[0], -Fp[1], -Fp[2]};
+        cross3(g.rcb, mF, Mi);
+    }
+    double sgn = i == a ? 1.0 : -1.0;
+    for (int c = 0; c < 3; ++c) {
+        F[c] += sgn * Fp[c];
+        M[c] += Mi[c];
+    }
+}
+
+// Contribution of wall face `face` on particle i (history per particle and face).
+__device__ void wall_contrib(const DemArgs& A, const double* st, int i, int face, double F[3], double M[3]) {
+    const int ax = face >> 1;
+    double* wh = A.whist + ((long long)i * 6 + face) * 3;
+    Geo g;
+    if (A.per[ax] || !wall_geo(A, st, i, face, g)) {
+        wh[0] = wh[1] = wh[2] = 0.0;
+        return;
+    }
+    double vi[3], wi[3];
+    ld3(A, st, SV, i, vi);
+    ld3(A, st, SW, i, wi);
+    const double* uw = A.uw[ax][face & 1];
+    double zero[3] = {0.0, 0.0, 0.0}, Fw[3], Ft[3], Mw[3];
+    spring_dashpot(A, g, g.Ra, A.P.mass[i], vi, wi, uw, zero, wh, Fw, Ft);
+    if (g.sphere) {
+        double mr[3];
+        cross3(g.en, Ft, mr);
+        for (int c = 0; c < 3; ++c) Mw[c] = -g.Ra * mr[c];
+    } else {
+        cross3(g.rca, Fw, Mw);
+    }
+    for (int c = 0; c < 3; ++c) {
+        F[c] += Fw[c];
+        M[c] += Mw[c];
+    }
+}
+
+// Warp-cooperative contact sum of particle i: lane l evaluates candidate slots l, l+32
+// and wall face l (l < 6); a fixed butterfly sums the lanes (deterministic order).
+__device__ void contact_sum_warp(const DemArgs& A, const double* st, int cb, int i, double F[3],
+                                 double M[3]) {
+    const int lane = threadIdx.x & 31;
+    for (int c = 0; c < 3; ++c) F[c] = M[c] = 0.0;
+    const int nc = A.ncand[cb][i];
+    for (int m = lane; m < nc; m += 32) pair_contrib(A, st, cb, i, m, F, M);
+    if (lane < 6) wall_contrib(A, st, i, lane, F, M);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            F[c] += __shfl_xor_sync(0xffffffffu, F[c], off);
+            M[c] += __shfl_xor_sync(0xffffffffu, M[c], off);
+        }
+}
+
+// ------------------------------------------------------------------------------------
+// Integration (Sec. 2.2)
+// ------------------------------------------------------------------------------------
+// Predictor: Eq. (advance-r) and the triad update with w(t), then Gram-Schmidt;
+// positions wrapped on periodic axes; displacement since the last rebuild checked.
+__device__ void predict(const DemArgs& A, int k, double r[3], const double v[3], const double acc[3],
+                        const double w[3], double d[9]) {
+    const double dt = A.dt;
+    for (int a = 0; a < 3; ++a) r[a] = r[a] + dt * v[a] + (dt * dt / 2.0) * acc[a];
+    for (int a = 0; a < 3; ++a)
+        if (A.per[a]) r[a] = r[a] - A.L[a] * floor((r[a] - A.lo[a]) / A.L[a]);
+    for (int m = 0; m < 3; ++m) {
+        double* dm = d + 3 * m;
+        double wxd[3], ds[3], mid[3], wxm[3];
+        cross3(w, dm, wxd);
+        for (int a = 0; a < 3; ++a) ds[a] = dm[a] + dt * wxd[a];
+        for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (dm[a] + ds[a]);
+        cross3(w, mid, wxm);
+        for (int a = 0; a < 3; ++a) dm[a] = dm[a] + dt * wxm[a];
+    }
+    double* d1 = d;
+    double* d2 = d + 3;
+    double n1 = norm3(d1);
+    for (int a = 0; a < 3; ++a) d1[a] /= n1;
+    double p = dot3(d2, d1);
+    for (int a = 0; a < 3; ++a) d2[a] -= p * d1[a];
+    double n2 = norm3(d2);
+    for (int a = 0; a < 3; ++a) d2[a] /= n2;
+    cross3(d1, d2, d + 6);
+    double disp2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = min_image(A, a, r[a] - A.P.pos_build[(long long)a * A.P.cap + k]);
+        disp2 += e * e;
+    }
+    if (disp2 > 0.25 * A.skin * A.skin) atomicAdd(&A.status->skin_violation, 1);
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(r[a]);
+    if (bad) atomicAdd(&A.status->nan_detected, 1);
+}
+
+// Corrector: a' = F/m + g (1 - rho_f/rho_p); alpha' = R^T I^-1 [R M - (R w) x (I R w)]
+// (Eq. advance-omega, body-frame Euler equations), v += dt/2 (a + a'), w += dt/2 (alpha + alpha').
+__device__ void correct(const DemArgs& A, int k, const double F[3], const double M[3], const double d[9],
+                        double v[3], double w[3]) {
+    const double dt = A.dt;
+    double an[3], wb[3], Mb[3], Iw[3], gyr[3], ab[3], al[3];
+    const double m = A.P.mass[k], gf = A.P.gfac[k];
+    for (int a = 0; a < 3; ++a) an[a] = F[a] / m + A.gravity[a] * gf;
+    for (int q = 0; q < 3; ++q) {
+        wb[q] = dot3(d + 3 * q, w);
+        Mb[q] = dot3(d + 3 * q, M);
+    }
+    double I[3];
+    for (int q = 0; q < 3; ++q) I[q] = A.P.inertia[(long long)q * A.P.cap + k];
+    for (int q = 0; q < 3; ++q) Iw[q] = I[q] * wb[q];
+    cross3(wb, Iw, gyr);
+    for (int q = 0; q < 3; ++q) ab[q] = (Mb[q] - gyr[q]) / I[q];
+    for (int a = 0; a < 3; ++a) al[a] = ab[0] * d[0 + a] + ab[1] * d[3 + a] + ab[2] * d[6 + a];
+    for (int a = 0; a < 3; ++a) {
+        long long o = (long long)a * A.P.cap + k;
+        v[a] += dt / 2.0 * (A.P.acc[o] + an[a]);
+        w[a] += dt / 2.0 * (A.P.alpha[o] + al[a]);
+        A.P.acc[o] = an[a];
+        A.P.alpha[o] = al[a];
+    }
+}
+
+__device__ __forceinline__ void load_state(const DemArgs& A, const double* st, int k, double r[3],
+                                           double v[3], double w[3], double d[9]) {
+    ld3(A, st, SP, k, r);
+    ld3(A, st, SV, k, v);
+    ld3(A, st, SW, k, w);
+    tri_of(A, st, k, d);
+}
+__device__ __forceinline__ void store_state(const DemArgs& A, double* st, int k, const double r[3],
+                                            const double v[3], const double w[3], const double d[9]) {
+    for (int a = 0; a < 3; ++a) {
+        st[(long long)(SP + a) * A.P.cap + k] = r[a];
+        st[(long long)(SV + a) * A.P.cap + k] = v[a];
+        st[(long long)(SW + a) * A.P.cap + k] = w[a];
+    }
+    for (int m = 0; m < 9; ++m) st[(long long)(ST + m) * A.P.cap + k] = d[m];
+}
+
+// First substep predictor, in place on buffer 0.
+__global__ void k_predict_first(DemArgs A) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], acc[3];
+    load_state(A, A.P.st[0], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+    predict(A, k, r, v, acc, w, d);
+    for (int a = 0; a < 3; ++a) A.P.st[0][(long long)(SP + a) * A.P.cap + k] = r[a];
+    for (int m = 0; m < 9; ++m) A.P.st[0][(long long)(ST + m) * A.P.cap + k] = d[m];
+}
+
+// Contact forces of a substep, one warp per particle, from buffer `in` (Table 1 "Compute
+// DEM forces" and "Reduce DEM forces"): stored in Fc, Mc.
+__global__ void k_contacts(DemArgs A, int in, int cb) {
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (k >= A.P.n) return;  // uniform across the warp
+    double F[3], M[3];
+    contact_sum_warp(A, A.P.st[in], cb, k, F, M);
+    if ((threadIdx.x & 31) != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        A.P.Fc[(long long)a * A.P.cap + k] = F[a];
+        A.P.Mc[(long long)a * A.P.cap + k] = M[a];
+    }
+}
+
+// End of a substep for one particle (thread per particle): the corrector with the held
+// hydrodynamic force, then the predictor of the next substep, from buffer `in` to `out`.
+__global__ void k_integrate(DemArgs A, int in, int out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], Ft[3], Mt[3], acc[3];
+    load_state(A, A.P.st[in], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) {
+        long long o = (long long)a * A.P.cap + k;
+        Ft[a] = A.P.Fc[o] + A.P.Fhp[o];
+        Mt[a] = A.P.Mc[o] + A.P.Mhp[o];
+    }
+    correct(A, k, Ft, Mt, d, v, w);
+    for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+    predict(A, k, r, v, acc, w, d);
+    store_state(A, A.P.st[out], k, r, v, w, d);
+}
+
+// Velocity update of the last substep (flowchart: after the fluid forces are reduced):
+// corrector with the fresh hydrodynamic force (or none for DEM-only), result in buffer 0;
+// the hydrodynamic force is held for the next step's substeps.
+__global__ void k_final(DemArgs A, int in, int use_hydro) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], F[3], M[3];
+    load_state(A, A.P.st[in], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) {
+        long long o = (long long)a * A.P.cap + k;
+        double fh = use_hydro ? A.P.Fh[o] : 0.0, mh = use_hydro ? A.P.Mh[o] : 0.0;
+        F[a] = A.P.Fc[o] + fh;
+        M[a] = A.P.Mc[o] + mh;
+        A.P.Fhp[o] = fh;
+        A.P.Mhp[o] = mh;
+    }
+    correct(A, k, F, M, d, v, w);
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(v[a]) || !isfinite(w[a]);
+    if (bad) atomicAdd(&A.status->nan_detected, 1);
+    store_state(A, A.P.st[0], k, r, v, w, d);
+}
+
+// Contact set at buffer 0 positions: counts of partners j > i, then keys (i << 32 | j).
+__global__ void k_pair_count(DemArgs A, int cb, uint32_t* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.P.n) return;
+    const int nc = A.ncand[cb][i];
+    const int* cl = A.cand[cb] + (long long)i * A.ccap;
+    uint32_t c = 0;
+    for (int m = 0; m < nc; ++m) {
+        int j = cl[m];
+        if (j <= i) continue;
+        Geo g;
+        c += pair_geo(A, A.P.st[0], i, j, g) ? 1u : 0u;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_pair_emit(DemArgs A, int cb, const uint32_t* off, unsigned long long* keys, int cap) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.P.n) return;
+    const int nc = A.ncand[cb][i];
+    const int* cl = A.cand[cb] + (long long)i * A.ccap;
+    uint32_t o = off[i];
+    for (int m = 0; m < nc; ++m) {
+        int j = cl[m];
+        if (j <= i) continue;
+        Geo g;
+        if (pair_geo(A, A.P.st[0], i, j, g)) {
+            if ((int)o < cap) keys[o] = ((unsigned long long)i << 32) | (unsigned)j;
+            ++o;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------
+static inline unsigned nblk(int n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_rebuild(const DemArgs& A, int ob, int nb, uint32_t* scan_partial, cudaStream_t s,
+                           int* launches) {
+    int n = A.P.n;
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(A.cell_count, 0, sizeof(uint32_t) * (A.G + 1), s);
+    if (e != cudaSuccess) return e;
+    k_keys<<<nblk(n, 128), 128, 0, s>>>(A);
+    e = launch_scan(A.cell_count, A.G, A.cell_start, scan_partial, s);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<nblk(n, 128), 128, 0, s>>>(A);
+    k_segsort<<<nblk(A.G, 128), 128, 0, s>>>(A);
+    k_candidates<<<nblk(n, 64), 64, 0, s>>>(A, ob, nb);
+    *launches += 7;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
+    if (A.P.n <= 0) return cudaSuccess;
+    k_predict_first<<<nblk(A.P.n, 128), 128, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+// do_step = 1: contact forces then corrector + next predictor (in -> out);
+// do_step = 0: contact forces only.
+cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int, cudaStream_t s) {
+    if (A.P.n <= 0) return cudaSuccess;
+    k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
+    if (do_step) k_integrate<<<nblk(A.P.n, 64), 64, 0, s>>>(A, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final(const DemArgs& A, int in, int use_hydro, cudaStream_t s) {
+    if (A.P.n <= 0) return cudaSuccess;
+    k_final<<<nblk(A.P.n, 128), 128, 0, s>>>(A, in, use_hydro);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(const DemArgs& A, int cb, uint32_t* cnt, uint32_t* off, uint32_t* partial,
+                         unsigned long long* keys, int cap, cudaStream_t s) {
+    if (A.P.n <= 0) return cudaSuccess;
+    k_pair_count<<<nblk(A.P.n, 64), 64, 0, s>>>(A, cb, cnt);
+    cudaError_t e = launch_scan(cnt, A.P.n, off, partial, s);
+    if (e != cudaSuccess) return e;
+    k_pair_emit<<<nblk(A.P.n, 64), 64, 0, s>>>(A, cb, off, keys, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace ledds

@@ -1,0 +1,178 @@
+// internal.cuh -- shared device definitions of the LEDDS GB300 library.
+//
+// D3Q19 lattice tables (Sec. 2.3), storage formats of the populations, kernel argument
+// structs and the launch helpers used by lbm.cu, dem.cu and api.cu.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ledds.h"
+
+namespace ledds {
+
+// ------------------------------------------------------------------------------------
+// D3Q19 velocity set in the order documented in ledds.h: rest; +x,-x,+y,-y,+z,-z; then
+// the 12 edge velocities, each followed by its opposite. Written as constexpr functions
+// so that fully unrolled loops fold every table entry into an immediate.
+// ------------------------------------------------------------------------------------
+__host__ __device__ constexpr int CX(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13)   ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int CY(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17)   ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18)  ? -1
+                                                                  : 0;
+}
+__host__ __device__ constexpr int CZ(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18)  ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1
+                                                                   : 0;
+}
+__host__ __device__ constexpr float TW(int i) {
+    return i == 0 ? 1.0f / 3.0f : (i <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+__host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// ------------------------------------------------------------------------------------
+// Population storage: g_i = f_i - t_i in FP32, FP16 or BF16; 16-bit formats keep
+// g_i * 2^s (s = storage_scale_log2) to stay clear of FP16 subnormals.
+// ------------------------------------------------------------------------------------
+template <int STORE>
+struct Store;
+
+template <>
+struct Store<LEDDS_STORE_F32> {
+    using T = float;
+    static __device__ __forceinline__ float load(const T* p, float) { return *p; }
+    static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
+};
+template <>
+struct Store<LEDDS_STORE_F16> {
+    using T = __half;
+    static __device__ __forceinline__ float load(const T* p, float inv) {
+        return __half2float(*p) * inv;
+    }
+    static __device__ __forceinline__ void store(T* p, float v, float scale) {
+        __stcs(reinterpret_cast<unsigned short*>(p),
+               __half_as_ushort(__float2half_rn(v * scale)));
+    }
+};
+template <>
+struct Store<LEDDS_STORE_BF16> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float load(const T* p, float inv) {
+        return __bfloat162float(*p) * inv;
+    }
+    static __device__ __forceinline__ void store(T* p, float v, float scale) {
+        __stcs(reinterpret_cast<unsigned short*>(p),
+               __bfloat16_as_ushort(__float2bfloat16_rn(v * scale)));
+    }
+};
+
+inline size_t storage_bytes(int store) { return store == LEDDS_STORE_F32 ? 4 : 2; }
+
+// Lattice tile handled by one CTA of the PSM kernel: 32 x 8 nodes per plane (one warp
+// per x-row), TILE_Z planes.
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+constexpr int TILE_Z = 16;
+constexpr int MAX_TILE_CAP = 64;
+constexpr int MAX_CAND_CAP = 64;
+
+// Device status counters (one struct in the workspace).
+struct DevStatus {
+    unsigned long long steps;
+    int tile_overflow;
+    int cand_overflow;
+    int solids_overflow;
+    int skin_violation;
+    int ell_nonconverged;
+    int nan_detected;
+    int pad[2];
+};
+
+// Particle arrays in the workspace. State buffers hold [18][cap] doubles: pos xyz,
+// vel xyz, omega xyz, triad d1 d2 d3.
+struct DevParticles {
+    int n, cap;
+    double* st[2];
+    double *acc, *alpha;          // [3][cap]
+    double *Fc, *Mc;              // contact force/torque of the last substep
+    double *Fh, *Mh;              // hydrodynamic force/torque of the last fluid step
+    double *Fhp, *Mhp;            // held hydrodynamic force/torque for substeps
+    double* pos_build;            // positions at the last neighbour rebuild
+    double *radius, *semi, *bound, *mass, *inertia, *gfac;  // semi, inertia: [3][cap]
+    int* shape;
+};
+
+// Offsets of the state buffer components.
+constexpr int SP = 0, SV = 3, SW = 6, ST = 9;
+
+struct LbmArgs {
+    int nx, ny, nz;
+    long long N;
+    int per[3];
+    float uw[3][2][3];
+    float tau, omega;
+    float F[3];
+    int has_force;
+    float guo_pref;               // 1 - 1/(2 tau)
+    float scale, inv_scale;
+    const void* pop_in;
+    void* pop_out;
+    int pN[19];                   // i * N: start of plane i (19 N < 2^31 is required)
+    int off[19];                  // c_x + nx c_y + nx ny c_z: pull offset of direction i
+    unsigned off_odd;             // bit i: off[i] is odd (16-bit word selection)
+    // tile lists
+    int ntx, nty, ntz, tile_cap;
+    const int* tile_count;
+    const int* tile_ids;
+    // particles (the state buffer the fluid step sees)
+    const double* st;
+    int pcap;
+    const double *radius, *semi, *bound;
+    const int* shape;
+    double *Fh, *Mh;
+    int voxel, subdiv_n;
+    float Rc;
+    DevStatus* status;
+};
+
+struct DemArgs {
+    DevParticles P;
+    // domain
+    double lo[3], hi[3], L[3];
+    int per[3];
+    double uw[3][2][3];
+    // grid
+    int gn[3];
+    double gh[3];
+    int G;
+    // parameters
+    double dt;
+    double gravity[3];
+    int law;
+    double k_n, k_t, beta, Ystar, Gstar, mu;
+    double skin;
+    int ell_max_iter;
+    double ell_tol;
+    // lists
+    int ccap;
+    uint32_t* keys;
+    int* rank;
+    int* sorted;
+    uint32_t* cell_count;
+    uint32_t* cell_start;
+    int* cand[2];
+    int* ncand[2];
+    double* hist[2];
+    double* whist;
+    DevStatus* status;
+};
+
+}  // namespace ledds
