@@ -263,7 +263,7 @@ def test_dem_forces_and_trajectories(oracle):
 def test_dem_ellipsoids_hertz(oracle):
     """Ellipsoid contacts (common-normal iteration) with the Hertz law and walls."""
     g = W.rng(604)
-    n = 200
+    n = 500
     box = (30.0, 30.0, 30.0)
     w = W.Workload(name="ell", box_lo=(0, 0, 0), box_hi=box, periodic=(1, 0, 0))
     w.params = W.base_params(law="hertz", young=5.0, poisson=0.3, restitution=0.8, friction=0.3,
@@ -279,8 +279,8 @@ def test_dem_ellipsoids_hertz(oracle):
     w.triad = W.quaternion_to_triad(W.random_quaternions(g, n))
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
-    o.step(60)
-    s.step(60)
+    o.step(80)
+    s.step(80)
     pairs_o = o.contacts()
     pairs_g = s.pairs()
     assert len(pairs_o) > 5
