@@ -211,6 +211,30 @@ int ledds_read_profile(ledds_sim_t s, double ms[5], long long* steps, long long*
 int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes);
 int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes);
 
+/* Cell keys and (key, id)-sorted particle ids of the DEM grid, computed without any
+ * device allocation. The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory themselves, such as code running under a memory
+ * pool that owns the whole device, or a latency-critical path where an allocation could
+ * block or fail. It takes no simulation object and no workspace; its scratch (per-cell
+ * counts and starts, scan partials, per-particle ranks) lives in a fixed array inside
+ * the library that every GPU loading the library keeps until the process exits.
+ *   d_pos      particle positions on the device, [3][n] doubles (x row, y row, z row)
+ *   box_lo/hi  domain; the grid has floor(L/h) cells per axis (at least one), of width
+ *              L/cells, exactly as a simulation with dem_h = h builds it
+ *   d_keys     output, n cell keys k_x + n_x (k_y + n_y k_z) (device)
+ *   d_sorted_ids output, n ids sorted by (key, id) (device)
+ *   grid_n     may be NULL; receives the cells per axis
+ *   stream     cudaStream_t the work is enqueued on (asynchronous)
+ * Limits: at most 262144 grid cells and 262144 particles; larger inputs return
+ * LEDDS_ERR_CAPACITY before any device work. Every call reuses the same scratch, so
+ * calls that may overlap on the GPU (different streams or devices' concurrent use of
+ * one stream order aside) race and must be serialised by the caller. The first call on
+ * each device looks up the scratch address (cudaGetSymbolAddress); make that first call
+ * before any stream capture. Errors: INVALID_ARG, CAPACITY, CUDA. */
+int ledds_cell_list_noalloc(const double* d_pos, int n, const double box_lo[3],
+                            const double box_hi[3], double h, uint32_t* d_keys,
+                            int32_t* d_sorted_ids, int grid_n[3], void* stream);
+
 const char* ledds_strerror(int code);
 int ledds_version(void);
 

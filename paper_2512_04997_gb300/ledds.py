@@ -82,6 +82,8 @@ _SIGS = {
     "ledds_read_profile": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "ledds_save": (C.c_int, [VP, VP, C.POINTER(C.c_size_t)]),
     "ledds_load": (C.c_int, [VP, VP, C.c_size_t]),
+    "ledds_cell_list_noalloc": (C.c_int, [VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.c_double, VP, VP, C.POINTER(C.c_int), VP]),
 }
 
 _lib = None
