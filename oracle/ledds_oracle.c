@@ -435,6 +435,7 @@ static cell_solids* compute_solids(const or_sim* s) {
         const double* r = s->pos + 3 * k;
         double e = s->bound[k] + 1.0;
         int lo[3], hi[3];
+        if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) continue;
         for (int a = 0; a < 3; ++a) {
             lo[a] = (int)ceil(r[a] - e);
             hi[a] = (int)floor(r[a] + e);
@@ -694,9 +695,10 @@ static unsigned cell_key(const or_sim* s, const double r[3]) {
     int k[3];
     for (int a = 0; a < 3; ++a) {
         double q = floor((r[a] - s->lo[a]) / s->gh[a]);
-        int v = (int)q;
-        if (q < 0) v = 0;
-        if (q > s->gn[a] - 1) v = s->gn[a] - 1;
+        int v;
+        if (!(q >= 0.0)) v = 0;            /* also catches a non-finite position */
+        else if (q > s->gn[a] - 1) v = s->gn[a] - 1;
+        else v = (int)q;
         k[a] = v;
     }
     return (unsigned)(k[0] + s->gn[0] * (k[1] + s->gn[1] * k[2]));

@@ -63,6 +63,7 @@ struct ledds_sim_s {
     double* hist[2] = {nullptr, nullptr};
     double* whist = nullptr;
     DevStatus* status = nullptr;
+    double max_bound = 0.0;  // largest bounding radius of the current particles
     // state
     double uw[3][2][3];
     int parity = 0;          // pop[parity], cand[parity] hold the current data
@@ -280,6 +281,16 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
         a.off[i] = CX(i) + s->d.nx * (CY(i) + s->d.ny * CZ(i));
         if (a.off[i] & 1) a.off_odd |= 1u << i;
     }
+    a.nx_even = (s->d.nx % 2) == 0;
+    {
+        // Cached centres are minimum-imaged against the tile origin; a node offset can
+        // still need a wrap only if the box is narrower than the reach of a particle
+        // from a tile (both sides) plus the tile itself.
+        const int n3[3] = {s->d.nx, s->d.ny, s->d.nz};
+        const int T[3] = {TILE_X, TILE_Y, TILE_Z};
+        for (int q = 0; q < 3; ++q)
+            a.mi[q] = s->d.periodic[q] && (double)n3[q] < 2.0 * (s->max_bound + 2.0 + T[q]) + 2.0;
+    }
     a.ntx = s->ntx;
     a.nty = s->nty;
     a.ntz = s->ntz;
@@ -297,6 +308,7 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     a.voxel = s->p.voxel;
     a.subdiv_n = s->p.subdiv_n;
     a.Rc = (float)cbrt(3.0 / (4.0 * kPi));
+    a.inv2Rc = (float)(1.0 / (2.0 * cbrt(3.0 / (4.0 * kPi))));
     a.status = s->status;
     return a;
 }
@@ -645,6 +657,7 @@ int ledds_set_particles(ledds_sim_t s, int n, const ledds_particle* h) {
             if (s->d.periodic[a] && 2.0 * reach + 2.0 >= n3[a]) return LEDDS_ERR_INVALID_ARG;
     }
     s->P.n = n;
+    s->max_bound = bmax;
     drop_graphs(s);
     if (n > 0) {
         int rc;

@@ -138,9 +138,11 @@ cudaError_t launch_scan(const uint32_t* in, int n, uint32_t* out, uint32_t* part
 __device__ __forceinline__ uint32_t cell_key(const DemArgs& A, const double r[3], int c[3]) {
     for (int a = 0; a < 3; ++a) {
         double q = floor((r[a] - A.lo[a]) / A.gh[a]);
-        int v = (int)q;
-        if (q < 0) v = 0;
-        if (q > A.gn[a] - 1) v = A.gn[a] - 1;
+        // clamp before converting: a non-finite position lands in cell 0, never out of range
+        int v;
+        if (!(q >= 0.0)) v = 0;
+        else if (q > A.gn[a] - 1) v = A.gn[a] - 1;
+        else v = (int)q;
         c[a] = v;
     }
     return (uint32_t)(c[0] + A.gn[0] * (c[1] + A.gn[1] * c[2]));

@@ -49,6 +49,7 @@ template <>
 struct Store<LEDDS_STORE_F32> {
     using T = float;
     static __device__ __forceinline__ float load(const T* p, float) { return *p; }
+    static __device__ __forceinline__ float from_bits(unsigned short, float) { return 0.f; }
     static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
 };
 template <>
@@ -56,6 +57,9 @@ struct Store<LEDDS_STORE_F16> {
     using T = __half;
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __half2float(*p) * inv;
+    }
+    static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
+        return __half2float(__ushort_as_half(h)) * inv;
     }
     static __device__ __forceinline__ void store(T* p, float v, float scale) {
         __stcs(reinterpret_cast<unsigned short*>(p),
@@ -67,6 +71,9 @@ struct Store<LEDDS_STORE_BF16> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __bfloat162float(*p) * inv;
+    }
+    static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
+        return __bfloat162float(__ushort_as_bfloat16(h)) * inv;
     }
     static __device__ __forceinline__ void store(T* p, float v, float scale) {
         __stcs(reinterpret_cast<unsigned short*>(p),
@@ -128,6 +135,8 @@ struct LbmArgs {
     int pN[19];                   // i * N: start of plane i (19 N < 2^31 is required)
     int off[19];                  // c_x + nx c_y + nx ny c_z: pull offset of direction i
     unsigned off_odd;             // bit i: off[i] is odd (16-bit word selection)
+    int nx_even;                  // nx even: a pulled index has the parity of x - c_x
+    int mi[3];                    // per axis: node-particle offsets may need a periodic wrap
     // tile lists
     int ntx, nty, ntz, tile_cap;
     const int* tile_count;
@@ -139,7 +148,7 @@ struct LbmArgs {
     const int* shape;
     double *Fh, *Mh;
     int voxel, subdiv_n;
-    float Rc;
+    float Rc, inv2Rc;
     DevStatus* status;
 };
 

@@ -261,6 +261,8 @@ __device__ __forceinline__ float reach_of(const LbmArgs& a, int shape, double R,
 }
 
 __device__ __forceinline__ int axis_tiles(double r, float reach, int n, int per, int T, int* out) {
+    // a particle far outside the lattice (or not finite) reaches no tile
+    if (!(r > -2.0 * n && r < 3.0 * n)) return 0;
     int lo = (int)ceil(r - (double)reach);
     int hi = (int)floor(r + (double)reach);
     int cnt = 0, last = -1;
@@ -289,6 +291,10 @@ __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
     double r[3] = {a.st[(SP + 0) * a.pcap + k], a.st[(SP + 1) * a.pcap + k],
                    a.st[(SP + 2) * a.pcap + k]};
     float reach = reach_of(a, a.shape[k], a.radius[k], a.bound[k]);
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) {
+        atomicAdd(&a.status->nan_detected, 1);
+        return;
+    }
     int tl[3][16], tc[3];
     tc[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
     tc[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
@@ -306,19 +312,20 @@ __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
 // ------------------------------------------------------------------------------------
 // Per-tile particle cache and solid fractions (Sec. 2.4)
 // ------------------------------------------------------------------------------------
+// Per-tile particle cache. The hot fields are packed in float4 records so one 128-bit
+// shared load (a broadcast: every lane reads the same entry) fetches a whole record.
 struct TileCache {
-    float r[3][MAX_TILE_CAP];     // centre minus tile origin (FP32, minimum image)
-    double p[3][MAX_TILE_CAP];    // centre (FP64) for the exact subdivision path
-    float R[MAX_TILE_CAP];        // radius (spheres) / bounding radius (ellipsoids)
-    float R2[MAX_TILE_CAP];       // fl32(R*R) of the subdivision predicate
-    float reach2[MAX_TILE_CAP];
-    float v[3][MAX_TILE_CAP];
-    float w[3][MAX_TILE_CAP];
-    float m[9][MAX_TILE_CAP];     // ellipsoid rows fl32(d_j / semi_j)
-    int pid[MAX_TILE_CAP];
+    float4 pos[MAX_TILE_CAP];     // centre minus tile origin (FP32, minimum image), radius
+    float4 vel[MAX_TILE_CAP];     // velocity, squared reach of the solid fraction
+    float4 spin[MAX_TILE_CAP];    // angular velocity, particle id (bits)
     int shape[MAX_TILE_CAP];
+    float R2[MAX_TILE_CAP];       // fl32(R*R) of the subdivision predicate
+    double p[3][MAX_TILE_CAP];    // centre (FP64) for the exact subdivision path
+    float m[9][MAX_TILE_CAP];     // ellipsoid rows fl32(d_j / semi_j)
     double acc[6][MAX_TILE_CAP];  // force and torque sums of this tile
 };
+
+__device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
 
 __device__ __forceinline__ double min_image_d(double d, int per, double L) {
     if (per) {
@@ -341,21 +348,22 @@ __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int cnt, in
     const double Ls[3] = {(double)a.nx, (double)a.ny, (double)a.nz};
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
         int k = a.tile_ids[(long long)tile * a.tile_cap + e];
-        tc.pid[e] = k;
         int sh = a.shape[k];
         tc.shape[e] = sh;
+        float r[3], v[3], w[3];
         for (int c = 0; c < 3; ++c) {
             double pc = a.st[(SP + c) * a.pcap + k];
             tc.p[c][e] = pc;
-            tc.r[c][e] = (float)min_image_d(pc - org[c], a.per[c], Ls[c]);
-            tc.v[c][e] = (float)a.st[(SV + c) * a.pcap + k];
-            tc.w[c][e] = (float)a.st[(SW + c) * a.pcap + k];
+            r[c] = (float)min_image_d(pc - org[c], a.per[c], Ls[c]);
+            v[c] = (float)a.st[(SV + c) * a.pcap + k];
+            w[c] = (float)a.st[(SW + c) * a.pcap + k];
         }
         double R = sh == LEDDS_SPHERE ? a.radius[k] : a.bound[k];
-        tc.R[e] = (float)R;
         tc.R2[e] = __double2float_rn(R * R);
         float reach = reach_of(a, sh, a.radius[k], a.bound[k]);
-        tc.reach2[e] = reach * reach;
+        tc.pos[e] = make_float4(r[0], r[1], r[2], (float)R);
+        tc.vel[e] = make_float4(v[0], v[1], v[2], reach * reach);
+        tc.spin[e] = make_float4(w[0], w[1], w[2], __int_as_float(k));
         if (sh == LEDDS_ELLIPSOID) {
             for (int j = 0; j < 3; ++j)
                 for (int c = 0; c < 3; ++c)
@@ -427,22 +435,22 @@ __device__ __noinline__ float beta_subdiv_exact(const LbmArgs& a, const TileCach
 
 // Solid fraction of cached particle e at node (x,y,z); (dx,dy,dz) = node - centre (FP32).
 __device__ __forceinline__ float beta_of(const LbmArgs& a, const TileCache& tc, int e, int x, int y,
-                                         int z, float dx, float dy, float dz) {
+                                         int z, float dx, float dy, float dz, float R) {
     const int sh = tc.shape[e];
     const float d2 = dx * dx + dy * dy + dz * dz;
     if (sh == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) {
-        // Eq. (naiveSolidFrac)
-        float dsc = tc.R[e] + a.Rc - sqrtf(d2);
-        return fminf(fmaxf(dsc / (2.0f * a.Rc), 0.0f), 1.0f);
+        // Eq. (naiveSolidFrac): (R + R_c - d) / (2 R_c), clamped
+        float dsc = R + a.Rc - sqrtf(d2);
+        return fminf(fmaxf(dsc * a.inv2Rc, 0.0f), 1.0f);
     }
     const int n = a.subdiv_n;
     const float h = (float)(n - 1) / (float)(2 * n);  // largest sample offset
     const float hd = 1.7320508f * h;                  // sample-to-node distance bound
     // exact early-outs (margins far above FP32 rounding): no sample can be inside ...
-    const float far = tc.R[e] + hd + 1e-3f;
+    const float far = R + hd + 1e-3f;
     if (d2 > far * far) return 0.0f;
     if (sh == LEDDS_SPHERE) {
-        const float nearr = tc.R[e] - hd - 1e-3f;
+        const float nearr = R - hd - 1e-3f;
         if (nearr > 0.0f && d2 < nearr * nearr) return 1.0f;  // ... or every sample is
     } else {
         // every corner of the sample box strictly inside (convexity) => all samples are
@@ -471,9 +479,10 @@ __device__ __forceinline__ unsigned long long row_mask(const LbmArgs& a, const T
         int e = base + lane;
         bool hit = false;
         if (e < cnt) {
-            float dy = min_image_f((float)ly - tc.r[1][e], a.per[1], (float)a.ny);
-            float dz = min_image_f((float)lz - tc.r[2][e], a.per[2], (float)a.nz);
-            hit = dy * dy + dz * dz < tc.reach2[e];
+            const float4 ps = tc.pos[e];
+            float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+            float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+            hit = dy * dy + dz * dz < tc.vel[e].w;
         }
         unsigned b = __ballot_sync(FULL, hit);
         mask |= (unsigned long long)b << base;
@@ -490,7 +499,7 @@ struct Two {
 };
 
 __device__ __forceinline__ bool ranks_before(const TileCache& tc, float b, int e, float bw, int ew) {
-    return b > bw || (b == bw && tc.pid[e] < tc.pid[ew]);
+    return b > bw || (b == bw && tc_pid(tc, e) < tc_pid(tc, ew));
 }
 
 __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
@@ -503,10 +512,11 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& t
     while (mask) {
         const int e = __ffsll((long long)mask) - 1;
         mask &= mask - 1;
-        float dx = min_image_f((float)lx - tc.r[0][e], a.per[0], (float)a.nx);
-        float dy = min_image_f((float)ly - tc.r[1][e], a.per[1], (float)a.ny);
-        float dz = min_image_f((float)lz - tc.r[2][e], a.per[2], (float)a.nz);
-        float b = beta_of(a, tc, e, x, y, z, dx, dy, dz);
+        const float4 ps = tc.pos[e];
+        float dx = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
+        float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+        float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+        float b = beta_of(a, tc, e, x, y, z, dx, dy, dz, ps.w);
         if (!(b > 0.0f)) continue;
         t.total++;
         if (t.ns == 0) {
@@ -527,30 +537,39 @@ struct SolidAt {
 
 __device__ __forceinline__ void solid_at(const LbmArgs& a, const TileCache& tc, int e, float b, int lx,
                                          int ly, int lz, float tau, SolidAt& q) {
-    q.ax = min_image_f((float)lx - tc.r[0][e], a.per[0], (float)a.nx);
-    q.ay = min_image_f((float)ly - tc.r[1][e], a.per[1], (float)a.ny);
-    q.az = min_image_f((float)lz - tc.r[2][e], a.per[2], (float)a.nz);
-    q.B = b * (tau - 0.5f) / ((1.0f - b) + (tau - 0.5f));
-    q.ux = tc.v[0][e] + (tc.w[1][e] * q.az - tc.w[2][e] * q.ay);
-    q.uy = tc.v[1][e] + (tc.w[2][e] * q.ax - tc.w[0][e] * q.az);
-    q.uz = tc.v[2][e] + (tc.w[0][e] * q.ay - tc.w[1][e] * q.ax);
+    const float4 ps = tc.pos[e], vs = tc.vel[e], ws = tc.spin[e];
+    q.ax = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
+    q.ay = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+    q.az = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+    q.B = __fdividef(b * (tau - 0.5f), (1.0f - b) + (tau - 0.5f));
+    q.ux = vs.x + (ws.y * q.az - ws.z * q.ay);
+    q.uy = vs.y + (ws.z * q.ax - ws.x * q.az);
+    q.uz = vs.z + (ws.x * q.ay - ws.y * q.ax);
     q.usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
     q.sx = q.sy = q.sz = 0.f;
 }
 
-// Warp reduction of one solid slot's force and torque into the tile accumulators:
-// one butterfly per distinct cached particle present in the warp.
-__device__ __forceinline__ void reduce_slot(TileCache& tc, int key, const SolidAt& q) {
+// Force and torque of one node-solid pair, Eqs. (forceSF), (torqueSF):
+// F = -B sum_i Omega^s_i c_i, M = arm x F. The direction sum has the closed form
+// sum_i Omega^s_i c_i = F_fluid - rho (u - u_k) (momentum exchange: sum_i neq_i c_i =
+// -F_fluid/2 and sum_i (geq_i(rho,u) - geq_i(rho,u_k)) c_i = rho (u - u_k)), so
+// F = B (rho (u - u_k) - F_fluid).
+__device__ __forceinline__ void solid_force(const SolidAt& q, float rho, float dux, float duy, float duz,
+                                            const LbmArgs& a, float v[6]) {
+    const float fx = a.has_force ? a.F[0] : 0.f, fy = a.has_force ? a.F[1] : 0.f;
+    const float fz = a.has_force ? a.F[2] : 0.f;
+    v[0] = q.B * (rho * dux - fx);
+    v[1] = q.B * (rho * duy - fy);
+    v[2] = q.B * (rho * duz - fz);
+    v[3] = q.ay * v[2] - q.az * v[1];
+    v[4] = q.az * v[0] - q.ax * v[2];
+    v[5] = q.ax * v[1] - q.ay * v[0];
+}
+
+// Warp-aggregated addition of per-lane (key, 6 values) into the tile accumulators: one
+// butterfly per distinct key present in the warp (lanes with key < 0 take no part).
+__device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
     const int lane = threadIdx.x & 31;
-    float val[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (key >= 0) {
-        val[0] = -q.B * q.sx;
-        val[1] = -q.B * q.sy;
-        val[2] = -q.B * q.sz;
-        val[3] = q.ay * val[2] - q.az * val[1];
-        val[4] = q.az * val[0] - q.ax * val[2];
-        val[5] = q.ax * val[1] - q.ay * val[0];
-    }
     unsigned pending = __ballot_sync(FULL, key >= 0);
     while (pending) {
         const int leader = __ffs(pending) - 1;
@@ -577,8 +596,16 @@ __device__ __forceinline__ void reduce_slot(TileCache& tc, int key, const SolidA
 // needs no CTA barrier, and two planes of loads stay in flight per thread whatever the
 // occupancy.
 // ------------------------------------------------------------------------------------
+// Resident CTAs per SM the PSM kernel is compiled for (register budget) and depth of its
+// asynchronous pull pipeline (planes in flight + 1); tuned on GB300.
+#ifndef LEDDS_PSM_MINB
+#define LEDDS_PSM_MINB 3
+#endif
+#ifndef LEDDS_PSM_STAGES
+#define LEDDS_PSM_STAGES 3
+#endif
 constexpr int PSM_THREADS = TILE_X * TILE_Y;
-constexpr int PSM_STAGES = 3;
+constexpr int PSM_STAGES = LEDDS_PSM_STAGES;
 
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src, bool pred) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
@@ -639,69 +666,181 @@ __device__ __forceinline__ int fast_elem(const LbmArgs& a, const Plan& p) {
     return a.pN[I] + src;
 }
 
+// Runtime-indexed copies of the velocity set for the out-of-line wall path.
+__constant__ int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ int kCY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__constant__ int kCZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+__constant__ float kTW[19] = {1.f / 3, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18,
+                              1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36,
+                              1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
+
+// General pull of direction i at node (x,y,z): element index, plus the moving-wall term
+// when the link crosses a wall (halfway bounce-back reads the node's own opposite value).
+__device__ __forceinline__ int general_elem(const LbmArgs& a, int i, int x, int y, int z, float* wterm) {
+    const int cx = kCX[i], cy = kCY[i], cz = kCZ[i];
+    int sx = x - cx, sy = y - cy, sz = z - cz;
+    bool wx = false, wy = false, wz = false;
+    if (sx < 0 || sx >= a.nx) { if (a.per[0]) sx = sx < 0 ? sx + a.nx : sx - a.nx; else wx = true; }
+    if (sy < 0 || sy >= a.ny) { if (a.per[1]) sy = sy < 0 ? sy + a.ny : sy - a.ny; else wy = true; }
+    if (sz < 0 || sz >= a.nz) { if (a.per[2]) sz = sz < 0 ? sz + a.nz : sz - a.nz; else wz = true; }
+    const int cell = x + a.nx * (y + a.ny * z);
+    *wterm = 0.f;
+    if (wx || wy || wz) {
+        const int ax = wz ? 2 : (wy ? 1 : 0);
+        const int cc = ax == 2 ? cz : (ax == 1 ? cy : cx);
+        const int side = cc == 1 ? 0 : 1;
+        float u0, u1, u2;
+        // constant-index selection (no dynamic indexing of the parameter block)
+        if (ax == 2) { u0 = side ? a.uw[2][1][0] : a.uw[2][0][0]; u1 = side ? a.uw[2][1][1] : a.uw[2][0][1]; u2 = side ? a.uw[2][1][2] : a.uw[2][0][2]; }
+        else if (ax == 1) { u0 = side ? a.uw[1][1][0] : a.uw[1][0][0]; u1 = side ? a.uw[1][1][1] : a.uw[1][0][1]; u2 = side ? a.uw[1][1][2] : a.uw[1][0][2]; }
+        else { u0 = side ? a.uw[0][1][0] : a.uw[0][0][0]; u1 = side ? a.uw[0][1][1] : a.uw[0][0][1]; u2 = side ? a.uw[0][1][2] : a.uw[0][0][2]; }
+        *wterm = 6.0f * kTW[i] * ((float)cx * u0 + (float)cy * u1 + (float)cz * u2);
+        const int o = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+        return a.pN[o] + cell;
+    }
+    return a.pN[i] + sx + a.nx * (sy + a.ny * sz);
+}
+
+template <class SS>
+__device__ __noinline__ void issue_general(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
+                                           uint32_t* slot) {
+    for (int i = 0; i < 19; ++i) {
+        float wt;
+        int elem = general_elem(a, i, x, y, z, &wt);
+        uintptr_t q = reinterpret_cast<uintptr_t>(pin + elem);
+        if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
+        cp_async4(slot + i * PSM_THREADS, reinterpret_cast<const void*>(q), true);
+    }
+}
+
+template <class SS>
+__device__ __noinline__ void read_general(const LbmArgs& a, int x, int y, int z, const uint32_t* slot, float* g) {
+    for (int i = 0; i < 19; ++i) {
+        float wt;
+        int elem = general_elem(a, i, x, y, z, &wt);
+        const uint32_t w = slot[i * PSM_THREADS];
+        float v;
+        if (sizeof(typename SS::T) == 4) {
+            v = __uint_as_float(w);
+        } else {
+            v = SS::from_bits((elem & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), a.inv_scale);
+        }
+        g[i] = v + wt;
+    }
+}
+
 template <class SS, int I>
 struct IssueAll {
     static __device__ __forceinline__ void run(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
-                                               uint32_t* slot, bool pred) {
-        int elem = 0;
-        if (pred) {
-            if (!p.wall) {
-                elem = fast_elem<I>(a, p);
-            } else {
-                // general path (rare): halfway bounce-back where the link crosses a wall
-                const int nxy = a.nx * a.ny;
-                const int z = p.cell / nxy, y = (p.cell - z * nxy) / a.nx, x = p.cell - z * nxy - y * a.nx;
-                Nbr nb;
-                make_nbr(a, x, y, z, nb);
-                bool wall, wx, wy, wz;
-                elem = (int)pull_addr<I>(a, nb, wall, wx, wy, wz);
-            }
-        }
-        uintptr_t q = reinterpret_cast<uintptr_t>(pin + elem);
+                                               uint32_t* slot) {
+        uintptr_t q = reinterpret_cast<uintptr_t>(pin + fast_elem<I>(a, p));
         if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
-        cp_async4(slot + I * PSM_THREADS, reinterpret_cast<const void*>(q), pred);
-        IssueAll<SS, I + 1>::run(a, pin, p, slot, pred);
+        cp_async4(slot + I * PSM_THREADS, reinterpret_cast<const void*>(q), true);
+        IssueAll<SS, I + 1>::run(a, pin, p, slot);
     }
 };
 template <class SS>
 struct IssueAll<SS, 19> {
-    static __device__ __forceinline__ void run(const LbmArgs&, const typename SS::T*, const Plan&, uint32_t*,
-                                               bool) {}
+    static __device__ __forceinline__ void run(const LbmArgs&, const typename SS::T*, const Plan&, uint32_t*) {}
 };
+
+// Issue the 19 pulls of node (x,y,z) into its shared-memory slots (nothing if !pred).
+template <class SS>
+__device__ __forceinline__ void issue_node(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
+                                           bool pred, uint32_t* slot) {
+    if (!pred) return;
+    Plan p;
+    make_plan(a, x, y, z, p);
+    if (!p.wall) IssueAll<SS, 0>::run(a, pin, p, slot);
+    else issue_general<SS>(a, pin, x, y, z, slot);
+}
 
 template <class SS>
 __device__ __forceinline__ float decode(uint32_t w, int odd, float inv) {
     if (sizeof(typename SS::T) == 4) return __uint_as_float(w);
-    unsigned short h = odd ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu);
-    typename SS::T v;
-    memcpy(&v, &h, 2);
-    return SS::load(&v, inv);
+    return SS::from_bits(odd ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), inv);
 }
 
 template <class SS, int I>
 struct ReadAll {
-    static __device__ __forceinline__ void run(const LbmArgs& a, const Plan& p, const Nbr* nb,
-                                               const uint32_t* slot, float* g) {
+    static __device__ __forceinline__ void run(const LbmArgs& a, const Plan& p, const uint32_t* slot, float* g) {
         const uint32_t w = slot[I * PSM_THREADS];
-        if (!nb) {
-            // parity of pN[I] + cell - off[I] (+ even wrap corrections for even sizes is
-            // not assumed: use the exact element index)
-            const int odd = sizeof(typename SS::T) == 2 ? (fast_elem<I>(a, p) & 1) : 0;
-            g[I] = decode<SS>(w, odd, a.inv_scale);
-        } else {
-            bool wall, wx, wy, wz;
-            long long addr = pull_addr<I>(a, *nb, wall, wx, wy, wz);
-            float v = decode<SS>(w, (int)(addr & 1), a.inv_scale);
-            if (wall) v += wall_term<I>(a.uw, wx, wy, wz);
-            g[I] = v;
-        }
-        ReadAll<SS, I + 1>::run(a, p, nb, slot, g);
+        // 16-bit storage: which half of the copied word holds the value. With nx even every
+        // offset and wrap correction except c_x is even, so the parity is that of x - c_x.
+        int odd = 0;
+        if (sizeof(typename SS::T) == 2) odd = a.nx_even ? ((p.cell ^ CX(I)) & 1) : (fast_elem<I>(a, p) & 1);
+        g[I] = decode<SS>(w, odd, a.inv_scale);
+        ReadAll<SS, I + 1>::run(a, p, slot, g);
     }
 };
 template <class SS>
 struct ReadAll<SS, 19> {
-    static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const Nbr*, const uint32_t*,
-                                               float*) {}
+    static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const uint32_t*, float*) {}
+};
+
+// Collision and store of the direction pair (I, I+1) (c_{I+1} = -c_I). On entry g holds
+// the pulled populations of the pair; the symmetric and antisymmetric parts of the
+// equilibrium and of geq(rho,u) - geq(rho,u_k) are shared by the two directions:
+//   geq_{I,I+1} = t (base + 4.5 rho cu^2 +/- 3 rho cu)
+//   Omega^s_I = neq_{I+1} - neq_I - t rho ( 3 c.(u-u_k) + 4.5 (cu^2 - cuk^2) - 1.5 (u^2 - u_k^2))
+//   Omega^s_{I+1} = neq_I - neq_{I+1} - t rho (-3 c.(u-u_k) + 4.5 (cu^2 - cuk^2) - 1.5 (...))
+// The force sum over the directions is not accumulated here: see solid_force.
+template <class SS, int I>
+struct CollidePairs {
+    static __device__ __forceinline__ void run(float* g, float rho, float ux, float uy, float uz, float base,
+                                               const LbmArgs& a, float Fu, float force_w, float keep, int ns,
+                                               SolidAt& q0, SolidAt& q1, float d0x, float d0y, float d0z,
+                                               float d0s, float d1x, float d1y, float d1z, float d1s,
+                                               typename SS::T* dst, bool valid) {
+        constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+        constexpr float t = TW(I);
+        const float cu = (float)cx * ux + (float)cy * uy + (float)cz * uz;
+        const float cu2 = cu * cu;
+        const float sym = base + 4.5f * rho * cu2;
+        const float asym = 3.0f * rho * cu;
+        const float n0 = g[I] - t * (sym + asym);       // neq_I
+        const float n1 = g[I + 1] - t * (sym - asym);   // neq_{I+1}
+        float o0 = t * (sym + asym) + keep * n0;
+        float o1 = t * (sym - asym) + keep * n1;
+        if (a.has_force) {
+            const float cF = (float)cx * a.F[0] + (float)cy * a.F[1] + (float)cz * a.F[2];
+            // Guo term t [3 (c.F - u.F) + 9 (c.u)(c.F)]: c -> -c flips only 3 c.F
+            const float fs = force_w * t * (-3.0f * Fu + 9.0f * cu * cF);
+            const float fa = force_w * t * 3.0f * cF;
+            o0 += fs + fa;
+            o1 += fs - fa;
+        }
+        if (ns > 0) {
+            const float cuk = cu - ((float)cx * d0x + (float)cy * d0y + (float)cz * d0z);
+            const float dsym = t * rho * (4.5f * (cu2 - cuk * cuk) - 1.5f * d0s);
+            const float dasym = t * rho * 3.0f * (cu - cuk);
+            const float w0 = n1 - n0 - (dsym + dasym);
+            const float w1 = n0 - n1 - (dsym - dasym);
+            o0 += q0.B * w0;
+            o1 += q0.B * w1;
+        }
+        if (ns > 1) {
+            const float cuk = cu - ((float)cx * d1x + (float)cy * d1y + (float)cz * d1z);
+            const float dsym = t * rho * (4.5f * (cu2 - cuk * cuk) - 1.5f * d1s);
+            const float dasym = t * rho * 3.0f * (cu - cuk);
+            const float w0 = n1 - n0 - (dsym + dasym);
+            const float w1 = n0 - n1 - (dsym - dasym);
+            o0 += q1.B * w0;
+            o1 += q1.B * w1;
+        }
+        if (valid) {
+            SS::store(dst + a.pN[I], o0, a.scale);
+            SS::store(dst + a.pN[I + 1], o1, a.scale);
+        }
+        CollidePairs<SS, I + 2>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, ns, q0, q1, d0x, d0y,
+                                     d0z, d0s, d1x, d1y, d1z, d1s, dst, valid);
+    }
+};
+template <class SS>
+struct CollidePairs<SS, 19> {
+    static __device__ __forceinline__ void run(float*, float, float, float, float, float, const LbmArgs&, float,
+                                               float, float, int, SolidAt&, SolidAt&, float, float, float,
+                                               float, float, float, float, float, typename SS::T*, bool) {}
 };
 
 // ------------------------------------------------------------------------------------
@@ -713,7 +852,7 @@ struct ReadAll<SS, 19> {
 //   Omega^s_{i,k} = neq_ibar - neq_i - (geq_i(rho,u) - geq_i(rho,u_k)).
 // ------------------------------------------------------------------------------------
 template <int STORE>
-__global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
+__global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmArgs a) {
     using SS = Store<STORE>;
     using T = typename SS::T;
     const T* pin = (const T*)a.pop_in;
@@ -732,10 +871,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
 #pragma unroll
     for (int q = 0; q < PSM_STAGES - 1; ++q) {
         const int z = z0 + q;
-        const bool pred = valid_xy && z < a.nz;
-        Plan pl;
-        if (pred) make_plan(a, x, y, z, pl);
-        IssueAll<SS, 0>::run(a, pin, pl, stage + (q * 19) * PSM_THREADS + tid, pred);
+        issue_node<SS>(a, pin, x, y, z, valid_xy && z < a.nz, stage + (q * 19) * PSM_THREADS + tid);
         cp_async_commit();
     }
     const int cnt = min(a.tile_count[tile], a.tile_cap);
@@ -743,14 +879,14 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
     __syncthreads();
 
     const float tau = a.tau, omega = a.omega;
+    int hkey = -1;                                   // solid held in the running sum
+    float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // its force and torque so far
     for (int iz = 0; iz < TILE_Z; ++iz) {
         {   // keep PSM_STAGES - 1 planes ahead in flight
             const int q = iz + PSM_STAGES - 1;
             const int z = z0 + q;
-            const bool pred = q < TILE_Z && valid_xy && z < a.nz;
-            Plan pl;
-            if (pred) make_plan(a, x, y, z, pl);
-            IssueAll<SS, 0>::run(a, pin, pl, stage + ((q % PSM_STAGES) * 19) * PSM_THREADS + tid, pred);
+            issue_node<SS>(a, pin, x, y, z, q < TILE_Z && valid_xy && z < a.nz,
+                           stage + ((q % PSM_STAGES) * 19) * PSM_THREADS + tid);
             cp_async_commit();
         }
         cp_async_wait<PSM_STAGES - 1>();
@@ -765,13 +901,8 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
         if (valid) {
             make_plan(a, x, y, z, pl);
             const uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
-            if (!pl.wall) {
-                ReadAll<SS, 0>::run(a, pl, nullptr, slot, g);
-            } else {
-                Nbr nb;
-                make_nbr(a, x, y, z, nb);
-                ReadAll<SS, 0>::run(a, pl, &nb, slot, g);
-            }
+            if (!pl.wall) ReadAll<SS, 0>::run(a, pl, slot, g);
+            else read_general<SS>(a, x, y, z, slot, g);
         } else {
 #pragma unroll
             for (int i = 0; i < 19; ++i) g[i] = 0.f;
@@ -800,61 +931,68 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
         const float usq = ux * ux + uy * uy + uz * uz;
         const float base = drho - rho * 1.5f * usq;
 
-        // B_k, B_tot (Eqs. bk, btot)
-        float B0 = 0.f, B1 = 0.f;
-        if (t.ns > 0) B0 = t.b0 * (tau - 0.5f) / ((1.0f - t.b0) + (tau - 0.5f));
-        if (t.ns > 1) B1 = t.b1 * (tau - 0.5f) / ((1.0f - t.b1) + (tau - 0.5f));
-        const float Btot = fminf(B0 + B1, 1.0f);
+        // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
+        SolidAt q0, q1;
+        q0.B = q1.B = 0.f;
+        q0.ux = q0.uy = q0.uz = q0.usq = q0.ax = q0.ay = q0.az = 0.f;
+        q1.ux = q1.uy = q1.uz = q1.usq = q1.ax = q1.ay = q1.az = 0.f;
+        q0.sx = q0.sy = q0.sz = q1.sx = q1.sy = q1.sz = 0.f;
+        if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
+        if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
+        const float Btot = fminf(q0.B + q1.B, 1.0f);
         const float keep = 1.0f - (1.0f - Btot) * omega;
         const float force_w = (1.0f - Btot) * a.guo_pref;
         const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
+        // solid k: du = u - u_k, dusq = u^2 - u_k^2, and rho t_i folded later
+        const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
+        const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
 
-        float neq[19], out[19];
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            const float cu = (float)CX(i) * ux + (float)CY(i) * uy + (float)CZ(i) * uz;
-            const float geq = TW(i) * (base + rho * (3.0f * cu + 4.5f * cu * cu));
-            neq[i] = g[i] - geq;
-            out[i] = geq + keep * neq[i];
-            if (a.has_force) {
-                const float cF = (float)CX(i) * a.F[0] + (float)CY(i) * a.F[1] + (float)CZ(i) * a.F[2];
-                out[i] += force_w * TW(i) * (3.0f * (cF - Fu) + 9.0f * cu * cF);
-            }
+        // non-equilibrium parts in place: g_i <- g_i - geq_i(rho, u)
+        {
+            const float sym0 = base;  // rest direction: c = 0
+            g[0] -= TW(0) * sym0;
+        }
+        CollidePairs<SS, 1>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, t.ns, q0, q1,
+                                 d0x, d0y, d0z, d0s, d1x, d1y, d1z, d1s, pout + pl.cell, valid);
+        {   // rest direction: Omega^s_0 = -(geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho dusq_k
+            float out0 = TW(0) * base + keep * g[0];
+            if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
+            if (t.ns > 0) out0 += q0.B * (1.5f * TW(0) * rho * d0s);
+            if (t.ns > 1) out0 += q1.B * (1.5f * TW(0) * rho * d1s);
+            if (valid) SS::store(pout + pl.cell, out0, a.scale);
         }
 
-        // solid operators, one solid at a time; the slot loop is warp-uniform
-        for (int k = 0; k < 2; ++k) {
-            const bool act = k < t.ns;
-            if (!__any_sync(FULL, act)) break;
-            SolidAt q;
-            q.B = 0.f;
-            q.ax = q.ay = q.az = 0.f;
-            q.sx = q.sy = q.sz = 0.f;
-            if (act) {
-                solid_at(a, tc, k == 0 ? t.e0 : t.e1, k == 0 ? t.b0 : t.b1, lane, warp, iz, tau, q);
-                const float dux = ux - q.ux, duy = uy - q.uy, duz = uz - q.uz;
-                const float dusq = usq - q.usq;
+        // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
+        // Down a column a thread rarely meets a second particle within one tile, so it
+        // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
+        // FP64 sums only when some lane meets a different particle (and at the end of the
+        // tile); a second solid in a node (rare) is flushed at once.
+        {
+            const int key0 = t.ns > 0 ? t.e0 : -1;
+            float v0[6];
+            solid_force(q0, rho, d0x, d0y, d0z, a, v0);
+            // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
+            // held sum (the lane may meet the same particle again further down)
+            const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
+            if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
+            if (change) {
+                hkey = -1;
 #pragma unroll
-                for (int i = 0; i < 19; ++i) {
-                    const float cu = (float)CX(i) * ux + (float)CY(i) * uy + (float)CZ(i) * uz;
-                    const float cuk = (float)CX(i) * q.ux + (float)CY(i) * q.uy + (float)CZ(i) * q.uz;
-                    const float cdu = (float)CX(i) * dux + (float)CY(i) * duy + (float)CZ(i) * duz;
-                    // geq_i(rho,u) - geq_i(rho,u_k)
-                    const float dgeq = TW(i) * rho * (3.0f * cdu + 4.5f * (cu * cu - cuk * cuk) - 1.5f * dusq);
-                    const float oms = neq[OPP(i)] - neq[i] - dgeq;
-                    out[i] += q.B * oms;
-                    if (CX(i)) q.sx += (float)CX(i) * oms;
-                    if (CY(i)) q.sy += (float)CY(i) * oms;
-                    if (CZ(i)) q.sz += (float)CZ(i) * oms;
-                }
+                for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
             }
-            reduce_slot(tc, act ? (k == 0 ? t.e0 : t.e1) : -1, q);
-        }
-        if (valid) {
+            if (key0 >= 0) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) SS::store(pout + (a.pN[i] + pl.cell), out[i], a.scale);
+                for (int c = 0; c < 6; ++c) hacc[c] += v0[c];
+                hkey = key0;
+            }
+            if (__any_sync(FULL, t.ns > 1)) {
+                float v1[6];
+                solid_force(q1, rho, d1x, d1y, d1z, a, v1);
+                warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
+            }
         }
     }
+    warp_flush(tc, hkey, hacc);
     cp_async_wait<0>();
     __syncthreads();
     for (int idx = tid; idx < 6 * cnt; idx += blockDim.x) {
@@ -862,7 +1000,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm(const LbmArgs a) {
         double v = tc.acc[c][e];
         if (v != 0.0) {
             double* dst = c < 3 ? a.Fh + (long long)c * a.pcap : a.Mh + (long long)(c - 3) * a.pcap;
-            atomicAdd(dst + tc.pid[e], v);
+            atomicAdd(dst + tc_pid(tc, e), v);
         }
     }
 }
@@ -893,8 +1031,8 @@ __global__ void __launch_bounds__(256) k_voxelize(const LbmArgs a, float* beta, 
         long long cell = x + (long long)a.nx * (y + (long long)a.ny * z);
         beta[2 * cell] = t.ns > 0 ? t.b0 : 0.f;
         beta[2 * cell + 1] = t.ns > 1 ? t.b1 : 0.f;
-        ids[2 * cell] = t.ns > 0 ? tc.pid[t.e0] : -1;
-        ids[2 * cell + 1] = t.ns > 1 ? tc.pid[t.e1] : -1;
+        ids[2 * cell] = t.ns > 0 ? tc_pid(tc, t.e0) : -1;
+        ids[2 * cell + 1] = t.ns > 1 ? tc_pid(tc, t.e1) : -1;
         nsolid[cell] = t.total;
     }
 }

@@ -59,9 +59,11 @@ __global__ void k_na_keys(const double* pos, int n, Grid g, uint32_t* keys, uint
     int c[3];
     for (int a = 0; a < 3; ++a) {
         double q = floor((pos[(long long)a * n + k] - g.lo[a]) / g.gh[a]);
-        int v = (int)q;
-        if (q < 0) v = 0;
-        if (q > g.gn[a] - 1) v = g.gn[a] - 1;
+        // clamp before converting: a non-finite position lands in cell 0, never out of range
+        int v;
+        if (!(q >= 0.0)) v = 0;
+        else if (q > g.gn[a] - 1) v = g.gn[a] - 1;
+        else v = (int)q;
         c[a] = v;
     }
     uint32_t key = (uint32_t)(c[0] + g.gn[0] * (c[1] + g.gn[1] * c[2]));
