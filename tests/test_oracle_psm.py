@@ -173,3 +173,36 @@ def test_rotating_sphere_torque(oracle):
     ratio = Mh[0, 2] / (-8 * math.pi * nu * R ** 3 * w)
     assert 0.6 < ratio < 1.1
     assert abs(Mh[0, 0]) < 1e-10 * abs(Mh[0, 2]) + 1e-15
+
+
+def test_coupled_step_momentum_budget(oracle):
+    """The flowchart order (Sec. 3.2) couples fluid and particles through the same force:
+    the collision removes F_h(n) from the fluid, while the velocity-Verlet corrector gives
+    the particle (F_h(n-1) + F_h(n))/2. In a periodic box without walls or gravity the sum
+    p_fluid + p_particles + F_h(last)/2 is therefore exactly conserved (contacts cancel)."""
+    N = 24
+    g = W.rng(205)
+    p = oracle.default_params(tau=0.9, voxel=0, n_sub=1, rho_f=1.0, k_n=5.0, k_t=5.0 * 2 / 7,
+                              dem_h=7.5)
+    s = oracle.Sim(N, N, N, periodic=(1, 1, 1), params=p, max_particles=3)
+    rho, u = W.random_fields(g, N, N, N, amp_u=0.01)
+    s.init_equilibrium(rho, u)
+    pos = np.array([[5.0, 6.0, 7.0], [12.0, 12.5, 11.0], [18.0, 5.0, 17.0]])
+    vel = np.array([[0.01, -0.005, 0.002], [-0.004, 0.003, 0.0], [0.0, 0.006, -0.008]])
+    s.set_particles([0, 0, 0], [3.0] * 3, [[3.0] * 3] * 3, [1.5, 1.2, 2.0], pos, vel=vel)
+    c, _, _ = oracle.lattice_tables()
+    m = np.array([1.5, 1.2, 2.0]) * 4.0 / 3.0 * math.pi * 27.0
+
+    def budget():
+        f = s.populations()
+        pf = (f.T @ c).sum(0)
+        _, v, _, _ = s.particles()
+        Fh, _, _, _ = s.forces()
+        return pf + (m[:, None] * v).sum(0) + 0.5 * Fh.sum(0)
+
+    b0 = budget()
+    s.step(40)
+    b1 = budget()
+    _, v1, _, _ = s.particles()
+    assert np.abs(v1 - vel).max() > 1e-4          # the particles did exchange momentum
+    assert np.allclose(b1, b0, rtol=0, atol=1e-12)
