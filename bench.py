@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--edge", type=int, default=256,
+                    help="lattice edge of the Couette workload (spheres scaled to keep the "
+                         "solid fraction); smaller than 256 only for profiler captures")
     return ap.parse_args()
 
 
@@ -53,6 +56,18 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, dist):
+    """Largest value of x over all ranks (x itself without a process group). The
+    reduction runs on the GPU under NCCL and on the host under gloo."""
+    if dist is None:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def peaks():
@@ -126,6 +141,53 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def ensemble_measure(args, device, stream):
+    """The batched ensemble (64 independent settling/shear simulations, edges U{24..96},
+    1-64 spheres, FP16-stored populations) advanced in one batch, timed with CUDA events;
+    beside it the same members stepped one after another as separate simulations."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    ws = W.batched_ensemble(nsim=64, seed_index=5, storage="f16")
+    cells = sum(w.ncell for w in ws)
+    b = ledds.batch_from_workloads(ws, device=device)
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    bad = {k: 0 for k in ("tile_overflow", "cand_overflow", "nan_detected", "solids_overflow")}
+    for m in b.members:
+        st = m.status()
+        for k in bad:
+            bad[k] += st[k]
+    b.close()
+    del b
+    serial_ms = 0.0
+    for w in ws:
+        s = ledds.from_workload(w, device=device)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        serial_ms += e0.elapsed_time(e1)
+        s.close()
+        del s
+    torch.cuda.empty_cache()
+    return {"workload": "ensemble of 64 settling/shear simulations, edges U{24..96}, 1-64 spheres R 3-8, "
+                        "tau U[0.6,1.2], FP16-stored f, one batch",
+            "value": cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "per_sim_latency_ms_per_step": ms / args.steps,
+            "sims": len(ws), "cells": cells, "particles": int(sum(w.n for w in ws)),
+            "separate_sims_MLUPS": cells * args.steps / (serial_ms * 1e-3) / 1e6,
+            "speedup_vs_separate_sims": serial_ms / ms,
+            "launches_per_step": 4, "status": bad}
+
+
 def oracle_sample(steps):
     """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
     slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps."""
@@ -184,7 +246,9 @@ def main():
         td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         dist = td
     hbm, peak_kind = peaks()
-    w = W.couette_suspension(storage=args.storage)
+    E = args.edge
+    w = W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
+                             storage=args.storage)
     N = w.ncell
     sim = ledds.from_workload(w, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
@@ -206,11 +270,7 @@ def main():
     e1.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
     value = N * args.steps * world / (ms * 1e-3) / 1e6
     st = sim.status()
 
@@ -243,7 +303,7 @@ def main():
         sim.step(1)
         ledds.check("ledds_read_particles", ledds.lib().ledds_read_particles(sim.h, h_out.data_ptr(), 0))
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
     e2e = {"value": N * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 18 * 8 * n, "d2h_bytes_per_step": 18 * 8 * n,
            "api": "ledds_write_kinematics(host) + ledds_step(1) + ledds_read_particles(host)"}
@@ -279,6 +339,9 @@ def main():
             del v
             torch.cuda.empty_cache()
 
+    if not args.no_variants:
+        variants["ensemble"] = ensemble_measure(args, f"cuda:{local}", stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(2)
@@ -292,7 +355,7 @@ def main():
                 "config": {"workload": w.name, "cells": N, "particles": w.n,
                            "storage": args.storage, "n_sub": w.params["n_sub"],
                            "tau": w.params["tau"], "voxel": w.params["voxel"],
-                           "l2": "inputs larger than L2 (populations 2 x 19 x 16.8M values)",
+                           "l2": f"inputs larger than L2 (populations 2 x 19 x {N / 1e6:.1f}M values)",
                            "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": st["launches_per_step"] * args.steps,

@@ -211,6 +211,42 @@ int ledds_read_profile(ledds_sim_t s, double ms[5], long long* steps, long long*
 int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes);
 int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes);
 
+/* ------------------------------------------------------------------------------------
+ * Batches: many independent simulations (uneven lattices and particle counts) advanced
+ * together. Not in the paper; an ensemble form of the same coupled step. Per fluid step
+ * the whole batch uses four kernel launches (graph-replayed): a DEM kernel with one CTA
+ * per simulation running all substeps, tile binning, one persistent PSM kernel whose
+ * CTAs take (simulation, tile) work items from a queue, and the velocity corrector. DEM
+ * candidates are found by direct search within each simulation (same contact set as the
+ * cell list), so members hold at most 4096 particles.
+ * ------------------------------------------------------------------------------------ */
+typedef struct ledds_batch_s* ledds_batch_t;
+
+/* Workspace bytes for nsim members described by the arrays dims[nsim], params[nsim]. Every
+ * member needs a lattice; all members share the storage format.
+ * Errors: INVALID_ARG (as ledds_workspace_size, or a member without a lattice, mixed
+ * storage, more than 4096 particles). */
+int ledds_batch_workspace_size(int nsim, const ledds_dims* dims, const ledds_params* params,
+                               size_t* bytes);
+
+/* Create the batch in a caller-owned workspace of at least ledds_batch_workspace_size
+ * bytes (256-byte aligned) on `stream`. Members start with fluid at rest, no particles. */
+int ledds_batch_create(int nsim, const ledds_dims* dims, const ledds_params* params,
+                       void* d_workspace, size_t bytes, void* stream, ledds_batch_t* out);
+
+/* Handle of member i, valid until ledds_batch_destroy. All single-simulation calls apply
+ * to it (walls, forcing, initialisation, particles, reads, status, checkpoint) except
+ * ledds_step, ledds_destroy and ledds_read_cell_keys (the batch finds contact candidates
+ * by direct search and keeps no cell list), which return LEDDS_ERR_STATE. */
+int ledds_batch_sim(ledds_batch_t b, int i, ledds_sim_t* out);
+
+/* Advance every member by n_steps fluid steps (each with its own n_sub DEM substeps).
+ * Asynchronous on the batch's stream. */
+int ledds_batch_step(ledds_batch_t b, int n_steps);
+
+/* Release the batch and its members' host objects (the workspace stays the caller's). */
+int ledds_batch_destroy(ledds_batch_t b);
+
 /* Cell keys and (key, id)-sorted particle ids of the DEM grid, computed without any
  * device allocation. The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory themselves, such as code running under a memory

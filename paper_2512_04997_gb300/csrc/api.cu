@@ -27,6 +27,11 @@ cudaError_t launch_final(const DemArgs&, int, int, cudaStream_t);
 cudaError_t launch_pairs(const DemArgs&, int, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
                          int, cudaStream_t);
 cudaError_t launch_scan(const uint32_t*, int, uint32_t*, uint32_t*, cudaStream_t);
+cudaError_t launch_psm_batch(const LbmArgs*, const int*, int, int*, int, int, cudaStream_t);
+cudaError_t launch_bin_batch(const LbmArgs*, const int*, int, cudaStream_t);
+cudaError_t launch_dem_batch(const DemArgs*, const int*, int, int, cudaStream_t);
+cudaError_t launch_final_batch(const DemArgs*, int, cudaStream_t);
+size_t psm_smem_bytes();
 }  // namespace ledds
 
 using namespace ledds;
@@ -77,6 +82,9 @@ struct ledds_sim_s {
     bool ev_made = false;
     double prof_ms[NSTAGE];
     long long prof_steps = 0, prof_launches = 0;
+    // batch membership
+    bool in_batch = false;
+    long long version = 0;   // bumped by every change that invalidates captured graphs
 };
 
 // ------------------------------------------------------------------------------------
@@ -328,6 +336,7 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     memcpy(A.uw, s->uw, sizeof(A.uw));
     A.G = s->G;
     A.dt = 1.0 / s->p.n_sub;
+    A.n_sub = s->p.n_sub;
     A.law = s->p.law;
     A.k_n = s->p.k_n;
     A.k_t = s->p.k_t;
@@ -364,6 +373,7 @@ static DemArgs dem_args(const ledds_sim_s* s) {
 }
 
 static void drop_graphs(ledds_sim_s* s) {
+    s->version++;
     for (int q = 0; q < 2; ++q) {
         if (s->g1[q]) cudaGraphExecDestroy(s->g1[q]);
         if (s->g2[q]) cudaGraphExecDestroy(s->g2[q]);
@@ -532,6 +542,7 @@ int ledds_create(const ledds_dims* d, const ledds_params* p, void* d_workspace, 
 
 int ledds_destroy(ledds_sim_t s) {
     if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (s->in_batch) return LEDDS_ERR_STATE;  // owned by its batch
     drop_graphs(s);
     if (s->ev_made)
         for (int q = 0; q <= NSTAGE; ++q) cudaEventDestroy(s->ev[q]);
@@ -697,6 +708,7 @@ int ledds_write_kinematics(ledds_sim_t s, const double* state, int on_device) {
 
 int ledds_step(ledds_sim_t s, int n_steps) {
     if (!s || n_steps < 0) return LEDDS_ERR_INVALID_ARG;
+    if (s->in_batch) return LEDDS_ERR_STATE;  // members advance with ledds_batch_step
     if (s->profiling) {
         if (!s->ev_made) {
             for (int q = 0; q <= NSTAGE; ++q)
@@ -826,6 +838,7 @@ int ledds_read_pairs(ledds_sim_t s, uint64_t* d_keys, int cap, int* n_out) {
 
 int ledds_read_cell_keys(ledds_sim_t s, uint32_t* d_keys, int32_t* d_sorted_ids, int grid_n[3]) {
     if (!s) return LEDDS_ERR_INVALID_ARG;
+    if (s->in_batch) return LEDDS_ERR_STATE;  // a batch searches candidates directly, without a cell list
     int n = s->P.n;
     if (grid_n)
         for (int a = 0; a < 3; ++a) grid_n[a] = s->gn[a];
@@ -924,6 +937,199 @@ int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     s->steps = hd.steps;
     memcpy(s->uw, hd.uw, sizeof(hd.uw));
     drop_graphs(s);
+    return LEDDS_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Batches: many independent simulations advanced by one set of launches per step.
+// ------------------------------------------------------------------------------------
+struct ledds_batch_s {
+    int nsim = 0;
+    std::vector<ledds_sim_s*> sims;
+    cudaStream_t stream = nullptr, cap_stream = nullptr;
+    int storage = 0, parity = 0, nblocks = 0;
+    long long steps = 0;
+    LbmArgs* d_largs[2] = {nullptr, nullptr};
+    DemArgs* d_dargs = nullptr;
+    int *d_tile_start = nullptr, *d_np = nullptr, *d_poff = nullptr, *d_counter = nullptr;
+    cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
+    std::vector<long long> versions;
+};
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+static int batch_layout(int nsim, const ledds_dims* dims, const ledds_params* params, std::vector<size_t>* offs,
+                        size_t* total) {
+    if (nsim <= 0 || !dims || !params) return LEDDS_ERR_INVALID_ARG;
+    size_t off = 0;
+    for (int i = 0; i < nsim; ++i) {
+        int rc = check_args(&dims[i], &params[i]);
+        if (rc != LEDDS_OK) return rc;
+        if (dims[i].nx <= 0) return LEDDS_ERR_INVALID_ARG;  // every member has a lattice
+        if (params[i].storage != params[0].storage) return LEDDS_ERR_INVALID_ARG;
+        if (dims[i].max_particles > 4096) return LEDDS_ERR_INVALID_ARG;  // direct candidate search
+        if (offs) offs->push_back(off);
+        off = align256(off + layout(nullptr, &dims[i], &params[i], nullptr));
+    }
+    off = align256(off + 2 * sizeof(LbmArgs) * nsim);
+    off = align256(off + sizeof(DemArgs) * nsim);
+    off = align256(off + sizeof(int) * (3 * nsim + 2));
+    *total = off + 256;
+    return LEDDS_OK;
+}
+
+int ledds_batch_workspace_size(int nsim, const ledds_dims* dims, const ledds_params* params, size_t* bytes) {
+    if (!bytes) return LEDDS_ERR_INVALID_ARG;
+    return batch_layout(nsim, dims, params, nullptr, bytes);
+}
+
+static void batch_drop_graphs(ledds_batch_s* b) {
+    for (int q = 0; q < 2; ++q) {
+        if (b->g1[q]) cudaGraphExecDestroy(b->g1[q]);
+        if (b->g2[q]) cudaGraphExecDestroy(b->g2[q]);
+        b->g1[q] = b->g2[q] = nullptr;
+    }
+}
+
+int ledds_batch_destroy(ledds_batch_t b) {
+    if (!b) return LEDDS_ERR_INVALID_ARG;
+    batch_drop_graphs(b);
+    for (auto* s : b->sims) {
+        s->in_batch = false;
+        ledds_destroy(s);
+    }
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    return LEDDS_OK;
+}
+
+int ledds_batch_create(int nsim, const ledds_dims* dims, const ledds_params* params, void* d_workspace,
+                       size_t bytes, void* stream, ledds_batch_t* out) {
+    std::vector<size_t> offs;
+    size_t need = 0;
+    int rc = batch_layout(nsim, dims, params, &offs, &need);
+    if (rc != LEDDS_OK) return rc;
+    if (!out || !d_workspace || ((uintptr_t)d_workspace & 255) || bytes < need) return LEDDS_ERR_INVALID_ARG;
+    ledds_batch_s* b = new ledds_batch_s();
+    b->nsim = nsim;
+    b->stream = (cudaStream_t)stream;
+    b->storage = params[0].storage;
+    char* ws = (char*)d_workspace;
+    for (int i = 0; i < nsim; ++i) {
+        ledds_sim_t s = nullptr;
+        size_t sz = layout(nullptr, &dims[i], &params[i], nullptr);
+        rc = ledds_create(&dims[i], &params[i], ws + offs[i], sz, stream, &s);
+        if (rc != LEDDS_OK) {
+            ledds_batch_destroy(b);
+            return rc;
+        }
+        s->in_batch = true;
+        b->sims.push_back(s);
+    }
+    size_t off = align256(offs.back() + layout(nullptr, &dims[nsim - 1], &params[nsim - 1], nullptr));
+    b->d_largs[0] = reinterpret_cast<LbmArgs*>(ws + off);
+    b->d_largs[1] = b->d_largs[0] + nsim;
+    off = align256(off + 2 * sizeof(LbmArgs) * nsim);
+    b->d_dargs = reinterpret_cast<DemArgs*>(ws + off);
+    off = align256(off + sizeof(DemArgs) * nsim);
+    b->d_tile_start = reinterpret_cast<int*>(ws + off);
+    b->d_np = b->d_tile_start + nsim + 1;
+    b->d_poff = b->d_np + nsim;
+    b->d_counter = b->d_poff + nsim;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->nblocks = 2 * (sms > 0 ? sms : 1);
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ledds_batch_destroy(b);
+        return LEDDS_ERR_CUDA;
+    }
+    *out = b;
+    return LEDDS_OK;
+}
+
+int ledds_batch_sim(ledds_batch_t b, int i, ledds_sim_t* out) {
+    if (!b || !out || i < 0 || i >= b->nsim) return LEDDS_ERR_INVALID_ARG;
+    *out = b->sims[i];
+    return LEDDS_OK;
+}
+
+// Upload the per-member kernel arguments (both batch parities), the tile prefix, the
+// particle counts and each member's buffer parity relative to the batch's (a member
+// restored from a checkpoint may sit on the other population buffer).
+static cudaError_t batch_upload(ledds_batch_s* b) {
+    const int n = b->nsim;
+    std::vector<LbmArgs> la(2 * n);
+    std::vector<DemArgs> da(n);
+    std::vector<int> ts(3 * n + 2, 0);
+    for (int i = 0; i < n; ++i) {
+        ledds_sim_s* s = b->sims[i];
+        const int last = (s->p.n_sub - 1) & 1;
+        const int off = s->parity ^ b->parity;
+        la[i] = lbm_args(s, off, off ^ 1, last);
+        la[n + i] = lbm_args(s, off ^ 1, off, last);
+        da[i] = dem_args(s);
+        ts[i + 1] = ts[i] + s->ntiles;
+        ts[n + 1 + i] = s->P.n;
+        ts[2 * n + 1 + i] = off;
+    }
+    CK(cudaMemcpyAsync(b->d_largs[0], la.data(), sizeof(LbmArgs) * 2 * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_dargs, da.data(), sizeof(DemArgs) * n, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->d_tile_start, ts.data(), sizeof(int) * (3 * n + 1), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->versions.assign(n, 0);
+    for (int i = 0; i < n; ++i) b->versions[i] = b->sims[i]->version;
+    return cudaSuccess;
+}
+
+static cudaError_t batch_enqueue(ledds_batch_s* b, int p, cudaStream_t st) {
+    CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    CK(launch_dem_batch(b->d_dargs, b->d_poff, b->nsim, p, st));
+    CK(launch_bin_batch(b->d_largs[p], b->d_np, b->nsim, st));
+    CK(launch_psm_batch(b->d_largs[p], b->d_tile_start, b->nsim, b->d_counter, b->storage, b->nblocks, st));
+    CK(launch_final_batch(b->d_dargs, b->nsim, st));
+    return cudaSuccess;
+}
+
+static cudaError_t batch_capture(ledds_batch_s* b, int p, int nsteps, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < nsteps && e == cudaSuccess; ++q) e = batch_enqueue(b, p ^ (q & 1), b->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+    }
+    if (e2 != cudaSuccess) return e2;
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+int ledds_batch_step(ledds_batch_t b, int n_steps) {
+    if (!b || n_steps < 0) return LEDDS_ERR_INVALID_ARG;
+    bool stale = b->versions.size() != (size_t)b->nsim;
+    for (int i = 0; i < b->nsim && !stale; ++i) stale = b->versions[i] != b->sims[i]->version;
+    if (stale) {
+        batch_drop_graphs(b);
+        if (batch_upload(b) != cudaSuccess) return LEDDS_ERR_CUDA;
+    }
+    int left = n_steps;
+    while (left > 0) {
+        const int p = b->parity;
+        const int k = left >= 2 ? 2 : 1;
+        cudaGraphExec_t* g = k == 2 ? &b->g2[p] : &b->g1[p];
+        if (!*g && batch_capture(b, p, k, g) != cudaSuccess) return LEDDS_ERR_CUDA;
+        if (cudaGraphLaunch(*g, b->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+        left -= k;
+        b->steps += k;
+        if (k == 1) b->parity ^= 1;
+        for (auto* s : b->sims) {
+            s->steps += k;
+            if (k == 1) s->parity ^= 1;
+        }
+    }
     return LEDDS_OK;
 }
 

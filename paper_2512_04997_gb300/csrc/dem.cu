@@ -758,6 +758,131 @@ __global__ void k_final(DemArgs A, int in, int use_hydro) {
     store_state(A, A.P.st[0], k, r, v, w, d);
 }
 
+// ------------------------------------------------------------------------------------
+// Batched DEM: one CTA per simulation runs the whole particle stage of a fluid step
+// (candidate lists, every substep, the last contact sums) with CTA barriers between the
+// phases instead of kernel launches. Candidates are found by direct search over the
+// simulation's particles: for the small per-simulation counts this path serves it
+// replaces the cell list and yields the same candidate lists (all particles within the
+// sum of bounding radii plus the skin, ascending ids).
+// ------------------------------------------------------------------------------------
+__device__ void candidates_direct(const DemArgs& A, int i, int ob, int nbuf) {
+    const double* st = A.P.st[0];
+    double ri[3];
+    ld3(A, st, SP, i, ri);
+    for (int a = 0; a < 3; ++a) A.P.pos_build[(long long)a * A.P.cap + i] = ri[a];
+    const double bi = A.P.bound[i];
+    int* nc = A.cand[nbuf] + (long long)i * A.ccap;
+    int cnt = 0, over = 0;
+    for (int j = 0; j < A.P.n; ++j) {  // ascending ids: the list comes out sorted
+        if (j == i) continue;
+        double d[3];
+        for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        double lim = bi + A.P.bound[j] + A.skin;
+        if (d2 < lim * lim) {
+            if (cnt < A.ccap) nc[cnt++] = j;
+            else over = 1;
+        }
+    }
+    if (over) atomicAdd(&A.status->cand_overflow, 1);
+    const int* oc = A.cand[ob] + (long long)i * A.ccap;
+    const double* oh = A.hist[ob] + (long long)i * A.ccap * 3;
+    double* nh = A.hist[nbuf] + (long long)i * A.ccap * 3;
+    int nold = A.ncand[ob][i], p = 0;
+    for (int m = 0; m < cnt; ++m) {
+        int j = nc[m];
+        while (p < nold && oc[p] < j) ++p;
+        bool found = p < nold && oc[p] == j;
+        for (int a = 0; a < 3; ++a) nh[3 * m + a] = found ? oh[3 * p + a] : 0.0;
+    }
+    A.ncand[nbuf][i] = cnt;
+}
+
+__device__ void contact_sum_serial(const DemArgs& A, const double* st, int cb, int i, double F[3], double M[3]) {
+    for (int c = 0; c < 3; ++c) F[c] = M[c] = 0.0;
+    const int nc = A.ncand[cb][i];
+    for (int m = 0; m < nc; ++m) pair_contrib(A, st, cb, i, m, F, M);
+    for (int face = 0; face < 6; ++face) wall_contrib(A, st, i, face, F, M);
+}
+
+__global__ void k_dem_batch(const DemArgs* args, const int* poff, int batch_parity) {
+    const DemArgs& A = args[blockIdx.x];
+    const int n = A.P.n;
+    if (n == 0) return;  // uniform across the CTA
+    const int p = batch_parity ^ poff[blockIdx.x];  // this member's buffer parity
+    const int cb = p ^ 1, nsub = A.n_sub;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) candidates_direct(A, k, p, cb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double r[3], v[3], w[3], d[9], acc[3];
+        load_state(A, A.P.st[0], k, r, v, w, d);
+        for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+        predict(A, k, r, v, acc, w, d);
+        for (int a = 0; a < 3; ++a) A.P.st[0][(long long)(SP + a) * A.P.cap + k] = r[a];
+        for (int m = 0; m < 9; ++m) A.P.st[0][(long long)(ST + m) * A.P.cap + k] = d[m];
+    }
+    __syncthreads();
+    for (int sub = 1; sub <= nsub; ++sub) {
+        const int in = (sub - 1) & 1, out = sub & 1;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            double F[3], M[3];
+            contact_sum_serial(A, A.P.st[in], cb, k, F, M);
+            for (int a = 0; a < 3; ++a) {
+                A.P.Fc[(long long)a * A.P.cap + k] = F[a];
+                A.P.Mc[(long long)a * A.P.cap + k] = M[a];
+            }
+            if (sub == nsub) continue;  // the last substep's velocities wait for the fluid
+            double r[3], v[3], w[3], d[9], Ft[3], Mt[3], acc[3];
+            load_state(A, A.P.st[in], k, r, v, w, d);
+            for (int a = 0; a < 3; ++a) {
+                long long o = (long long)a * A.P.cap + k;
+                Ft[a] = F[a] + A.P.Fhp[o];
+                Mt[a] = M[a] + A.P.Mhp[o];
+            }
+            correct(A, k, Ft, Mt, d, v, w);
+            for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+            predict(A, k, r, v, acc, w, d);
+            store_state(A, A.P.st[out], k, r, v, w, d);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_final_batch(const DemArgs* args, int use_hydro_mask) {
+    const DemArgs& A = args[blockIdx.x];
+    const int n = A.P.n;
+    const int in = (A.n_sub - 1) & 1;
+    const int use_hydro = (use_hydro_mask >> 0) & 1;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        double r[3], v[3], w[3], d[9], F[3], M[3];
+        load_state(A, A.P.st[in], k, r, v, w, d);
+        for (int a = 0; a < 3; ++a) {
+            long long o = (long long)a * A.P.cap + k;
+            double fh = use_hydro ? A.P.Fh[o] : 0.0, mh = use_hydro ? A.P.Mh[o] : 0.0;
+            F[a] = A.P.Fc[o] + fh;
+            M[a] = A.P.Mc[o] + mh;
+            A.P.Fhp[o] = fh;
+            A.P.Mhp[o] = mh;
+        }
+        correct(A, k, F, M, d, v, w);
+        bool bad = false;
+        for (int a = 0; a < 3; ++a) bad |= !isfinite(v[a]) || !isfinite(w[a]);
+        if (bad) atomicAdd(&A.status->nan_detected, 1);
+        store_state(A, A.P.st[0], k, r, v, w, d);
+    }
+}
+
+cudaError_t launch_dem_batch(const DemArgs* args, const int* poff, int nsim, int p, cudaStream_t s) {
+    k_dem_batch<<<nsim, 128, 0, s>>>(args, poff, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_final_batch(const DemArgs* args, int nsim, cudaStream_t s) {
+    k_final_batch<<<nsim, 128, 0, s>>>(args, 1);
+    return cudaGetLastError();
+}
+
 // Contact set at buffer 0 positions: counts of partners j > i, then keys (i << 32 | j).
 __global__ void k_pair_count(DemArgs A, int cb, uint32_t* cnt) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -164,6 +164,7 @@ struct DemArgs {
     int G;
     // parameters
     double dt;
+    int n_sub;
     double gravity[3];
     int law;
     double k_n, k_t, beta, Ystar, Gstar, mu;

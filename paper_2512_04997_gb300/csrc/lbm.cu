@@ -851,19 +851,20 @@ struct CollidePairs<SS, 19> {
 //   f*_i = geq_i + (1 - (1-B_tot)/tau) neq_i + sum_k B_k Omega^s_{i,k},
 //   Omega^s_{i,k} = neq_ibar - neq_i - (geq_i(rho,u) - geq_i(rho,u_k)).
 // ------------------------------------------------------------------------------------
+// One 32x8xTILE_Z tile (bx, by, bz) of the lattice described by `a`; psm_smem holds the
+// tile cache followed by the pipeline stages (psm_smem_bytes()).
 template <int STORE>
-__global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmArgs a) {
+__device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, unsigned char* psm_smem) {
     using SS = Store<STORE>;
     using T = typename SS::T;
     const T* pin = (const T*)a.pop_in;
     T* pout = (T*)a.pop_out;
-    extern __shared__ __align__(16) unsigned char psm_smem[];
     TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
     uint32_t* stage = reinterpret_cast<uint32_t*>(psm_smem + ((sizeof(TileCache) + 15) & ~(size_t)15));
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * TILE_Z;
-    const int tile = (blockIdx.z * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int tile = (bz * a.nty + by) * a.ntx + bx;
     const int x = x0 + lane, y = y0 + warp;
     const bool valid_xy = x < a.nx && y < a.ny;
 
@@ -1005,6 +1006,90 @@ __global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmAr
     }
 }
 
+template <int STORE>
+__global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmArgs a) {
+    extern __shared__ __align__(16) unsigned char psm_smem[];
+    psm_tile<STORE>(a, blockIdx.x, blockIdx.y, blockIdx.z, psm_smem);
+}
+
+// Batched form: persistent CTAs take (simulation, tile) work items from a queue, so many
+// simulations of uneven sizes advance in one launch with balanced load. The simulation's
+// parameters are copied to shared memory for each item.
+constexpr size_t ARGS_SMEM = (sizeof(LbmArgs) + 15) & ~(size_t)15;
+
+template <int STORE>
+__global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const LbmArgs* args,
+                                                                          const int* tile_start, int nsim,
+                                                                          int* counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    LbmArgs& sa = *reinterpret_cast<LbmArgs*>(smem);
+    __shared__ int s_item, s_sim;
+    const int total = tile_start[nsim];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int item = atomicAdd(counter, 1);
+            int lo = 0, hi = nsim - 1;
+            while (lo < hi) {  // last simulation whose first tile is <= item
+                int mid = (lo + hi + 1) >> 1;
+                if (tile_start[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            s_item = item;
+            s_sim = lo;
+        }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int sim = s_sim;
+        const int* src = reinterpret_cast<const int*>(args + sim);
+        int* dst = reinterpret_cast<int*>(&sa);
+        for (int i = threadIdx.x; i < (int)(sizeof(LbmArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+        const int t = item - tile_start[sim];
+        const int bx = t % sa.ntx, by = (t / sa.ntx) % sa.nty, bz = t / (sa.ntx * sa.nty);
+        psm_tile<STORE>(sa, bx, by, bz, smem + ARGS_SMEM);
+        __syncthreads();
+    }
+}
+
+// Tile binning of every simulation of a batch: one CTA per simulation clears its tile
+// lists and hydrodynamic sums, then bins its particles.
+__device__ __forceinline__ void bin_particle(const LbmArgs& a, int k, int* tile_count, int* tile_ids) {
+    double r[3] = {a.st[(SP + 0) * a.pcap + k], a.st[(SP + 1) * a.pcap + k], a.st[(SP + 2) * a.pcap + k]};
+    float reach = reach_of(a, a.shape[k], a.radius[k], a.bound[k]);
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) {
+        atomicAdd(&a.status->nan_detected, 1);
+        return;
+    }
+    int tl[3][16], tcn[3];
+    tcn[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
+    tcn[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
+    tcn[2] = axis_tiles(r[2], reach, a.nz, a.per[2], TILE_Z, tl[2]);
+    for (int c = 0; c < tcn[2]; ++c)
+        for (int b = 0; b < tcn[1]; ++b)
+            for (int q = 0; q < tcn[0]; ++q) {
+                int t = (tl[2][c] * a.nty + tl[1][b]) * a.ntx + tl[0][q];
+                int slot = atomicAdd(&tile_count[t], 1);
+                if (slot < a.tile_cap) tile_ids[(long long)t * a.tile_cap + slot] = k;
+                else atomicAdd(&a.status->tile_overflow, 1);
+            }
+}
+
+__global__ void k_bin_batch(const LbmArgs* args, const int* np) {
+    const LbmArgs& a = args[blockIdx.x];
+    const int n = np[blockIdx.x];
+    int* tcount = const_cast<int*>(a.tile_count);
+    int* tids = const_cast<int*>(a.tile_ids);
+    const int ntiles = a.ntx * a.nty * a.ntz;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) tcount[t] = 0;
+    for (int i = threadIdx.x; i < 3 * a.pcap; i += blockDim.x) {
+        a.Fh[i] = 0.0;
+        a.Mh[i] = 0.0;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n; k += blockDim.x) bin_particle(a, k, tcount, tids);
+}
+
 size_t psm_smem_bytes() {
     return ((sizeof(TileCache) + 15) & ~(size_t)15) + sizeof(uint32_t) * PSM_STAGES * 19 * PSM_THREADS;
 }
@@ -1095,6 +1180,32 @@ cudaError_t launch_psm(const LbmArgs& a, int store, cudaStream_t s) {
     if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32>(a, s);
     if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16>(a, s);
     return launch_psm_t<LEDDS_STORE_BF16>(a, s);
+}
+
+template <int STORE>
+static cudaError_t launch_psm_batch_t(const LbmArgs* args, const int* tile_start, int nsim, int* counter,
+                                      int nblocks, cudaStream_t s) {
+    static bool configured = false;
+    const size_t smem = ARGS_SMEM + psm_smem_bytes();
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_psm_batch<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_psm_batch<STORE><<<nblocks, PSM_THREADS, smem, s>>>(args, tile_start, nsim, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psm_batch(const LbmArgs* args, const int* tile_start, int nsim, int* counter, int store,
+                             int nblocks, cudaStream_t s) {
+    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32>(args, tile_start, nsim, counter, nblocks, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16>(args, tile_start, nsim, counter, nblocks, s);
+    return launch_psm_batch_t<LEDDS_STORE_BF16>(args, tile_start, nsim, counter, nblocks, s);
+}
+
+cudaError_t launch_bin_batch(const LbmArgs* args, const int* np, int nsim, cudaStream_t s) {
+    k_bin_batch<<<nsim, 256, 0, s>>>(args, np);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_voxelize(const LbmArgs& a, float* beta, int* ids, int* nsolid, cudaStream_t s) {

@@ -84,6 +84,11 @@ _SIGS = {
     "ledds_load": (C.c_int, [VP, VP, C.c_size_t]),
     "ledds_cell_list_noalloc": (C.c_int, [VP, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.c_double, VP, VP, C.POINTER(C.c_int), VP]),
+    "ledds_batch_workspace_size": (C.c_int, [C.c_int, VP, VP, C.POINTER(C.c_size_t)]),
+    "ledds_batch_create": (C.c_int, [C.c_int, VP, VP, VP, C.c_size_t, VP, C.POINTER(VP)]),
+    "ledds_batch_sim": (C.c_int, [VP, C.c_int, C.POINTER(VP)]),
+    "ledds_batch_step": (C.c_int, [VP, C.c_int]),
+    "ledds_batch_destroy": (C.c_int, [VP]),
 }
 
 _lib = None
@@ -181,6 +186,20 @@ def particles_array(shape, radius, semi, density, pos, vel=None, omg=None, triad
 class Sim:
     """A simulation whose workspace is a torch uint8 tensor on ``device``."""
 
+    @classmethod
+    def _member(cls, handle, dims, params, device, stream, owner):
+        obj = cls.__new__(cls)
+        import torch
+        obj.torch = torch
+        obj.device = torch.device(device)
+        obj.dims, obj.params = dims, params
+        obj.stream = stream
+        obj.h = handle
+        obj.ncell = dims.nx * dims.ny * dims.nz
+        obj.n = 0
+        obj._owner = owner          # the batch keeps the workspace alive
+        return obj
+
     def __init__(self, dims: ledds_dims, params: ledds_params, device="cuda:0", stream=None):
         import torch
         self.torch = torch
@@ -199,6 +218,9 @@ class Sim:
         self.n = 0
 
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self.h = None           # members are released by their batch
+            return
         if getattr(self, "h", None):
             lib().ledds_destroy(self.h)
             self.h = None
@@ -352,3 +374,70 @@ def from_workload(w, device="cuda:0", **over) -> Sim:
     if w.n:
         s.set_particles(w.shape, w.radius, w.semi, w.density, w.pos, w.vel, w.omg, w.triad)
     return s
+
+
+class Batch:
+    """Many simulations advanced together (ledds_batch_*); members are ``Sim`` objects."""
+
+    def __init__(self, dims_list, params_list, device="cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        L = lib()
+        n = len(dims_list)
+        self.dims = (ledds_dims * n)(*dims_list)
+        self.params = (ledds_params * n)(*params_list)
+        nbytes = C.c_size_t(0)
+        check("ledds_batch_workspace_size", L.ledds_batch_workspace_size(n, self.dims, self.params, C.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=torch.device(device))
+        self.stream = stream if stream is not None else torch.cuda.current_stream(torch.device(device))
+        h = VP()
+        check("ledds_batch_create", L.ledds_batch_create(n, self.dims, self.params, self.workspace.data_ptr(),
+                                                         nbytes.value, VP(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.members = []
+        for i in range(n):
+            mh = VP()
+            check("ledds_batch_sim", L.ledds_batch_sim(h, i, C.byref(mh)))
+            self.members.append(Sim._member(mh, dims_list[i], params_list[i], device, self.stream, self))
+
+    def step(self, n=1):
+        check("ledds_batch_step", lib().ledds_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self.torch.cuda.synchronize()
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None          # member handles die with the batch
+            lib().ledds_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_from_workloads(ws, device="cuda:0", **over):
+    """A batch whose members are the given workloads (fluid initial state and particles)."""
+    keys = {f for f, _ in ledds_params._fields_}
+    dims, params = [], []
+    for w in ws:
+        prm = dict(w.params)
+        prm.update(over)
+        params.append(make_params(**{k: v for k, v in prm.items() if k in keys}))
+        dims.append(make_dims(w.nx, w.ny, w.nz, w.periodic, w.n, w.box_lo, w.box_hi,
+                              cand_cap=prm.get("cand_cap", 0), tile_cap=prm.get("tile_cap", 0)))
+    b = Batch(dims, params, device)
+    for w, s in zip(ws, b.members):
+        for a in range(3):
+            if not w.periodic[a]:
+                for side in range(2):
+                    s.set_wall_velocity(a, side, w.u_wall[a, side])
+        if w.init_u is not None:
+            s.init_fluid(None, w.init_u)
+        if w.n:
+            s.set_particles(w.shape, w.radius, w.semi, w.density, w.pos, w.vel, w.omg, w.triad)
+    return b

@@ -291,3 +291,94 @@ def random_fields(g: np.random.Generator, nx: int, ny: int, nz: int, amp_u: floa
 def population_noise(g: np.random.Generator, ncell: int, amp: float = 1e-3) -> np.ndarray:
     """Uniform noise of shape (19, ncell) used to push populations off equilibrium."""
     return g.uniform(-amp, amp, (19, ncell))
+
+
+def _place_greedy(g: np.random.Generator, radii: np.ndarray, lo, hi, periodic, gap: float,
+                  draws: int = 256):
+    """Random sequential addition with a bounded number of draws per sphere: each sphere
+    takes the first of ``draws`` uniform candidates that clears every kept sphere by
+    ``gap`` (minimum image on periodic axes), or is dropped. Returns (positions, radii)."""
+    L = hi - lo
+    per = np.array([bool(x) for x in periodic])
+    keep_p, keep_r = [], []
+    for R in radii:
+        u = g.random((draws, 3))
+        lo_c = np.where(per, lo, lo + R)
+        span = np.where(per, L, L - 2 * R)
+        cand = lo_c + u * span
+        if keep_p:
+            P = np.array(keep_p)
+            d = cand[:, None, :] - P[None, :, :]
+            d = np.where(per, d - L * np.round(d / L), d)
+            ok = ((d ** 2).sum(-1) >= (R + np.array(keep_r) + gap) ** 2).all(1)
+        else:
+            ok = np.ones(draws, dtype=bool)
+        idx = np.flatnonzero(ok)
+        if idx.size:
+            keep_p.append(cand[idx[0]])
+            keep_r.append(R)
+    return np.array(keep_p).reshape(-1, 3), np.array(keep_r)
+
+
+def batched_ensemble(nsim: int = 64, seed_index: int = 5, steps: int = 1000,
+                     storage: str = "f16") -> list:
+    """Ensemble of independent simulations for one batched launch: lattice edges drawn
+    independently from U{24..96}, tau ~ U[0.6, 1.2], 1-64 spheres with radii U[3, 8],
+    alternately settling (closed box, gravity 1e-5 on particles of density ratio 2.5) and
+    sheared (z walls at -/+0.05, periodic x and y, neutrally buoyant), distance-based solid
+    fractions, one DEM substep.
+
+    Placement: random sequential addition at solid fraction <= 0.3 and one lattice unit
+    from the walls; a sphere that finds no room after a bounded number of draws is left
+    out, and the largest radius is capped where a small periodic box or lattice could not
+    hold it (a periodic edge must exceed twice the contact range, as the minimum-image
+    convention needs)."""
+    g = rng(seed_index)
+    out = []
+    skin = 0.5
+    for i in range(nsim):
+        n3 = [int(g.integers(24, 97)) for _ in range(3)]
+        tau = float(g.uniform(0.6, 1.2))
+        settling = i % 2 == 0
+        periodic = (0, 0, 0) if settling else (1, 1, 0)
+        w = Workload(name=f"ensemble_{i}", nx=n3[0], ny=n3[1], nz=n3[2], periodic=periodic)
+        if not settling:
+            w.u_wall[2, 0, 0] = -0.05
+            w.u_wall[2, 1, 0] = +0.05
+        rmax = min(8.0, (min(n3) - 4) / 2.0)
+        per_edges = [n3[a] for a in range(3) if periodic[a]]
+        if per_edges:
+            rmax = min(rmax, (min(per_edges) / 2.0 - skin) / 2.0 - 0.25)
+        rmax = max(rmax, 3.0)
+        n_target = int(g.integers(1, 65))
+        radii = g.uniform(3.0, rmax, n_target)
+        vol = float(np.prod(n3))
+        while len(radii) > 1 and (4.0 / 3.0 * math.pi * radii ** 3).sum() > 0.3 * vol:
+            radii = radii[:-1]
+        lo = np.array([-0.5 if periodic[a] else 0.5 for a in range(3)])
+        hi = np.array([n3[a] - 0.5 - (0 if periodic[a] else 1.0) for a in range(3)])
+        pos, radii = _place_greedy(g, radii, lo, hi, periodic, gap=0.2)
+        n = len(radii)
+        rho_p = 2.5 if settling else 1.0
+        m_min = rho_p * 4.0 / 3.0 * math.pi * radii.min() ** 3
+        kn = 0.5 * (m_min / 2) * (math.pi / 20.0) ** 2
+        w.params = base_params(tau=tau, storage=storage, voxel="distance", n_sub=1, rho_f=1.0,
+                               gravity=(0.0, 0.0, -1e-5) if settling else (0.0, 0.0, 0.0),
+                               k_n=kn, k_t=kn * 2.0 / 7.0, skin=skin, dem_h=2 * rmax + skin)
+        w.shape = np.zeros(n, dtype=np.int32)
+        w.radius = radii
+        w.semi = np.tile(radii[:, None], (1, 3))
+        w.density = np.full(n, rho_p)
+        w.pos = pos
+        w.vel = np.zeros((n, 3))
+        w.omg = np.zeros((n, 3))
+        w.triad = identity_triads(n)
+        if not settling:
+            w.vel[:, 0] = -0.05 + 0.1 * (pos[:, 2] + 0.5) / n3[2]
+            z = np.arange(n3[2], dtype=np.float64)
+            u = np.zeros((3, n3[2], n3[1], n3[0]))
+            u[0] = (-0.05 + 0.1 * (z + 0.5) / n3[2])[:, None, None]
+            w.init_u = u.reshape(3, -1)
+        w.steps = steps
+        out.append(w)
+    return out

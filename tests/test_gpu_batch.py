@@ -1,0 +1,73 @@
+"""The batched persistent step (ledds_batch_*) against independent simulations and the
+oracle, on an uneven ensemble (lattices 24..96 per edge, 1..64 spheres, settling and
+sheared members)."""
+import numpy as np
+import pytest
+
+from paper_2512_04997_gb300 import workloads as W
+
+from _helpers import gpu_from_workload, normwise, oracle_from_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def test_batch_members_match_independent_runs():
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=8, seed_index=55, storage="f32")
+    b = ledds.batch_from_workloads(ws)
+    b.step(1)
+    b.step(24)     # 1- and 2-step graphs, both parities
+    for w, m in zip(ws, b.members):
+        s = gpu_from_workload(w)
+        s.step(25)
+        _, u_b = m.fields()
+        _, u_s = s.fields()
+        assert normwise(u_b.cpu().numpy(), u_s.cpu().numpy()) < 1e-6
+        if w.n:
+            pb, vb, _, _ = m.particles()
+            ps, vs, _, _ = s.particles()
+            assert np.abs(pb - ps).max() < 1e-9
+            assert normwise(vb, vs) < 1e-6
+        st = m.status()
+        assert st["rc"] == 0, st
+    # members cannot be stepped on their own
+    rc = ledds.lib().ledds_step(b.members[0].h, 1)
+    assert rc == -6
+
+
+def test_batch_member_matches_oracle(oracle):
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=4, seed_index=56, storage="f32")
+    b = ledds.batch_from_workloads(ws)
+    b.step(30)
+    for k in (0, 1):     # one settling and one sheared member
+        o = oracle_from_workload(oracle, ws[k])
+        o.step(30)
+        _, u_o = o.moments()
+        _, u_b = b.members[k].fields()
+        assert normwise(u_b.cpu().numpy(), u_o) < 1e-5
+        if ws[k].n:
+            po, vo, _, _ = o.particles()
+            pb, vb, _, _ = b.members[k].particles()
+            assert normwise(vb, vo) < 1e-5
+
+
+def test_batch_fp16_storage_error():
+    """FP16-offset storage in the batch stays within 2e-3 of the FP32 run on the fields."""
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=6, seed_index=57, storage="f16")
+    b16 = ledds.batch_from_workloads(ws)
+    b32 = ledds.batch_from_workloads(ws, storage="f32")
+    b16.step(100)
+    b32.step(100)
+    for m16, m32 in zip(b16.members, b32.members):
+        _, u16 = m16.fields()
+        _, u32 = m32.fields()
+        assert normwise(u16.cpu().numpy(), u32.cpu().numpy()) < 2e-3
