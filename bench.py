@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="time only the batched 64-simulation ensemble (one JSON line)")
     ap.add_argument("--edge", type=int, default=256,
                     help="lattice edge of the Couette workload (spheres scaled to keep the "
                          "solid fraction); smaller than 256 only for profiler captures")
@@ -246,6 +248,11 @@ def main():
         td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         dist = td
     hbm, peak_kind = peaks()
+    if args.ensemble_only:
+        ens = ensemble_measure(args, f"cuda:{local}", torch.cuda.current_stream())
+        if rank == 0:
+            print(json.dumps({"ensemble": ens, "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return
     E = args.edge
     w = W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
                              storage=args.storage)

@@ -80,6 +80,9 @@ typedef struct {
                              /* particles; the grid size is fixed at creation)                */
     int ell_max_iter;        /* ellipsoid common-normal iterations, Sec. 2.1                 */
     double ell_tol;          /* ellipsoid convergence tolerance (fraction of min semi-axis)  */
+    int force_fp32;          /* 1: contact forces and torques evaluated in FP32 from FP64    */
+                             /* differences and summed in FP64 (contact sets unchanged);     */
+                             /* 0: every DEM operation in FP64. Integration is always FP64.  */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */
@@ -109,7 +112,7 @@ typedef struct ledds_sim_s* ledds_sim_t;
 
 /* Fill *p with defaults: tau 0.8, FP32 storage, distance voxels (subdiv_n 10), linear law,
  * n_sub 1, rho_f 1, no gravity/force, k_n 1000, k_t 2/7 k_n, restitution 0.7, friction
- * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
+ * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
 int ledds_params_default(ledds_params* p);
 
 /* Bytes of device workspace a simulation of these dimensions and parameters needs

@@ -9,6 +9,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -27,7 +28,7 @@ cudaError_t launch_final(const DemArgs&, int, int, cudaStream_t);
 cudaError_t launch_pairs(const DemArgs&, int, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
                          int, cudaStream_t);
 cudaError_t launch_scan(const uint32_t*, int, uint32_t*, uint32_t*, cudaStream_t);
-cudaError_t launch_psm_batch(const LbmArgs*, const int*, int, int*, int, int, cudaStream_t);
+cudaError_t launch_psm_batch(const BatchChunk&, int*, int, int, cudaStream_t);
 cudaError_t launch_bin_batch(const LbmArgs*, const int*, int, cudaStream_t);
 cudaError_t launch_dem_batch(const DemArgs*, const int*, int, int, cudaStream_t);
 cudaError_t launch_final_batch(const DemArgs*, int, cudaStream_t);
@@ -122,6 +123,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (d->tile_cap < 0 || d->tile_cap > MAX_TILE_CAP) return LEDDS_ERR_INVALID_ARG;
     if (d->max_particles > 0 && !(p->dem_h > 0.0)) return LEDDS_ERR_INVALID_ARG;
     if (p->skin < 0.0) return LEDDS_ERR_INVALID_ARG;
+    if (p->force_fp32 < 0 || p->force_fp32 > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -356,6 +358,7 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     A.skin = s->p.skin;
     A.ell_max_iter = s->p.ell_max_iter;
     A.ell_tol = s->p.ell_tol;
+    A.force_f32 = s->p.force_fp32;
     A.ccap = s->ccap;
     A.keys = s->keys;
     A.rank = s->rank;
@@ -494,6 +497,7 @@ int ledds_params_default(ledds_params* p) {
     p->dem_h = 0.0;
     p->ell_max_iter = 60;
     p->ell_tol = 1e-6;
+    p->force_fp32 = 1;
     return LEDDS_OK;
 }
 
@@ -952,6 +956,8 @@ struct ledds_batch_s {
     LbmArgs* d_largs[2] = {nullptr, nullptr};
     DemArgs* d_dargs = nullptr;
     int *d_tile_start = nullptr, *d_np = nullptr, *d_poff = nullptr, *d_counter = nullptr;
+    int nchunks = 0;
+    std::vector<BatchChunk> chunks[2];  // PSM launch arguments per batch parity
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
     std::vector<long long> versions;
 };
@@ -973,7 +979,8 @@ static int batch_layout(int nsim, const ledds_dims* dims, const ledds_params* pa
     }
     off = align256(off + 2 * sizeof(LbmArgs) * nsim);
     off = align256(off + sizeof(DemArgs) * nsim);
-    off = align256(off + sizeof(int) * (3 * nsim + 2));
+    const int nchunks = (nsim + BATCH_CHUNK - 1) / BATCH_CHUNK;
+    off = align256(off + sizeof(int) * (3 * nsim + 1 + nchunks));
     *total = off + 256;
     return LEDDS_OK;
 }
@@ -1036,6 +1043,7 @@ int ledds_batch_create(int nsim, const ledds_dims* dims, const ledds_params* par
     b->d_np = b->d_tile_start + nsim + 1;
     b->d_poff = b->d_np + nsim;
     b->d_counter = b->d_poff + nsim;
+    b->nchunks = (nsim + BATCH_CHUNK - 1) / BATCH_CHUNK;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1059,6 +1067,7 @@ int ledds_batch_sim(ledds_batch_t b, int i, ledds_sim_t* out) {
 // restored from a checkpoint may sit on the other population buffer).
 static cudaError_t batch_upload(ledds_batch_s* b) {
     const int n = b->nsim;
+    for (int q = 0; q < 2; ++q) b->chunks[q].assign(b->nchunks, BatchChunk{});
     std::vector<LbmArgs> la(2 * n);
     std::vector<DemArgs> da(n);
     std::vector<int> ts(3 * n + 2, 0);
@@ -1073,6 +1082,17 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
         ts[n + 1 + i] = s->P.n;
         ts[2 * n + 1 + i] = off;
     }
+    for (int q = 0; q < 2; ++q)
+        for (int c = 0; c < b->nchunks; ++c) {
+            BatchChunk& ch = b->chunks[q][c];
+            const int first = c * BATCH_CHUNK, cnt = std::min(BATCH_CHUNK, n - first);
+            ch.nsim = cnt;
+            ch.tile_start[0] = 0;
+            for (int k = 0; k < cnt; ++k) {
+                ch.a[k] = la[q * n + first + k];
+                ch.tile_start[k + 1] = ch.tile_start[k] + b->sims[first + k]->ntiles;
+            }
+        }
     CK(cudaMemcpyAsync(b->d_largs[0], la.data(), sizeof(LbmArgs) * 2 * n, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->d_dargs, da.data(), sizeof(DemArgs) * n, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->d_tile_start, ts.data(), sizeof(int) * (3 * n + 1), cudaMemcpyHostToDevice, b->stream));
@@ -1083,10 +1103,11 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
 }
 
 static cudaError_t batch_enqueue(ledds_batch_s* b, int p, cudaStream_t st) {
-    CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int), st));
+    CK(cudaMemsetAsync(b->d_counter, 0, sizeof(int) * (size_t)b->nchunks, st));
     CK(launch_dem_batch(b->d_dargs, b->d_poff, b->nsim, p, st));
     CK(launch_bin_batch(b->d_largs[p], b->d_np, b->nsim, st));
-    CK(launch_psm_batch(b->d_largs[p], b->d_tile_start, b->nsim, b->d_counter, b->storage, b->nblocks, st));
+    for (int c = 0; c < b->nchunks; ++c)
+        CK(launch_psm_batch(b->chunks[p][c], b->d_counter + c, b->storage, b->nblocks, st));
     CK(launch_final_batch(b->d_dargs, b->nsim, st));
     return cudaSuccess;
 }

@@ -183,72 +183,91 @@ __global__ void k_segsort(DemArgs A) {
 }
 
 // Candidate list of particle i (ascending ids) and its tangential history carried over
-// from the previous list by a merge join (Sec. 3.2.2: look-up in the previous sorted list).
-__global__ void k_candidates(DemArgs A, int ob, int nbuf) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.P.n) return;
+// from the previous list (Sec. 3.2.2: look-up in the previous sorted list). One warp per
+// particle: lane l < 27 scans neighbour cell l (a cell reached twice on a small periodic
+// grid is scanned by its lowest lane only), hits are compacted by ballot into the warp's
+// shared list, each entry is placed by its rank (ids are distinct), and finds its history
+// by binary search in the previous list.
+constexpr int CAND_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * CAND_WARPS) k_candidates(DemArgs A, int ob, int nbuf) {
+    __shared__ int s_list[CAND_WARPS][MAX_CAND_CAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int i = blockIdx.x * CAND_WARPS + wib;
+    if (i >= A.P.n) return;  // uniform across the warp
+    int* list = s_list[wib];
     const double* st = A.P.st[0];
     double ri[3];
     ld3(A, st, SP, i, ri);
     const double bi = A.P.bound[i];
-    int c[3];
-    cell_key(A, ri, c);
-    int lst[MAX_CAND_CAP];
-    int cnt = 0, over = 0;
-    int visited[27];
-    int nvis = 0;
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                int q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
-                bool ok = true;
-                for (int a = 0; a < 3; ++a) {
-                    if (q[a] < 0 || q[a] >= A.gn[a]) {
-                        if (A.per[a]) q[a] = (q[a] + A.gn[a]) % A.gn[a];
-                        else ok = false;
-                    }
-                }
-                if (!ok) continue;
-                int h = q[0] + A.gn[0] * (q[1] + A.gn[1] * q[2]);
-                bool dup = false;
-                for (int m = 0; m < nvis; ++m) dup |= visited[m] == h;
-                if (dup) continue;
-                visited[nvis++] = h;
-                for (uint32_t s = A.cell_start[h]; s < A.cell_start[h + 1]; ++s) {
-                    int j = A.sorted[s];
-                    if (j == i) continue;
-                    double d[3];
-                    for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
-                    double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    double lim = bi + A.P.bound[j] + A.skin;
-                    if (d2 < lim * lim) {
-                        if (cnt < A.ccap) lst[cnt++] = j;
-                        else over = 1;
-                    }
-                }
+    const uint32_t key = A.keys[i];
+    const int c0 = (int)(key % (uint32_t)A.gn[0]);
+    const int c1 = (int)((key / (uint32_t)A.gn[0]) % (uint32_t)A.gn[1]);
+    const int c2 = (int)(key / ((uint32_t)A.gn[0] * (uint32_t)A.gn[1]));
+    int h = -1;
+    if (lane < 27) {
+        int q[3] = {c0 + lane % 3 - 1, c1 + (lane / 3) % 3 - 1, c2 + lane / 9 - 1};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            if (q[a] < 0 || q[a] >= A.gn[a]) {
+                if (A.per[a]) q[a] = (q[a] + A.gn[a]) % A.gn[a];
+                else ok = false;
             }
-    if (over) atomicAdd(&A.status->cand_overflow, 1);
-    for (int m = 1; m < cnt; ++m) {
-        int v = lst[m], j = m - 1;
-        while (j >= 0 && lst[j] > v) {
-            lst[j + 1] = lst[j];
-            --j;
         }
-        lst[j + 1] = v;
+        if (ok) h = q[0] + A.gn[0] * (q[1] + A.gn[1] * q[2]);
     }
+    const unsigned same = __match_any_sync(0xffffffffu, h);
+    if (h >= 0 && __ffs(same) - 1 != lane) h = -1;
+    uint32_t s = 0, e = 0;
+    if (h >= 0) {
+        s = A.cell_start[h];
+        e = A.cell_start[h + 1];
+    }
+    int cnt = 0;
+    const unsigned lower = (1u << lane) - 1u;
+    while (__any_sync(0xffffffffu, s < e)) {
+        bool hit = false;
+        int j = -1;
+        if (s < e) {
+            j = A.sorted[s++];
+            if (j != i) {
+                double d[3];
+                for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
+                double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                double lim = bi + A.P.bound[j] + A.skin;
+                hit = d2 < lim * lim;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, hit);
+        const int pos = cnt + __popc(b & lower);
+        if (hit && pos < A.ccap) list[pos] = j;
+        cnt += __popc(b);
+    }
+    if (cnt > A.ccap) {
+        if (lane == 0) atomicAdd(&A.status->cand_overflow, 1);
+        cnt = A.ccap;
+    }
+    __syncwarp();
     const int* oc = A.cand[ob] + (long long)i * A.ccap;
     const double* oh = A.hist[ob] + (long long)i * A.ccap * 3;
     int* nc = A.cand[nbuf] + (long long)i * A.ccap;
     double* nh = A.hist[nbuf] + (long long)i * A.ccap * 3;
-    int nold = A.ncand[ob][i], p = 0;
-    for (int m = 0; m < cnt; ++m) {
-        int j = lst[m];
-        while (p < nold && oc[p] < j) ++p;
-        bool found = p < nold && oc[p] == j;
-        nc[m] = j;
-        for (int a = 0; a < 3; ++a) nh[3 * m + a] = found ? oh[3 * p + a] : 0.0;
+    const int nold = A.ncand[ob][i];
+    for (int m = lane; m < cnt; m += 32) {
+        const int v = list[m];
+        int r = 0;
+        for (int q = 0; q < cnt; ++q) r += list[q] < v;
+        nc[r] = v;
+        int lo = 0, hi = nold;  // first old entry >= v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (oc[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool found = lo < nold && oc[lo] == v;
+        for (int a = 0; a < 3; ++a) nh[3 * r + a] = found ? oh[3 * lo + a] : 0.0;
     }
-    A.ncand[nbuf][i] = cnt;
+    if (lane == 0) A.ncand[nbuf][i] = cnt;
 }
 
 // ------------------------------------------------------------------------------------
@@ -589,14 +608,279 @@ __device__ void wall_contrib(const DemArgs& A, const double* st, int i, int face
     }
 }
 
+// ------------------------------------------------------------------------------------
+// FP32 contact arithmetic (force_fp32): positions and velocities are differenced in FP64
+// and rounded, the contact predicate is decided in FP64 exactly as in the FP64 path (so
+// contact sets do not change), the spring-dashpot force and torque are evaluated in FP32
+// and summed per particle in FP64. The tangential history stays stored in FP64.
+// ------------------------------------------------------------------------------------
+struct GeoF {
+    float delta;
+    float en[3];
+    float rca[3], rcb[3];
+    float Ra, Rb;
+    bool sphere;
+};
+
+__device__ __forceinline__ void cross3f(const float a[3], const float b[3], float o[3]) {
+    float x = a[1] * b[2] - a[2] * b[1];
+    float y = a[2] * b[0] - a[0] * b[2];
+    float z = a[0] * b[1] - a[1] * b[0];
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+}
+__device__ __forceinline__ float dot3f(const float a[3], const float b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__device__ __forceinline__ float norm3f(const float a[3]) { return sqrtf(dot3f(a, a)); }
+
+__device__ __forceinline__ void geo_to_f(const Geo& g, GeoF& f) {
+    f.delta = (float)g.delta;
+    for (int c = 0; c < 3; ++c) {
+        f.en[c] = (float)g.en[c];
+        f.rca[c] = (float)g.rca[c];
+        f.rcb[c] = (float)g.rcb[c];
+    }
+    f.Ra = (float)g.Ra;
+    f.Rb = (float)g.Rb;
+    f.sphere = g.sphere;
+}
+
+// Sphere pair with dd = r_a - r_b (FP64, minimum image). The FP64 path's predicate
+// (Ra + Rb) - sqrt(|dd|^2) > 0 is decided from num = (Ra + Rb)^2 - |dd|^2 whenever |num|
+// exceeds its rounding error by far, and exactly as written otherwise; the overlap is
+// num / (Ra + Rb + |dd|), free of cancellation.
+__device__ __forceinline__ bool sphere_geo_f(const double dd[3], double Ra, double Rb, GeoF& g) {
+    const double d2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
+    const double S = Ra + Rb;
+    const double S2 = S * S;
+    const double num = S2 - d2;
+    if (fabs(num) <= 1e-10 * S2) {
+        if (!((S - sqrt(d2)) > 0.0)) return false;
+    } else if (!(num > 0.0)) {
+        return false;
+    }
+    const float dist = sqrtf((float)d2);
+    g.delta = (float)num / ((float)S + dist);
+    const float inv = 1.0f / dist;
+    const float ra = (float)Ra, rb = (float)Rb;
+    for (int c = 0; c < 3; ++c) {
+        g.en[c] = (float)dd[c] * inv;
+        g.rca[c] = -ra * g.en[c];
+        g.rcb[c] = rb * g.en[c];
+    }
+    g.Ra = ra;
+    g.Rb = rb;
+    g.sphere = true;
+    return true;
+}
+
+// The spring-dashpot law of spring_dashpot in FP32; dv = v_a - v_b (rounded from FP64).
+__device__ void spring_dashpot_f(const DemArgs& A, const GeoF& g, float Rstar, float mstar, const float dv[3],
+                                 const float wa[3], const float wb[3], float h[3], float F[3], float Ft[3]) {
+    float kn, kt, gn, gt;
+    const float beta = (float)A.beta;
+    if (A.law == LEDDS_LAW_LINEAR) {
+        kn = (float)A.k_n;
+        kt = (float)A.k_t;
+        gn = -2.0f * beta * sqrtf(kn * mstar);
+        gt = -2.0f * beta * sqrtf(kt * mstar);
+    } else {
+        const float sq = sqrtf(Rstar * g.delta);
+        const float Ys = (float)A.Ystar, Gs = (float)A.Gstar;
+        kn = 4.0f / 3.0f * Ys * sq;
+        kt = 8.0f * Gs * sq;
+        const float Sn = 2.0f * Ys * sq;
+        const float St = 8.0f * Gs * sq;
+        gn = -2.0f * 0.91287093f * beta * sqrtf(Sn * mstar);   // 0.91287093 = sqrt(5/6)
+        gt = -2.0f * 0.91287093f * beta * sqrtf(St * mstar);
+    }
+    float ca[3], cb[3], vrel[3];
+    cross3f(wa, g.rca, ca);
+    cross3f(wb, g.rcb, cb);
+    for (int c = 0; c < 3; ++c) vrel[c] = dv[c] + (ca[c] - cb[c]);
+    const float vn = dot3f(vrel, g.en);
+    float vt[3];
+    for (int c = 0; c < 3; ++c) vt[c] = vrel[c] - vn * g.en[c];
+    const float fn = kn * g.delta - gn * vn;
+    const float hn = dot3f(h, g.en);
+    float hp[3];
+    for (int c = 0; c < 3; ++c) hp[c] = h[c] - hn * g.en[c];
+    const float lh = norm3f(h), lp = norm3f(hp);
+    if (lp > 0.0f)
+        for (int c = 0; c < 3; ++c) hp[c] *= lh / lp;
+    const float dt = (float)A.dt;
+    for (int c = 0; c < 3; ++c) h[c] = hp[c] + vt[c] * dt;
+    for (int c = 0; c < 3; ++c) Ft[c] = -kt * h[c] - gt * vt[c];
+    const float lft = norm3f(Ft), lfn = fabsf(fn);
+    const float mu = (float)A.mu;
+    if (lft > mu * lfn) {
+        const float sc = lft > 0.0f ? mu * lfn / lft : 0.0f;
+        for (int c = 0; c < 3; ++c) Ft[c] *= sc;
+        if (kt > 0.0f)
+            for (int c = 0; c < 3; ++c) h[c] = -(Ft[c] + gt * vt[c]) / kt;
+    }
+    for (int c = 0; c < 3; ++c) F[c] = fn * g.en[c] + Ft[c];
+}
+
+// Compensated FP32 sums: a value is the unevaluated pair hi + lo, added with Knuth's
+// TwoSum, so sums of FP32 contact forces keep about 48 significant bits (the FP64 sum of
+// the same terms to within 2^-48) while running on the FP32 pipes. Converted to FP64 once
+// per particle.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    const float hi = __fadd_rn(s, lo);
+    return F2{hi, __fsub_rn(lo, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, float b) { return f2_add(a, F2{b, 0.0f}); }
+
+// pair_contrib with FP32 contact arithmetic (ellipsoid geometry stays FP64).
+__device__ void pair_contrib_f(const DemArgs& A, const double* st, int cb, int i, int m, F2 F[3], F2 M[3]) {
+    const int j = A.cand[cb][(long long)i * A.ccap + m];
+    double* hl = A.hist[cb] + ((long long)i * A.ccap + m) * 3;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    GeoF g;
+    bool hit_;
+    if (A.P.shape[a] == LEDDS_SPHERE && A.P.shape[b] == LEDDS_SPHERE) {
+        double dd[3];
+        for (int c = 0; c < 3; ++c) dd[c] = min_image(A, c, stv(A, st, SP + c, a) - stv(A, st, SP + c, b));
+        hit_ = sphere_geo_f(dd, A.P.radius[a], A.P.radius[b], g);
+    } else {
+        Geo g64;
+        hit_ = pair_geo(A, st, a, b, g64);
+        if (hit_) geo_to_f(g64, g);
+    }
+    if (!hit_) {
+        hl[0] = hl[1] = hl[2] = 0.0;
+        return;
+    }
+    float dv[3], wa[3], wb[3], h[3], Fp[3], Ft[3];
+    for (int c = 0; c < 3; ++c) {
+        dv[c] = (float)(stv(A, st, SV + c, a) - stv(A, st, SV + c, b));
+        wa[c] = (float)stv(A, st, SW + c, a);
+        wb[c] = (float)stv(A, st, SW + c, b);
+        h[c] = (float)hl[c];
+    }
+    const float Rstar = g.Ra * g.Rb / (g.Ra + g.Rb);
+    const float ma = (float)A.P.mass[a], mb = (float)A.P.mass[b];
+    const float mstar = ma * mb / (ma + mb);
+    spring_dashpot_f(A, g, Rstar, mstar, dv, wa, wb, h, Fp, Ft);
+    for (int c = 0; c < 3; ++c) hl[c] = (double)h[c];
+    float Mi[3];
+    if (g.sphere) {
+        float mr[3];
+        cross3f(g.en, Ft, mr);
+        const float Ri = i == a ? g.Ra : g.Rb;
+        for (int c = 0; c < 3; ++c) Mi[c] = -Ri * mr[c];
+    } else if (i == a) {
+        cross3f(g.rca, Fp, Mi);
+    } else {
+        float mF[3] = {-Fp[0], -Fp[1], -Fp[2]};
+        cross3f(g.rcb, mF, Mi);
+    }
+    const float sgn = i == a ? 1.0f : -1.0f;
+    for (int c = 0; c < 3; ++c) {
+        F[c] = f2_add(F[c], sgn * Fp[c]);
+        M[c] = f2_add(M[c], Mi[c]);
+    }
+}
+
+// wall_contrib with FP32 contact arithmetic.
+__device__ void wall_contrib_f(const DemArgs& A, const double* st, int i, int face, F2 F[3], F2 M[3]) {
+    const int ax = face >> 1, side = face & 1;
+    double* wh = A.whist + ((long long)i * 6 + face) * 3;
+    if (A.per[ax]) {
+        wh[0] = wh[1] = wh[2] = 0.0;
+        return;
+    }
+    GeoF g;
+    if (A.P.shape[i] == LEDDS_SPHERE) {
+        const double R = A.P.radius[i];
+        const double r = stv(A, st, SP + ax, i);
+        const double dist = side == 0 ? r - A.lo[ax] : A.hi[ax] - r;
+        const double delta = R - dist;
+        if (!(delta > 0.0)) {
+            wh[0] = wh[1] = wh[2] = 0.0;
+            return;
+        }
+        g.delta = (float)delta;
+        const float Rf = (float)R;
+        for (int c = 0; c < 3; ++c) {
+            g.en[c] = c == ax ? (side == 0 ? 1.0f : -1.0f) : 0.0f;
+            g.rca[c] = -Rf * g.en[c];
+            g.rcb[c] = 0.0f;
+        }
+        g.Ra = Rf;
+        g.sphere = true;
+    } else {
+        Geo g64;
+        if (!wall_geo(A, st, i, face, g64)) {
+            wh[0] = wh[1] = wh[2] = 0.0;
+            return;
+        }
+        geo_to_f(g64, g);
+    }
+    const double* uw = A.uw[ax][side];
+    float dv[3], wi[3], h[3], zero[3] = {0.0f, 0.0f, 0.0f}, Fw[3], Ft[3], Mw[3];
+    for (int c = 0; c < 3; ++c) {
+        dv[c] = (float)(stv(A, st, SV + c, i) - uw[c]);
+        wi[c] = (float)stv(A, st, SW + c, i);
+        h[c] = (float)wh[c];
+    }
+    spring_dashpot_f(A, g, g.Ra, (float)A.P.mass[i], dv, wi, zero, h, Fw, Ft);
+    for (int c = 0; c < 3; ++c) wh[c] = (double)h[c];
+    if (g.sphere) {
+        float mr[3];
+        cross3f(g.en, Ft, mr);
+        for (int c = 0; c < 3; ++c) Mw[c] = -g.Ra * mr[c];
+    } else {
+        cross3f(g.rca, Fw, Mw);
+    }
+    for (int c = 0; c < 3; ++c) {
+        F[c] = f2_add(F[c], Fw[c]);
+        M[c] = f2_add(M[c], Mw[c]);
+    }
+}
+
 // Warp-cooperative contact sum of particle i: lane l evaluates candidate slots l, l+32
-// and wall face l (l < 6); a fixed butterfly sums the lanes (deterministic order).
+// and wall face l (l < 6); a fixed butterfly sums the lanes (deterministic order): in
+// FP64 with FP64 contact arithmetic, in compensated FP32 pairs (converted to FP64 at the
+// end) with FP32 contact arithmetic.
 __device__ void contact_sum_warp(const DemArgs& A, const double* st, int cb, int i, double F[3],
                                  double M[3]) {
     const int lane = threadIdx.x & 31;
-    for (int c = 0; c < 3; ++c) F[c] = M[c] = 0.0;
     const int nc = A.ncand[cb][i];
-    for (int m = lane; m < nc; m += 32) pair_contrib(A, st, cb, i, m, F, M);
+    if (A.force_f32) {
+        F2 f[3], m[3];
+        for (int c = 0; c < 3; ++c) f[c] = m[c] = F2{0.0f, 0.0f};
+        for (int q = lane; q < nc; q += 32) pair_contrib_f(A, st, cb, i, q, f, m);
+        if (lane < 6) wall_contrib_f(A, st, i, lane, f, m);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F2 of{__shfl_xor_sync(0xffffffffu, f[c].hi, off), __shfl_xor_sync(0xffffffffu, f[c].lo, off)};
+                F2 om{__shfl_xor_sync(0xffffffffu, m[c].hi, off), __shfl_xor_sync(0xffffffffu, m[c].lo, off)};
+                // the same operand order on both lanes of a butterfly pair keeps them equal
+                const bool low = (lane & off) == 0;
+                f[c] = low ? f2_add(f[c], of) : f2_add(of, f[c]);
+                m[c] = low ? f2_add(m[c], om) : f2_add(om, m[c]);
+            }
+        for (int c = 0; c < 3; ++c) {
+            F[c] = (double)f[c].hi + (double)f[c].lo;
+            M[c] = (double)m[c].hi + (double)m[c].lo;
+        }
+        return;
+    }
+    for (int c = 0; c < 3; ++c) F[c] = M[c] = 0.0;
+    for (int q = lane; q < nc; q += 32) pair_contrib(A, st, cb, i, q, F, M);
     if (lane < 6) wall_contrib(A, st, i, lane, F, M);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
@@ -629,12 +913,13 @@ __device__ void predict(const DemArgs& A, int k, double r[3], const double v[3],
     }
     double* d1 = d;
     double* d2 = d + 3;
-    double n1 = norm3(d1);
-    for (int a = 0; a < 3; ++a) d1[a] /= n1;
+    // one FP64 division per normalisation (FP64 division is costly on this part)
+    const double i1 = 1.0 / norm3(d1);
+    for (int a = 0; a < 3; ++a) d1[a] *= i1;
     double p = dot3(d2, d1);
     for (int a = 0; a < 3; ++a) d2[a] -= p * d1[a];
-    double n2 = norm3(d2);
-    for (int a = 0; a < 3; ++a) d2[a] /= n2;
+    const double i2 = 1.0 / norm3(d2);
+    for (int a = 0; a < 3; ++a) d2[a] *= i2;
     cross3(d1, d2, d + 6);
     double disp2 = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -653,8 +938,8 @@ __device__ void correct(const DemArgs& A, int k, const double F[3], const double
                         double v[3], double w[3]) {
     const double dt = A.dt;
     double an[3], wb[3], Mb[3], Iw[3], gyr[3], ab[3], al[3];
-    const double m = A.P.mass[k], gf = A.P.gfac[k];
-    for (int a = 0; a < 3; ++a) an[a] = F[a] / m + A.gravity[a] * gf;
+    const double im = 1.0 / A.P.mass[k], gf = A.P.gfac[k];
+    for (int a = 0; a < 3; ++a) an[a] = F[a] * im + A.gravity[a] * gf;
     for (int q = 0; q < 3; ++q) {
         wb[q] = dot3(d + 3 * q, w);
         Mb[q] = dot3(d + 3 * q, M);
@@ -767,43 +1052,53 @@ __global__ void k_final(DemArgs A, int in, int use_hydro) {
 // sum of bounding radii plus the skin, ascending ids).
 // ------------------------------------------------------------------------------------
 __device__ void candidates_direct(const DemArgs& A, int i, int ob, int nbuf) {
+    // one warp: lanes test ids base + lane, so ballot order is ascending id order
+    const int lane = threadIdx.x & 31;
+    const unsigned lower = (1u << lane) - 1u;
     const double* st = A.P.st[0];
     double ri[3];
     ld3(A, st, SP, i, ri);
-    for (int a = 0; a < 3; ++a) A.P.pos_build[(long long)a * A.P.cap + i] = ri[a];
+    if (lane == 0)
+        for (int a = 0; a < 3; ++a) A.P.pos_build[(long long)a * A.P.cap + i] = ri[a];
     const double bi = A.P.bound[i];
     int* nc = A.cand[nbuf] + (long long)i * A.ccap;
-    int cnt = 0, over = 0;
-    for (int j = 0; j < A.P.n; ++j) {  // ascending ids: the list comes out sorted
-        if (j == i) continue;
-        double d[3];
-        for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
-        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        double lim = bi + A.P.bound[j] + A.skin;
-        if (d2 < lim * lim) {
-            if (cnt < A.ccap) nc[cnt++] = j;
-            else over = 1;
+    int cnt = 0;
+    for (int base = 0; base < A.P.n; base += 32) {
+        const int j = base + lane;
+        bool hit = false;
+        if (j < A.P.n && j != i) {
+            double d[3];
+            for (int a = 0; a < 3; ++a) d[a] = min_image(A, a, ri[a] - stv(A, st, SP + a, j));
+            double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            double lim = bi + A.P.bound[j] + A.skin;
+            hit = d2 < lim * lim;
         }
+        const unsigned b = __ballot_sync(0xffffffffu, hit);
+        const int pos = cnt + __popc(b & lower);
+        if (hit && pos < A.ccap) nc[pos] = j;
+        cnt += __popc(b);
     }
-    if (over) atomicAdd(&A.status->cand_overflow, 1);
+    if (cnt > A.ccap) {
+        if (lane == 0) atomicAdd(&A.status->cand_overflow, 1);
+        cnt = A.ccap;
+    }
+    __syncwarp();
     const int* oc = A.cand[ob] + (long long)i * A.ccap;
     const double* oh = A.hist[ob] + (long long)i * A.ccap * 3;
     double* nh = A.hist[nbuf] + (long long)i * A.ccap * 3;
-    int nold = A.ncand[ob][i], p = 0;
-    for (int m = 0; m < cnt; ++m) {
-        int j = nc[m];
-        while (p < nold && oc[p] < j) ++p;
-        bool found = p < nold && oc[p] == j;
-        for (int a = 0; a < 3; ++a) nh[3 * m + a] = found ? oh[3 * p + a] : 0.0;
+    const int nold = A.ncand[ob][i];
+    for (int m = lane; m < cnt; m += 32) {
+        const int v = nc[m];
+        int lo = 0, hi = nold;  // first old entry >= v
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (oc[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        const bool found = lo < nold && oc[lo] == v;
+        for (int a = 0; a < 3; ++a) nh[3 * m + a] = found ? oh[3 * lo + a] : 0.0;
     }
-    A.ncand[nbuf][i] = cnt;
-}
-
-__device__ void contact_sum_serial(const DemArgs& A, const double* st, int cb, int i, double F[3], double M[3]) {
-    for (int c = 0; c < 3; ++c) F[c] = M[c] = 0.0;
-    const int nc = A.ncand[cb][i];
-    for (int m = 0; m < nc; ++m) pair_contrib(A, st, cb, i, m, F, M);
-    for (int face = 0; face < 6; ++face) wall_contrib(A, st, i, face, F, M);
+    if (lane == 0) A.ncand[nbuf][i] = cnt;
 }
 
 __global__ void k_dem_batch(const DemArgs* args, const int* poff, int batch_parity) {
@@ -812,7 +1107,8 @@ __global__ void k_dem_batch(const DemArgs* args, const int* poff, int batch_pari
     if (n == 0) return;  // uniform across the CTA
     const int p = batch_parity ^ poff[blockIdx.x];  // this member's buffer parity
     const int cb = p ^ 1, nsub = A.n_sub;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) candidates_direct(A, k, p, cb);
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int k = warp; k < n; k += nwarps) candidates_direct(A, k, p, cb);
     __syncthreads();
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         double r[3], v[3], w[3], d[9], acc[3];
@@ -825,20 +1121,24 @@ __global__ void k_dem_batch(const DemArgs* args, const int* poff, int batch_pari
     __syncthreads();
     for (int sub = 1; sub <= nsub; ++sub) {
         const int in = (sub - 1) & 1, out = sub & 1;
-        for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        for (int k = warp; k < n; k += nwarps) {
             double F[3], M[3];
-            contact_sum_serial(A, A.P.st[in], cb, k, F, M);
-            for (int a = 0; a < 3; ++a) {
-                A.P.Fc[(long long)a * A.P.cap + k] = F[a];
-                A.P.Mc[(long long)a * A.P.cap + k] = M[a];
-            }
-            if (sub == nsub) continue;  // the last substep's velocities wait for the fluid
+            contact_sum_warp(A, A.P.st[in], cb, k, F, M);
+            if (lane == 0)
+                for (int a = 0; a < 3; ++a) {
+                    A.P.Fc[(long long)a * A.P.cap + k] = F[a];
+                    A.P.Mc[(long long)a * A.P.cap + k] = M[a];
+                }
+        }
+        __syncthreads();
+        if (sub == nsub) break;  // the last substep's velocities wait for the fluid
+        for (int k = threadIdx.x; k < n; k += blockDim.x) {
             double r[3], v[3], w[3], d[9], Ft[3], Mt[3], acc[3];
             load_state(A, A.P.st[in], k, r, v, w, d);
             for (int a = 0; a < 3; ++a) {
                 long long o = (long long)a * A.P.cap + k;
-                Ft[a] = F[a] + A.P.Fhp[o];
-                Mt[a] = M[a] + A.P.Mhp[o];
+                Ft[a] = A.P.Fc[o] + A.P.Fhp[o];
+                Mt[a] = A.P.Mc[o] + A.P.Mhp[o];
             }
             correct(A, k, Ft, Mt, d, v, w);
             for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
@@ -874,7 +1174,7 @@ __global__ void k_final_batch(const DemArgs* args, int use_hydro_mask) {
 }
 
 cudaError_t launch_dem_batch(const DemArgs* args, const int* poff, int nsim, int p, cudaStream_t s) {
-    k_dem_batch<<<nsim, 128, 0, s>>>(args, poff, p);
+    k_dem_batch<<<nsim, 256, 0, s>>>(args, poff, p);
     return cudaGetLastError();
 }
 
@@ -932,7 +1232,7 @@ cudaError_t launch_rebuild(const DemArgs& A, int ob, int nb, uint32_t* scan_part
     if (e != cudaSuccess) return e;
     k_scatter<<<nblk(n, 128), 128, 0, s>>>(A);
     k_segsort<<<nblk(A.G, 128), 128, 0, s>>>(A);
-    k_candidates<<<nblk(n, 64), 64, 0, s>>>(A, ob, nb);
+    k_candidates<<<nblk(n, CAND_WARPS), 32 * CAND_WARPS, 0, s>>>(A, ob, nb);
     *launches += 7;
     return cudaGetLastError();
 }
@@ -948,7 +1248,7 @@ cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
 cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
     k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
-    if (do_step) k_integrate<<<nblk(A.P.n, 64), 64, 0, s>>>(A, in, out);
+    if (do_step) k_integrate<<<nblk(A.P.n, 32), 32, 0, s>>>(A, in, out);
     return cudaGetLastError();
 }
 

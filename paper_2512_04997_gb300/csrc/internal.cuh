@@ -152,6 +152,15 @@ struct LbmArgs {
     DevStatus* status;
 };
 
+// Arguments of one batched PSM launch: up to BATCH_CHUNK members and the prefix sums of
+// their tile counts (passed by value: 64 x 456 bytes fit the 32 KB parameter limit).
+constexpr int BATCH_CHUNK = 64;
+struct BatchChunk {
+    LbmArgs a[BATCH_CHUNK];
+    int tile_start[BATCH_CHUNK + 1];
+    int nsim;
+};
+
 struct DemArgs {
     DevParticles P;
     // domain
@@ -171,6 +180,7 @@ struct DemArgs {
     double skin;
     int ell_max_iter;
     double ell_tol;
+    int force_f32;  // FP32 contact arithmetic, FP64 sums
     // lists
     int ccap;
     uint32_t* keys;

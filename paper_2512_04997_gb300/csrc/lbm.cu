@@ -778,23 +778,55 @@ struct ReadAll<SS, 19> {
     static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const uint32_t*, float*) {}
 };
 
+// c . v for a lattice vector c with components in {-1, 0, 1} known at compile time (no
+// multiplications by 0 or +/-1 left to run time), and c^T Q c for a symmetric Q.
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cdot(float x, float y, float z) {
+    float r = 0.0f;
+    if constexpr (CXv != 0) r = CXv > 0 ? x : -x;
+    if constexpr (CYv != 0) r = CXv != 0 ? (CYv > 0 ? r + y : r - y) : (CYv > 0 ? y : -y);
+    if constexpr (CZv != 0) r = (CXv != 0 || CYv != 0) ? (CZv > 0 ? r + z : r - z) : (CZv > 0 ? z : -z);
+    return r;
+}
+
+// Solid terms of one node summed over its (at most two) solids k, with d_k = u - u_k:
+//   Bs = sum B_k, D = sum B_k d_k, Q = sum B_k d_k d_k^T, S = sum B_k (u^2 - u_k^2).
+// With e_k = c.d_k, sum_k B_k Omega^s_{i,k} needs only c.D and c^T Q c:
+//   sum_k B_k (geq_i(rho,u) - geq_i(rho,u_k)) = t rho (3 c.D + 9 (c.u)(c.D) - 4.5 c^T Q c - 1.5 S)
+// (from (c.u)^2 - (c.u_k)^2 = 2 (c.u) e_k - e_k^2), the antisymmetric part being 3 t rho c.D.
+struct SolidSums {
+    float Bs, Dx, Dy, Dz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, S;
+};
+
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cqc(const SolidSums& m) {
+    float r = 0.0f;
+    if constexpr (CXv != 0) r += m.Qxx;
+    if constexpr (CYv != 0) r += m.Qyy;
+    if constexpr (CZv != 0) r += m.Qzz;
+    if constexpr (CXv != 0 && CYv != 0) r += (CXv * CYv > 0 ? 2.0f : -2.0f) * m.Qxy;
+    if constexpr (CXv != 0 && CZv != 0) r += (CXv * CZv > 0 ? 2.0f : -2.0f) * m.Qxz;
+    if constexpr (CYv != 0 && CZv != 0) r += (CYv * CZv > 0 ? 2.0f : -2.0f) * m.Qyz;
+    return r;
+}
+
 // Collision and store of the direction pair (I, I+1) (c_{I+1} = -c_I). On entry g holds
 // the pulled populations of the pair; the symmetric and antisymmetric parts of the
-// equilibrium and of geq(rho,u) - geq(rho,u_k) are shared by the two directions:
+// equilibrium and of the solid terms are shared by the two directions:
 //   geq_{I,I+1} = t (base + 4.5 rho cu^2 +/- 3 rho cu)
-//   Omega^s_I = neq_{I+1} - neq_I - t rho ( 3 c.(u-u_k) + 4.5 (cu^2 - cuk^2) - 1.5 (u^2 - u_k^2))
-//   Omega^s_{I+1} = neq_I - neq_{I+1} - t rho (-3 c.(u-u_k) + 4.5 (cu^2 - cuk^2) - 1.5 (...))
+//   sum_k B_k Omega^s_I     = Bs (neq_{I+1} - neq_I) - (dsym + dasym)
+//   sum_k B_k Omega^s_{I+1} = Bs (neq_I - neq_{I+1}) - (dsym - dasym)
+// with dsym = t rho (9 cu c.D - 4.5 c^T Q c - 1.5 S), dasym = 3 t rho c.D (SolidSums).
+// SOLID is uniform across the warp: false when no lane of the warp has a solid.
 // The force sum over the directions is not accumulated here: see solid_force.
-template <class SS, int I>
+template <class SS, int I, bool SOLID>
 struct CollidePairs {
     static __device__ __forceinline__ void run(float* g, float rho, float ux, float uy, float uz, float base,
-                                               const LbmArgs& a, float Fu, float force_w, float keep, int ns,
-                                               SolidAt& q0, SolidAt& q1, float d0x, float d0y, float d0z,
-                                               float d0s, float d1x, float d1y, float d1z, float d1s,
-                                               typename SS::T* dst, bool valid) {
+                                               const LbmArgs& a, float Fu, float force_w, float keep,
+                                               const SolidSums& m, typename SS::T* dst, bool valid) {
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         constexpr float t = TW(I);
-        const float cu = (float)cx * ux + (float)cy * uy + (float)cz * uz;
+        const float cu = cdot<cx, cy, cz>(ux, uy, uz);
         const float cu2 = cu * cu;
         const float sym = base + 4.5f * rho * cu2;
         const float asym = 3.0f * rho * cu;
@@ -803,44 +835,33 @@ struct CollidePairs {
         float o0 = t * (sym + asym) + keep * n0;
         float o1 = t * (sym - asym) + keep * n1;
         if (a.has_force) {
-            const float cF = (float)cx * a.F[0] + (float)cy * a.F[1] + (float)cz * a.F[2];
+            const float cF = cdot<cx, cy, cz>(a.F[0], a.F[1], a.F[2]);
             // Guo term t [3 (c.F - u.F) + 9 (c.u)(c.F)]: c -> -c flips only 3 c.F
             const float fs = force_w * t * (-3.0f * Fu + 9.0f * cu * cF);
             const float fa = force_w * t * 3.0f * cF;
             o0 += fs + fa;
             o1 += fs - fa;
         }
-        if (ns > 0) {
-            const float cuk = cu - ((float)cx * d0x + (float)cy * d0y + (float)cz * d0z);
-            const float dsym = t * rho * (4.5f * (cu2 - cuk * cuk) - 1.5f * d0s);
-            const float dasym = t * rho * 3.0f * (cu - cuk);
-            const float w0 = n1 - n0 - (dsym + dasym);
-            const float w1 = n0 - n1 - (dsym - dasym);
-            o0 += q0.B * w0;
-            o1 += q0.B * w1;
-        }
-        if (ns > 1) {
-            const float cuk = cu - ((float)cx * d1x + (float)cy * d1y + (float)cz * d1z);
-            const float dsym = t * rho * (4.5f * (cu2 - cuk * cuk) - 1.5f * d1s);
-            const float dasym = t * rho * 3.0f * (cu - cuk);
-            const float w0 = n1 - n0 - (dsym + dasym);
-            const float w1 = n0 - n1 - (dsym - dasym);
-            o0 += q1.B * w0;
-            o1 += q1.B * w1;
+        if constexpr (SOLID) {
+            const float cD = cdot<cx, cy, cz>(m.Dx, m.Dy, m.Dz);
+            const float trho = t * rho;
+            const float dsym = trho * (9.0f * cu * cD - 4.5f * cqc<cx, cy, cz>(m) - 1.5f * m.S);
+            const float dasym = 3.0f * trho * cD;
+            const float x = m.Bs * (n1 - n0);
+            o0 += x - (dsym + dasym);
+            o1 += -x - (dsym - dasym);
         }
         if (valid) {
             SS::store(dst + a.pN[I], o0, a.scale);
             SS::store(dst + a.pN[I + 1], o1, a.scale);
         }
-        CollidePairs<SS, I + 2>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, ns, q0, q1, d0x, d0y,
-                                     d0z, d0s, d1x, d1y, d1z, d1s, dst, valid);
+        CollidePairs<SS, I + 2, SOLID>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, dst, valid);
     }
 };
-template <class SS>
-struct CollidePairs<SS, 19> {
+template <class SS, bool SOLID>
+struct CollidePairs<SS, 19, SOLID> {
     static __device__ __forceinline__ void run(float*, float, float, float, float, float, const LbmArgs&, float,
-                                               float, float, int, SolidAt&, SolidAt&, float, float, float,
-                                               float, float, float, float, float, typename SS::T*, bool) {}
+                                               float, float, const SolidSums&, typename SS::T*, bool) {}
 };
 
 // ------------------------------------------------------------------------------------
@@ -944,22 +965,37 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         const float keep = 1.0f - (1.0f - Btot) * omega;
         const float force_w = (1.0f - Btot) * a.guo_pref;
         const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
-        // solid k: du = u - u_k, dusq = u^2 - u_k^2, and rho t_i folded later
+        // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
         const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
         const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
 
-        // non-equilibrium parts in place: g_i <- g_i - geq_i(rho, u)
-        {
-            const float sym0 = base;  // rest direction: c = 0
-            g[0] -= TW(0) * sym0;
+        // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
+        g[0] -= TW(0) * base;
+        SolidSums m;
+        const bool any_solid = __any_sync(FULL, t.ns > 0);
+        if (any_solid) {
+            const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
+            const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
+            m.Bs = q0.B + q1.B;
+            m.Dx = b0x + b1x;
+            m.Dy = b0y + b1y;
+            m.Dz = b0z + b1z;
+            m.Qxx = b0x * d0x + b1x * d1x;
+            m.Qyy = b0y * d0y + b1y * d1y;
+            m.Qzz = b0z * d0z + b1z * d1z;
+            m.Qxy = b0x * d0y + b1x * d1y;
+            m.Qxz = b0x * d0z + b1x * d1z;
+            m.Qyz = b0y * d0z + b1y * d1z;
+            m.S = q0.B * d0s + q1.B * d1s;
+            CollidePairs<SS, 1, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, pout + pl.cell, valid);
+        } else {
+            m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
+            CollidePairs<SS, 1, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, pout + pl.cell, valid);
         }
-        CollidePairs<SS, 1>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, t.ns, q0, q1,
-                                 d0x, d0y, d0z, d0s, d1x, d1y, d1z, d1s, pout + pl.cell, valid);
-        {   // rest direction: Omega^s_0 = -(geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho dusq_k
+        {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
             float out0 = TW(0) * base + keep * g[0];
             if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
-            if (t.ns > 0) out0 += q0.B * (1.5f * TW(0) * rho * d0s);
-            if (t.ns > 1) out0 += q1.B * (1.5f * TW(0) * rho * d1s);
+            out0 += 1.5f * TW(0) * rho * m.S;
             if (valid) SS::store(pout + pl.cell, out0, a.scale);
         }
 
@@ -1013,25 +1049,23 @@ __global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmAr
 }
 
 // Batched form: persistent CTAs take (simulation, tile) work items from a queue, so many
-// simulations of uneven sizes advance in one launch with balanced load. The simulation's
-// parameters are copied to shared memory for each item.
-constexpr size_t ARGS_SMEM = (sizeof(LbmArgs) + 15) & ~(size_t)15;
-
+// simulations of uneven sizes advance in one launch with balanced load. The members'
+// arguments travel in the launch's parameter block (read-only for the whole launch, like
+// the single-simulation kernel's argument), up to BATCH_CHUNK members per launch.
 template <int STORE>
-__global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const LbmArgs* args,
-                                                                          const int* tile_start, int nsim,
+__global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const __grid_constant__ BatchChunk P,
                                                                           int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
-    LbmArgs& sa = *reinterpret_cast<LbmArgs*>(smem);
     __shared__ int s_item, s_sim;
-    const int total = tile_start[nsim];
+    const int nsim = P.nsim;
+    const int total = P.tile_start[nsim];
     for (;;) {
         if (threadIdx.x == 0) {
             int item = atomicAdd(counter, 1);
             int lo = 0, hi = nsim - 1;
             while (lo < hi) {  // last simulation whose first tile is <= item
                 int mid = (lo + hi + 1) >> 1;
-                if (tile_start[mid] <= item) lo = mid;
+                if (P.tile_start[mid] <= item) lo = mid;
                 else hi = mid - 1;
             }
             s_item = item;
@@ -1041,13 +1075,10 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const LbmArgs* arg
         const int item = s_item;
         if (item >= total) break;
         const int sim = s_sim;
-        const int* src = reinterpret_cast<const int*>(args + sim);
-        int* dst = reinterpret_cast<int*>(&sa);
-        for (int i = threadIdx.x; i < (int)(sizeof(LbmArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
-        __syncthreads();
-        const int t = item - tile_start[sim];
-        const int bx = t % sa.ntx, by = (t / sa.ntx) % sa.nty, bz = t / (sa.ntx * sa.nty);
-        psm_tile<STORE>(sa, bx, by, bz, smem + ARGS_SMEM);
+        const LbmArgs& a = P.a[sim];
+        const int t = item - P.tile_start[sim];
+        const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
+        psm_tile<STORE>(a, bx, by, bz, smem);
         __syncthreads();
     }
 }
@@ -1183,24 +1214,22 @@ cudaError_t launch_psm(const LbmArgs& a, int store, cudaStream_t s) {
 }
 
 template <int STORE>
-static cudaError_t launch_psm_batch_t(const LbmArgs* args, const int* tile_start, int nsim, int* counter,
-                                      int nblocks, cudaStream_t s) {
+static cudaError_t launch_psm_batch_t(const BatchChunk& P, int* counter, int nblocks, cudaStream_t s) {
     static bool configured = false;
-    const size_t smem = ARGS_SMEM + psm_smem_bytes();
+    const size_t smem = psm_smem_bytes();
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k_psm_batch<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm_batch<STORE><<<nblocks, PSM_THREADS, smem, s>>>(args, tile_start, nsim, counter);
+    k_psm_batch<STORE><<<nblocks, PSM_THREADS, smem, s>>>(P, counter);
     return cudaGetLastError();
 }
 
-cudaError_t launch_psm_batch(const LbmArgs* args, const int* tile_start, int nsim, int* counter, int store,
-                             int nblocks, cudaStream_t s) {
-    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32>(args, tile_start, nsim, counter, nblocks, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16>(args, tile_start, nsim, counter, nblocks, s);
-    return launch_psm_batch_t<LEDDS_STORE_BF16>(args, tile_start, nsim, counter, nblocks, s);
+cudaError_t launch_psm_batch(const BatchChunk& P, int* counter, int store, int nblocks, cudaStream_t s) {
+    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32>(P, counter, nblocks, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16>(P, counter, nblocks, s);
+    return launch_psm_batch_t<LEDDS_STORE_BF16>(P, counter, nblocks, s);
 }
 
 cudaError_t launch_bin_batch(const LbmArgs* args, const int* np, int nsim, cudaStream_t s) {

@@ -38,7 +38,8 @@ class ledds_params(C.Structure):
                 ("gravity", C.c_double * 3), ("k_n", C.c_double), ("k_t", C.c_double),
                 ("young", C.c_double), ("poisson", C.c_double), ("restitution", C.c_double),
                 ("friction", C.c_double), ("skin", C.c_double), ("dem_h", C.c_double),
-                ("ell_max_iter", C.c_int), ("ell_tol", C.c_double)]
+                ("ell_max_iter", C.c_int), ("ell_tol", C.c_double),
+                ("force_fp32", C.c_int)]
 
 
 class ledds_particle(C.Structure):
