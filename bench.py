@@ -190,6 +190,108 @@ def ensemble_measure(args, device, stream):
             "launches_per_step": 4, "status": bad}
 
 
+def settling_measure(device, stream):
+    """The single settling sphere (32x32x64, walls, subdivision fractions) over its 2000
+    steps: microseconds per coupled step (65,536 cells: L2-resident, latency-bound)."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    w = W.settling_sphere(steps=2000)
+    s = ledds.from_workload(w, device=device)
+    s.step(200)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(w.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.status()
+    s.close()
+    return {"workload": "settling sphere 32x32x64, R 4, density ratio 2.5, subdivision fractions, n_sub 1",
+            "steps": w.steps, "us_per_step": 1e3 * ms / w.steps,
+            "value": w.ncell * w.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "launches_per_step": st["launches_per_step"]}
+
+
+def granular_measure(device, stream, steps=10000, sample=100):
+    """DEM only: 1e5 spheres (radii U[0.8, 1.2]) settling under gravity in a walled
+    120x120x240 box over 10,000 steps, all timed. Contacts per second = sum over steps of
+    the contact count / time; the counts come from a replay of the same (deterministic)
+    run, read every `sample` steps."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    w = W.granular_box(steps=steps)
+    s = ledds.from_workload(w, device=device)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.status()
+    s.close()
+    r = ledds.from_workload(w, device=device)
+    total = 0
+    counts = []
+    for k in range(steps // sample):
+        r.step(sample)
+        c = len(r.pairs())
+        counts.append(c)
+        total += c * sample
+    r.close()
+    return {"workload": "granular box, 1e5 spheres R U[0.8,1.2], 120x120x240 walled box, linear law, "
+                        "mu 0.4, e 0.7, g 2e-6, 10,000 steps from a jittered lattice",
+            "steps": steps, "ms_per_step": ms / steps, "value": total / (ms * 1e-3), "unit": "contacts/s",
+            "contacts_final": counts[-1] if counts else 0, "contacts_mean": total / steps,
+            "status": {k: st[k] for k in ("cand_overflow", "skin_violation", "nan_detected")}}
+
+
+def ellipsoid_measure(args, device, stream):
+    """Prolate ellipsoids (semi-axes 6, 2, 2) in shear, 384x384x192, 2e4 particles at
+    random orientations, subdivision solid fractions, common-normal contacts, n_sub 10:
+    MLUPS with FP32 and BF16 storage on the same workload, BF16 field error against FP32,
+    and the event-timed stage split of each."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    t0 = time.perf_counter()
+    w = W.ellipsoid_shear()
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"{w.name}: semi-axes (6,2,2), random orientations, shear rate 1e-4, "
+                       "subdivision fractions, common-normal contacts, n_sub 10",
+           "generate_s": gen_s, "cells": w.ncell, "particles": w.n}
+    u_ref = None
+    for sto in ("f32", "bf16"):
+        s = ledds.from_workload(w, device=device, storage=sto)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, u = s.fields()
+        s.set_profiling(True)
+        s.step(min(args.steps, 10))
+        sm_, ps_, _ = s.read_profile()
+        st = s.status()
+        rec = {"value": w.ncell * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+               "ms_per_step": ms / args.steps,
+               "stages_ms_per_step": {k: v / ps_ for k, v in zip(STAGES, sm_)},
+               "status": {k: st[k] for k in ("tile_overflow", "cand_overflow", "skin_violation",
+                                             "ell_nonconverged", "nan_detected", "solids_overflow")}}
+        if u_ref is None:
+            u_ref = u
+        else:
+            rec["field_error_vs_f32"] = float((u - u_ref).abs().max() / u_ref.abs().max())
+        out[sto] = rec
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    out["bf16_speedup_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
+    return out
+
+
 def oracle_sample(steps):
     """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
     slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps."""
@@ -348,6 +450,9 @@ def main():
 
     if not args.no_variants:
         variants["ensemble"] = ensemble_measure(args, f"cuda:{local}", stream)
+        variants["settling_sphere"] = settling_measure(f"cuda:{local}", stream)
+        variants["granular_dem"] = granular_measure(f"cuda:{local}", stream)
+        variants["ellipsoid_shear"] = ellipsoid_measure(args, f"cuda:{local}", stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -483,17 +483,23 @@ void or_voxelize(or_sim* s, double* beta2, int* id2, int* nsolid) {
 /* ------------------------------------------------------------------------------------ */
 
 /* One cell's collision with partially saturated solids, Eqs. (psm1), (lbePS):
- *   f*_i = f_i + (1 - B_tot) Omega^BGK_i + sum_k B_k Omega^s_{i,k}
- * with Omega^BGK from Eq. (BGK), the solid operator
+ *   f*_i = f_i + (1 - B_tot) Omega^fluid_i + sum_k B_k Omega^s_{i,k}
+ * with Omega^fluid the BGK operator, Eq. (BGK), or the TRT operator, Eq. (TRT):
+ *   f+_i = (f_i + f_ibar)/2, f-_i = (f_i - f_ibar)/2 (Eq. trt_populations), the same split
+ *   of f^eq, Omega^TRT_i = -(1/tau+) (f+_i - feq+_i) - (1/tau-) (f-_i - feq-_i),
+ *   tau+ = tau and 1/tau- = 8 (2 - 1/tau+) / (8 - 1/tau+);
+ * the solid operator
  *   Omega^s_{i,k} = [f_ibar - f^eq_ibar(rho,u)] - [f_i - f^eq_i(rho,u_k)],
  * B_tot = min(sum_k B_k, 1) (Eq. btot) and the hydrodynamic force and torque of
  * Eqs. (forceSF), (torqueSF) for this cell (dx^3/dt = 1 in lattice units):
  *   F_k = -B_k sum_i Omega^s_{i,k} c_i,  M_k = -B_k arm_k x sum_i Omega^s_{i,k} c_i.
  * The paper does not renormalise B_k when their sum exceeds one; reading: as written.
- * A fluid body force (not part of the paper; Guo forcing) adds
- *   (1 - B_tot) (1 - 1/(2 tau)) t_i [3 (c_i - u) + 9 (c_i.u) c_i] . F.
+ * A fluid body force (not part of the paper; Guo forcing) adds (1 - B_tot) times
+ *   BGK: (1 - 1/(2 tau)) t_i [3 (c_i - u) + 9 (c_i.u) c_i] . F,
+ *   TRT: the part even in c_i, t_i [-3 u + 9 (c_i.u) c_i] . F, times (1 - 1/(2 tau+)) and
+ *        the part odd in c_i, t_i 3 c_i . F, times (1 - 1/(2 tau-)) (reading).
  * B[k], uk[3k..], arm[3k..] describe the ns <= 2 solids. */
-void or_cell_collide(const double f[19], double tau, const double force[3], int ns,
+void or_cell_collide(const double f[19], double tau, int collision, const double force[3], int ns,
                      const double* B, const double* uk, const double* arm,
                      double fstar[19], double* Fk, double* Mk) {
     double rho, u[3];
@@ -503,15 +509,31 @@ void or_cell_collide(const double f[19], double tau, const double force[3], int 
     double Btot = 0.0;
     for (int k = 0; k < ns; ++k) Btot += B[k];
     if (Btot > 1.0) Btot = 1.0;
+    const double wp = 1.0 / tau;                       /* 1/tau+ */
+    const double wm = 8.0 * (2.0 - wp) / (8.0 - wp);   /* 1/tau- */
     double fs[19];
     for (int i = 0; i < 19; ++i) {
-        double om_bgk = -(1.0 / tau) * (f[i] - feq[i]);
+        const int o = OPP(i);
+        double om;
+        if (collision == OR_COLLIDE_TRT) {
+            const double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+            const double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+            om = -wp * (fp - ep) - wm * (fm - em);
+        } else {
+            om = -(1.0 / tau) * (f[i] - feq[i]);
+        }
         double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
-        double guo = 0.0;
-        for (int a = 0; a < 3; ++a)
-            guo += (3.0 * (CV[i][a] - u[a]) + 9.0 * cu * CV[i][a]) * force[a];
-        guo *= (1.0 - 0.5 / tau) * TW(i);
-        fs[i] = f[i] + (1.0 - Btot) * (om_bgk + guo);
+        double even = 0.0, odd = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            even += (-3.0 * u[a] + 9.0 * cu * CV[i][a]) * force[a];
+            odd += 3.0 * CV[i][a] * force[a];
+        }
+        double guo;
+        if (collision == OR_COLLIDE_TRT)
+            guo = TW(i) * ((1.0 - 0.5 * wp) * even + (1.0 - 0.5 * wm) * odd);
+        else
+            guo = TW(i) * (1.0 - 0.5 / tau) * (even + odd);
+        fs[i] = f[i] + (1.0 - Btot) * (om + guo);
     }
     for (int k = 0; k < ns; ++k) {
         double feqk[19];
@@ -573,7 +595,7 @@ void or_lbm_psm_step(or_sim* s) {
                     for (int a = 0; a < 3; ++a) uk[3 * m + a] = s->vel[3 * k + a] + wxr[a];
                 }
                 double fstar[19];
-                or_cell_collide(f, s->p.tau, s->p.fluid_force, ns, B, uk, arm, fstar, Fk, Mk);
+                or_cell_collide(f, s->p.tau, s->p.collision, s->p.fluid_force, ns, B, uk, arm, fstar, Fk, Mk);
                 for (int m = 0; m < ns; ++m) {
                     int k = cs[c].id[m];
                     for (int a = 0; a < 3; ++a) {

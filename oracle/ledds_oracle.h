@@ -24,6 +24,7 @@ extern "C" {
 enum { OR_SPHERE = 0, OR_ELLIPSOID = 1 };
 enum { OR_VOXEL_DISTANCE = 0, OR_VOXEL_SUBDIV = 1 };
 enum { OR_LAW_LINEAR = 0, OR_LAW_HERTZ = 1 };
+enum { OR_COLLIDE_BGK = 0, OR_COLLIDE_TRT = 1 };
 
 typedef struct {
     double tau;             /* BGK relaxation time, Eq. (tau)                                */
@@ -41,6 +42,7 @@ typedef struct {
     double dem_h;           /* requested DEM grid spacing (>= largest particle diameter)      */
     int ell_max_iter;       /* common-normal iteration cap (Sec. 2.1)                         */
     double ell_tol;         /* common-normal convergence tolerance, relative to min semi-axis */
+    int collision;          /* OR_COLLIDE_BGK (Eq. BGK) or OR_COLLIDE_TRT (Eq. TRT)            */
 } or_params;
 
 typedef struct or_sim or_sim;
@@ -87,7 +89,7 @@ void or_contact_forces(or_sim* s, double dt);                 /* Fc, Mc at curre
 int  or_subdiv_count(const double rel[3], int shape, double radius, const double semi[3],
                      const double triad[9], int n);
 double or_beta_distance(const double rel[3], double radius);
-void or_cell_collide(const double f[19], double tau, const double force[3], int ns,
+void or_cell_collide(const double f[19], double tau, int collision, const double force[3], int ns,
                      const double* B, const double* uk, const double* arm,
                      double fstar[19], double* Fk, double* Mk);
 int  or_ellipsoid_contact(const double ri[3], const double Ri[9], const double si[3],

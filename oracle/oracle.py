@@ -14,6 +14,7 @@ from . import build as _build
 SPHERE, ELLIPSOID = 0, 1
 VOXEL_DISTANCE, VOXEL_SUBDIV = 0, 1
 LAW_LINEAR, LAW_HERTZ = 0, 1
+COLLIDE_BGK, COLLIDE_TRT = 0, 1
 
 
 class Params(C.Structure):
@@ -35,6 +36,7 @@ class Params(C.Structure):
         ("dem_h", C.c_double),
         ("ell_max_iter", C.c_int),
         ("ell_tol", C.c_double),
+        ("collision", C.c_int),
     ]
 
 
@@ -76,7 +78,7 @@ def lib():
         L.or_subdiv_count.argtypes = [dp, C.c_int, C.c_double, dp, dp, C.c_int]
         L.or_beta_distance.restype = C.c_double
         L.or_beta_distance.argtypes = [dp, C.c_double]
-        L.or_cell_collide.argtypes = [dp, C.c_double, dp, C.c_int, dp, dp, dp, dp, dp, dp]
+        L.or_cell_collide.argtypes = [dp, C.c_double, C.c_int, dp, C.c_int, dp, dp, dp, dp, dp, dp]
         L.or_ellipsoid_contact.restype = C.c_int
         L.or_ellipsoid_contact.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_double,
                                            dp, dp, dp, dp, dp, ip]
@@ -102,6 +104,7 @@ def default_params(**kw) -> Params:
     p.dem_h = 1.0
     p.ell_max_iter = 60
     p.ell_tol = 1e-6
+    p.collision = COLLIDE_BGK
     for k, v in kw.items():
         if k in ("fluid_force", "gravity"):
             getattr(p, k)[:] = list(v)
@@ -254,7 +257,7 @@ def beta_distance(rel, radius):
     return lib().or_beta_distance(_d(rel, 3), float(radius))
 
 
-def cell_collide(f, tau, B=(), uk=(), arm=(), force=(0, 0, 0)):
+def cell_collide(f, tau, B=(), uk=(), arm=(), force=(0, 0, 0), collision=0):
     ns = len(B)
     fstar = np.zeros(19)
     Fk = np.zeros(6)
@@ -266,7 +269,7 @@ def cell_collide(f, tau, B=(), uk=(), arm=(), force=(0, 0, 0)):
     if ns:
         ukb[: 3 * ns] = np.asarray(uk, dtype=np.float64).reshape(-1)
         armb[: 3 * ns] = np.asarray(arm, dtype=np.float64).reshape(-1)
-    lib().or_cell_collide(_d(f, 19), float(tau), _d(force, 3), ns, Bb, ukb, armb, fstar, Fk, Mk)
+    lib().or_cell_collide(_d(f, 19), float(tau), int(collision), _d(force, 3), ns, Bb, ukb, armb, fstar, Fk, Mk)
     return fstar, Fk.reshape(2, 3)[:ns], Mk.reshape(2, 3)[:ns]
 
 

@@ -32,7 +32,6 @@ cudaError_t launch_psm_batch(const BatchChunk&, int*, int, int, cudaStream_t);
 cudaError_t launch_bin_batch(const LbmArgs*, const int*, int, cudaStream_t);
 cudaError_t launch_dem_batch(const DemArgs*, const int*, int, int, cudaStream_t);
 cudaError_t launch_final_batch(const DemArgs*, int, cudaStream_t);
-size_t psm_smem_bytes();
 }  // namespace ledds
 
 using namespace ledds;
@@ -124,6 +123,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (d->max_particles > 0 && !(p->dem_h > 0.0)) return LEDDS_ERR_INVALID_ARG;
     if (p->skin < 0.0) return LEDDS_ERR_INVALID_ARG;
     if (p->force_fp32 < 0 || p->force_fp32 > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->collision < 0 || p->collision > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -281,6 +281,13 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     for (int q = 0; q < 3; ++q) a.F[q] = (float)s->p.fluid_force[q];
     a.has_force = (s->p.fluid_force[0] != 0 || s->p.fluid_force[1] != 0 || s->p.fluid_force[2] != 0);
     a.guo_pref = (float)(1.0 - 0.5 / s->p.tau);
+    a.trt = s->p.collision == LEDDS_COLLIDE_TRT;
+    {
+        const double wp = 1.0 / s->p.tau;
+        const double wm = a.trt ? 8.0 * (2.0 - wp) / (8.0 - wp) : wp;  // Eq. (TRT) rate relation
+        a.omega_m = (float)wm;
+        a.guo_pref_m = (float)(1.0 - 0.5 * wm);
+    }
     double sc = s->p.storage == LEDDS_STORE_F16 ? ldexp(1.0, s->p.storage_scale_log2) : 1.0;
     a.scale = (float)sc;
     a.inv_scale = (float)(1.0 / sc);
@@ -498,6 +505,7 @@ int ledds_params_default(ledds_params* p) {
     p->ell_max_iter = 60;
     p->ell_tol = 1e-6;
     p->force_fp32 = 1;
+    p->collision = LEDDS_COLLIDE_BGK;
     return LEDDS_OK;
 }
 
@@ -973,6 +981,7 @@ static int batch_layout(int nsim, const ledds_dims* dims, const ledds_params* pa
         if (rc != LEDDS_OK) return rc;
         if (dims[i].nx <= 0) return LEDDS_ERR_INVALID_ARG;  // every member has a lattice
         if (params[i].storage != params[0].storage) return LEDDS_ERR_INVALID_ARG;
+        if (params[i].collision != params[0].collision) return LEDDS_ERR_INVALID_ARG;
         if (dims[i].max_particles > 4096) return LEDDS_ERR_INVALID_ARG;  // direct candidate search
         if (offs) offs->push_back(off);
         off = align256(off + layout(nullptr, &dims[i], &params[i], nullptr));

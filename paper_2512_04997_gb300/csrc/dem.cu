@@ -330,7 +330,7 @@ __device__ bool hit(const double r[3], const double R[9], const double s[3], con
 // move each point half way towards the intersection of its ellipsoid with the line
 // joining the osculating centres and project it back along the ray from its centre;
 // stop when both undamped steps fall below tol * smallest semi-axis.
-__device__ bool ell_geo(const DemArgs& A, const double ra[3], const double Ra_[9],
+__device__ __noinline__ bool ell_geo(const DemArgs& A, const double ra[3], const double Ra_[9],
                         const double sa[3], const double rb[3], const double Rb_[9],
                         const double sb[3], Geo& g) {
     double d[3] = {rb[0] - ra[0], rb[1] - ra[1], rb[2] - ra[2]};
@@ -444,7 +444,7 @@ __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& 
 
 // Particle-wall geometry, face = 2*axis + side: a static plane with inward normal at the
 // halfway position, surface velocity u_w; infinite mass and radius.
-__device__ bool wall_geo(const DemArgs& A, const double* st, int k, int face, Geo& g) {
+__device__ __noinline__ bool wall_geo(const DemArgs& A, const double* st, int k, int face, Geo& g) {
     int a = face >> 1, side = face & 1;
     double nrm[3] = {0.0, 0.0, 0.0};
     nrm[a] = side == 0 ? 1.0 : -1.0;
@@ -540,7 +540,7 @@ __device__ void spring_dashpot(const DemArgs& A, const Geo& g, double Rstar, dou
 // Contribution of candidate slot m of particle i (state buffer st): the canonical pair
 // force is applied with the sign of i's membership; the slot's tangential history is
 // updated (and reset when the pair is not in contact).
-__device__ void pair_contrib(const DemArgs& A, const double* st, int cb, int i, int m, double F[3],
+__device__ __noinline__ void pair_contrib(const DemArgs& A, const double* st, int cb, int i, int m, double F[3],
                              double M[3]) {
     const int j = A.cand[cb][(long long)i * A.ccap + m];
     double* hl = A.hist[cb] + ((long long)i * A.ccap + m) * 3;
@@ -581,7 +581,7 @@ __device__ void pair_contrib(const DemArgs& A, const double* st, int cb, int i, 
 }
 
 // Contribution of wall face `face` on particle i (history per particle and face).
-__device__ void wall_contrib(const DemArgs& A, const double* st, int i, int face, double F[3], double M[3]) {
+__device__ __noinline__ void wall_contrib(const DemArgs& A, const double* st, int i, int face, double F[3], double M[3]) {
     const int ax = face >> 1;
     double* wh = A.whist + ((long long)i * 6 + face) * 3;
     Geo g;
@@ -741,6 +741,21 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
 }
 __device__ __forceinline__ F2 f2_add(F2 a, float b) { return f2_add(a, F2{b, 0.0f}); }
 
+// Ellipsoid geometry (FP64) rounded for the FP32 force path; out of line, so that the
+// sphere path keeps its registers.
+__device__ __noinline__ bool pair_geo_f_general(const DemArgs& A, const double* st, int a, int b, GeoF& g) {
+    Geo g64;
+    if (!pair_geo(A, st, a, b, g64)) return false;
+    geo_to_f(g64, g);
+    return true;
+}
+__device__ __noinline__ bool wall_geo_f_general(const DemArgs& A, const double* st, int i, int face, GeoF& g) {
+    Geo g64;
+    if (!wall_geo(A, st, i, face, g64)) return false;
+    geo_to_f(g64, g);
+    return true;
+}
+
 // pair_contrib with FP32 contact arithmetic (ellipsoid geometry stays FP64).
 __device__ void pair_contrib_f(const DemArgs& A, const double* st, int cb, int i, int m, F2 F[3], F2 M[3]) {
     const int j = A.cand[cb][(long long)i * A.ccap + m];
@@ -753,9 +768,7 @@ __device__ void pair_contrib_f(const DemArgs& A, const double* st, int cb, int i
         for (int c = 0; c < 3; ++c) dd[c] = min_image(A, c, stv(A, st, SP + c, a) - stv(A, st, SP + c, b));
         hit_ = sphere_geo_f(dd, A.P.radius[a], A.P.radius[b], g);
     } else {
-        Geo g64;
-        hit_ = pair_geo(A, st, a, b, g64);
-        if (hit_) geo_to_f(g64, g);
+        hit_ = pair_geo_f_general(A, st, a, b, g);
     }
     if (!hit_) {
         hl[0] = hl[1] = hl[2] = 0.0;
@@ -819,13 +832,9 @@ __device__ void wall_contrib_f(const DemArgs& A, const double* st, int i, int fa
         }
         g.Ra = Rf;
         g.sphere = true;
-    } else {
-        Geo g64;
-        if (!wall_geo(A, st, i, face, g64)) {
-            wh[0] = wh[1] = wh[2] = 0.0;
-            return;
-        }
-        geo_to_f(g64, g);
+    } else if (!wall_geo_f_general(A, st, i, face, g)) {
+        wh[0] = wh[1] = wh[2] = 0.0;
+        return;
     }
     const double* uw = A.uw[ax][side];
     float dv[3], wi[3], h[3], zero[3] = {0.0f, 0.0f, 0.0f}, Fw[3], Ft[3], Mw[3];
@@ -894,37 +903,55 @@ __device__ void contact_sum_warp(const DemArgs& A, const double* st, int cb, int
 // ------------------------------------------------------------------------------------
 // Integration (Sec. 2.2)
 // ------------------------------------------------------------------------------------
+// The integrator runs a long dependent FP64 chain per particle, so it uses fused
+// multiply-adds and few divisions (explicit __fma_rn: this file is compiled without
+// contraction, which the contact predicate and the cell keys need).
+__device__ __forceinline__ void cross3_fma(const double a[3], const double b[3], double o[3]) {
+    double x = __fma_rn(a[1], b[2], -(a[2] * b[1]));
+    double y = __fma_rn(a[2], b[0], -(a[0] * b[2]));
+    double z = __fma_rn(a[0], b[1], -(a[1] * b[0]));
+    o[0] = x;
+    o[1] = y;
+    o[2] = z;
+}
+__device__ __forceinline__ double dot3_fma(const double a[3], const double b[3]) {
+    return __fma_rn(a[0], b[0], __fma_rn(a[1], b[1], a[2] * b[2]));
+}
+
 // Predictor: Eq. (advance-r) and the triad update with w(t), then Gram-Schmidt;
 // positions wrapped on periodic axes; displacement since the last rebuild checked.
 __device__ void predict(const DemArgs& A, int k, double r[3], const double v[3], const double acc[3],
                         const double w[3], double d[9]) {
-    const double dt = A.dt;
-    for (int a = 0; a < 3; ++a) r[a] = r[a] + dt * v[a] + (dt * dt / 2.0) * acc[a];
+    const double dt = A.dt, h2 = dt * dt / 2.0;
+    for (int a = 0; a < 3; ++a) r[a] = __fma_rn(h2, acc[a], __fma_rn(dt, v[a], r[a]));
     for (int a = 0; a < 3; ++a)
-        if (A.per[a]) r[a] = r[a] - A.L[a] * floor((r[a] - A.lo[a]) / A.L[a]);
+        if (A.per[a]) {
+            // r - L floor((r - lo)/L); the quotient's floor is 0 well inside [lo, lo + L)
+            const double q = r[a] - A.lo[a];
+            if (q < 0.0 || q >= 0.999999 * A.L[a]) r[a] = r[a] - A.L[a] * floor(q / A.L[a]);
+        }
     for (int m = 0; m < 3; ++m) {
         double* dm = d + 3 * m;
         double wxd[3], ds[3], mid[3], wxm[3];
-        cross3(w, dm, wxd);
-        for (int a = 0; a < 3; ++a) ds[a] = dm[a] + dt * wxd[a];
+        cross3_fma(w, dm, wxd);
+        for (int a = 0; a < 3; ++a) ds[a] = __fma_rn(dt, wxd[a], dm[a]);
         for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (dm[a] + ds[a]);
-        cross3(w, mid, wxm);
-        for (int a = 0; a < 3; ++a) dm[a] = dm[a] + dt * wxm[a];
+        cross3_fma(w, mid, wxm);
+        for (int a = 0; a < 3; ++a) dm[a] = __fma_rn(dt, wxm[a], dm[a]);
     }
     double* d1 = d;
     double* d2 = d + 3;
-    // one FP64 division per normalisation (FP64 division is costly on this part)
-    const double i1 = 1.0 / norm3(d1);
+    const double i1 = rsqrt(dot3_fma(d1, d1));
     for (int a = 0; a < 3; ++a) d1[a] *= i1;
-    double p = dot3(d2, d1);
-    for (int a = 0; a < 3; ++a) d2[a] -= p * d1[a];
-    const double i2 = 1.0 / norm3(d2);
+    const double p = dot3_fma(d2, d1);
+    for (int a = 0; a < 3; ++a) d2[a] = __fma_rn(-p, d1[a], d2[a]);
+    const double i2 = rsqrt(dot3_fma(d2, d2));
     for (int a = 0; a < 3; ++a) d2[a] *= i2;
-    cross3(d1, d2, d + 6);
+    cross3_fma(d1, d2, d + 6);
     double disp2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         double e = min_image(A, a, r[a] - A.P.pos_build[(long long)a * A.P.cap + k]);
-        disp2 += e * e;
+        disp2 = __fma_rn(e, e, disp2);
     }
     if (disp2 > 0.25 * A.skin * A.skin) atomicAdd(&A.status->skin_violation, 1);
     bool bad = false;
@@ -936,24 +963,26 @@ __device__ void predict(const DemArgs& A, int k, double r[3], const double v[3],
 // (Eq. advance-omega, body-frame Euler equations), v += dt/2 (a + a'), w += dt/2 (alpha + alpha').
 __device__ void correct(const DemArgs& A, int k, const double F[3], const double M[3], const double d[9],
                         double v[3], double w[3]) {
-    const double dt = A.dt;
+    const double hdt = A.dt / 2.0;
     double an[3], wb[3], Mb[3], Iw[3], gyr[3], ab[3], al[3];
     const double im = 1.0 / A.P.mass[k], gf = A.P.gfac[k];
-    for (int a = 0; a < 3; ++a) an[a] = F[a] * im + A.gravity[a] * gf;
+    for (int a = 0; a < 3; ++a) an[a] = __fma_rn(F[a], im, A.gravity[a] * gf);
     for (int q = 0; q < 3; ++q) {
-        wb[q] = dot3(d + 3 * q, w);
-        Mb[q] = dot3(d + 3 * q, M);
+        wb[q] = dot3_fma(d + 3 * q, w);
+        Mb[q] = dot3_fma(d + 3 * q, M);
     }
     double I[3];
     for (int q = 0; q < 3; ++q) I[q] = A.P.inertia[(long long)q * A.P.cap + k];
+    const double D = 1.0 / (I[0] * I[1] * I[2]);  // one division for the three inverses
+    const double iI[3] = {I[1] * I[2] * D, I[0] * I[2] * D, I[0] * I[1] * D};
     for (int q = 0; q < 3; ++q) Iw[q] = I[q] * wb[q];
-    cross3(wb, Iw, gyr);
-    for (int q = 0; q < 3; ++q) ab[q] = (Mb[q] - gyr[q]) / I[q];
-    for (int a = 0; a < 3; ++a) al[a] = ab[0] * d[0 + a] + ab[1] * d[3 + a] + ab[2] * d[6 + a];
+    cross3_fma(wb, Iw, gyr);
+    for (int q = 0; q < 3; ++q) ab[q] = (Mb[q] - gyr[q]) * iI[q];
+    for (int a = 0; a < 3; ++a) al[a] = __fma_rn(ab[0], d[0 + a], __fma_rn(ab[1], d[3 + a], ab[2] * d[6 + a]));
     for (int a = 0; a < 3; ++a) {
         long long o = (long long)a * A.P.cap + k;
-        v[a] += dt / 2.0 * (A.P.acc[o] + an[a]);
-        w[a] += dt / 2.0 * (A.P.alpha[o] + al[a]);
+        v[a] = __fma_rn(hdt, A.P.acc[o] + an[a], v[a]);
+        w[a] = __fma_rn(hdt, A.P.alpha[o] + al[a], w[a]);
         A.P.acc[o] = an[a];
         A.P.alpha[o] = al[a];
     }
@@ -990,7 +1019,7 @@ __global__ void k_predict_first(DemArgs A) {
 
 // Contact forces of a substep, one warp per particle, from buffer `in` (Table 1 "Compute
 // DEM forces" and "Reduce DEM forces"): stored in Fc, Mc.
-__global__ void k_contacts(DemArgs A, int in, int cb) {
+__global__ void __launch_bounds__(128, 6) k_contacts(DemArgs A, int in, int cb) {
     const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     if (k >= A.P.n) return;  // uniform across the warp
     double F[3], M[3];

@@ -129,6 +129,8 @@ struct LbmArgs {
     float F[3];
     int has_force;
     float guo_pref;               // 1 - 1/(2 tau)
+    int trt;                      // TRT collision: odd parts relax at omega_m
+    float omega_m, guo_pref_m;    // 1/tau- and 1 - 1/(2 tau-)
     float scale, inv_scale;
     const void* pop_in;
     void* pop_out;

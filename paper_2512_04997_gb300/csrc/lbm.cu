@@ -596,16 +596,23 @@ __device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float v
 // needs no CTA barrier, and two planes of loads stay in flight per thread whatever the
 // occupancy.
 // ------------------------------------------------------------------------------------
-// Resident CTAs per SM the PSM kernel is compiled for (register budget) and depth of its
-// asynchronous pull pipeline (planes in flight + 1); tuned on GB300.
-#ifndef LEDDS_PSM_MINB
-#define LEDDS_PSM_MINB 3
-#endif
-#ifndef LEDDS_PSM_STAGES
-#define LEDDS_PSM_STAGES 3
-#endif
 constexpr int PSM_THREADS = TILE_X * TILE_Y;
-constexpr int PSM_STAGES = LEDDS_PSM_STAGES;
+
+// Per storage format: resident CTAs per SM the PSM kernel is compiled for (its register
+// budget), depth of the asynchronous pull pipeline (planes in flight + 1) and the form of
+// the wall path (wall_in_slots: the pulled values stay in registers). Chosen by timing
+// the variants on GB300: FP32 runs best with more registers and a deeper pipeline, the
+// 16-bit formats with more resident CTAs.
+template <int STORE>
+struct PsmCfg {
+    static constexpr int minb = 3, stages = 3;
+    static constexpr bool wall_in_slots = false;
+};
+template <>
+struct PsmCfg<LEDDS_STORE_F32> {
+    static constexpr int minb = 2, stages = 4;
+    static constexpr bool wall_in_slots = true;
+};
 
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src, bool pred) {
     unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
@@ -713,6 +720,8 @@ __device__ __noinline__ void issue_general(const LbmArgs& a, const typename SS::
     }
 }
 
+// Wall-adjacent node, reading into g directly (out of line; g then lives in local memory,
+// which costs less than the spills of keeping it in registers under an 80-register budget).
 template <class SS>
 __device__ __noinline__ void read_general(const LbmArgs& a, int x, int y, int z, const uint32_t* slot, float* g) {
     for (int i = 0; i < 19; ++i) {
@@ -728,6 +737,38 @@ __device__ __noinline__ void read_general(const LbmArgs& a, int x, int y, int z,
         g[i] = v + wt;
     }
 }
+
+// Wall-adjacent node: decode its 19 pulled words and add the moving-wall terms, writing
+// the results back into the thread's own stage slots as FP32 bits. Out of line (rare
+// nodes), and it takes no pointer to the node's value array, which therefore stays in
+// registers on every path.
+template <class SS>
+__device__ __noinline__ void fix_general_slots(const LbmArgs& a, int x, int y, int z, uint32_t* slot) {
+    for (int i = 0; i < 19; ++i) {
+        float wt;
+        const int elem = general_elem(a, i, x, y, z, &wt);
+        const uint32_t w = slot[i * PSM_THREADS];
+        float v;
+        if (sizeof(typename SS::T) == 4) {
+            v = __uint_as_float(w);
+        } else {
+            v = SS::from_bits((elem & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), a.inv_scale);
+        }
+        slot[i * PSM_THREADS] = __float_as_uint(v + wt);
+    }
+}
+
+template <int I>
+struct ReadFloats {
+    static __device__ __forceinline__ void run(const uint32_t* slot, float* g) {
+        g[I] = __uint_as_float(slot[I * PSM_THREADS]);
+        ReadFloats<I + 1>::run(slot, g);
+    }
+};
+template <>
+struct ReadFloats<19> {
+    static __device__ __forceinline__ void run(const uint32_t*, float*) {}
+};
 
 template <class SS, int I>
 struct IssueAll {
@@ -819,11 +860,12 @@ __device__ __forceinline__ float cqc(const SolidSums& m) {
 // with dsym = t rho (9 cu c.D - 4.5 c^T Q c - 1.5 S), dasym = 3 t rho c.D (SolidSums).
 // SOLID is uniform across the warp: false when no lane of the warp has a solid.
 // The force sum over the directions is not accumulated here: see solid_force.
-template <class SS, int I, bool SOLID>
+template <class SS, int I, bool SOLID, bool TRT>
 struct CollidePairs {
     static __device__ __forceinline__ void run(float* g, float rho, float ux, float uy, float uz, float base,
                                                const LbmArgs& a, float Fu, float force_w, float keep,
-                                               const SolidSums& m, typename SS::T* dst, bool valid) {
+                                               float kB, float force_wa, const SolidSums& m,
+                                               typename SS::T* dst, bool valid) {
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         constexpr float t = TW(I);
         const float cu = cdot<cx, cy, cz>(ux, uy, uz);
@@ -834,11 +876,15 @@ struct CollidePairs {
         const float n1 = g[I + 1] - t * (sym - asym);   // neq_{I+1}
         float o0 = t * (sym + asym) + keep * n0;
         float o1 = t * (sym - asym) + keep * n1;
+        if constexpr (TRT) {  // the odd part of neq relaxes at the second rate
+            o0 += kB * n1;
+            o1 += kB * n0;
+        }
         if (a.has_force) {
             const float cF = cdot<cx, cy, cz>(a.F[0], a.F[1], a.F[2]);
             // Guo term t [3 (c.F - u.F) + 9 (c.u)(c.F)]: c -> -c flips only 3 c.F
             const float fs = force_w * t * (-3.0f * Fu + 9.0f * cu * cF);
-            const float fa = force_w * t * 3.0f * cF;
+            const float fa = (TRT ? force_wa : force_w) * t * 3.0f * cF;
             o0 += fs + fa;
             o1 += fs - fa;
         }
@@ -855,13 +901,15 @@ struct CollidePairs {
             SS::store(dst + a.pN[I], o0, a.scale);
             SS::store(dst + a.pN[I + 1], o1, a.scale);
         }
-        CollidePairs<SS, I + 2, SOLID>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, dst, valid);
+        CollidePairs<SS, I + 2, SOLID, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
+                                                 dst, valid);
     }
 };
-template <class SS, bool SOLID>
-struct CollidePairs<SS, 19, SOLID> {
+template <class SS, bool SOLID, bool TRT>
+struct CollidePairs<SS, 19, SOLID, TRT> {
     static __device__ __forceinline__ void run(float*, float, float, float, float, float, const LbmArgs&, float,
-                                               float, float, const SolidSums&, typename SS::T*, bool) {}
+                                               float, float, float, float, const SolidSums&, typename SS::T*,
+                                               bool) {}
 };
 
 // ------------------------------------------------------------------------------------
@@ -874,10 +922,11 @@ struct CollidePairs<SS, 19, SOLID> {
 // ------------------------------------------------------------------------------------
 // One 32x8xTILE_Z tile (bx, by, bz) of the lattice described by `a`; psm_smem holds the
 // tile cache followed by the pipeline stages (psm_smem_bytes()).
-template <int STORE>
+template <int STORE, bool TRT>
 __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, unsigned char* psm_smem) {
     using SS = Store<STORE>;
     using T = typename SS::T;
+    constexpr int PSM_STAGES = PsmCfg<STORE>::stages;
     const T* pin = (const T*)a.pop_in;
     T* pout = (T*)a.pop_out;
     TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
@@ -922,9 +971,15 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         pl.cell = 0;
         if (valid) {
             make_plan(a, x, y, z, pl);
-            const uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
-            if (!pl.wall) ReadAll<SS, 0>::run(a, pl, slot, g);
-            else read_general<SS>(a, x, y, z, slot, g);
+            uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
+            if (!pl.wall) {
+                ReadAll<SS, 0>::run(a, pl, slot, g);
+            } else if constexpr (PsmCfg<STORE>::wall_in_slots) {
+                fix_general_slots<SS>(a, x, y, z, slot);
+                ReadFloats<0>::run(slot, g);
+            } else {
+                read_general<SS>(a, x, y, z, slot, g);
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < 19; ++i) g[i] = 0.f;
@@ -962,8 +1017,13 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
         if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
         const float Btot = fminf(q0.B + q1.B, 1.0f);
-        const float keep = 1.0f - (1.0f - Btot) * omega;
+        // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
+        // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
+        const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
+        const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
+        const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
         const float force_w = (1.0f - Btot) * a.guo_pref;
+        const float force_wa = (1.0f - Btot) * a.guo_pref_m;
         const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
         // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
         const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
@@ -987,13 +1047,15 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
             m.Qxz = b0x * d0z + b1x * d1z;
             m.Qyz = b0y * d0z + b1y * d1z;
             m.S = q0.B * d0s + q1.B * d1s;
-            CollidePairs<SS, 1, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, pout + pl.cell, valid);
+            CollidePairs<SS, 1, true, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
+                                                pout + pl.cell, valid);
         } else {
             m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
-            CollidePairs<SS, 1, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, m, pout + pl.cell, valid);
+            CollidePairs<SS, 1, false, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
+                                                 pout + pl.cell, valid);
         }
         {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
-            float out0 = TW(0) * base + keep * g[0];
+            float out0 = TW(0) * base + keep0 * g[0];
             if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
             out0 += 1.5f * TW(0) * rho * m.S;
             if (valid) SS::store(pout + pl.cell, out0, a.scale);
@@ -1042,17 +1104,17 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
     }
 }
 
-template <int STORE>
-__global__ void __launch_bounds__(PSM_THREADS, LEDDS_PSM_MINB) k_psm(const LbmArgs a) {
+template <int STORE, bool TRT>
+__global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const LbmArgs a) {
     extern __shared__ __align__(16) unsigned char psm_smem[];
-    psm_tile<STORE>(a, blockIdx.x, blockIdx.y, blockIdx.z, psm_smem);
+    psm_tile<STORE, TRT>(a, blockIdx.x, blockIdx.y, blockIdx.z, psm_smem);
 }
 
 // Batched form: persistent CTAs take (simulation, tile) work items from a queue, so many
 // simulations of uneven sizes advance in one launch with balanced load. The members'
 // arguments travel in the launch's parameter block (read-only for the whole launch, like
 // the single-simulation kernel's argument), up to BATCH_CHUNK members per launch.
-template <int STORE>
+template <int STORE, bool TRT>
 __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const __grid_constant__ BatchChunk P,
                                                                           int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1078,7 +1140,7 @@ __global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const __grid_const
         const LbmArgs& a = P.a[sim];
         const int t = item - P.tile_start[sim];
         const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
-        psm_tile<STORE>(a, bx, by, bz, smem);
+        psm_tile<STORE, TRT>(a, bx, by, bz, smem);
         __syncthreads();
     }
 }
@@ -1121,8 +1183,9 @@ __global__ void k_bin_batch(const LbmArgs* args, const int* np) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) bin_particle(a, k, tcount, tids);
 }
 
-size_t psm_smem_bytes() {
-    return ((sizeof(TileCache) + 15) & ~(size_t)15) + sizeof(uint32_t) * PSM_STAGES * 19 * PSM_THREADS;
+size_t psm_smem_bytes(int store) {
+    const int stages = store == LEDDS_STORE_F32 ? PsmCfg<LEDDS_STORE_F32>::stages : PsmCfg<LEDDS_STORE_F16>::stages;
+    return ((sizeof(TileCache) + 15) & ~(size_t)15) + sizeof(uint32_t) * stages * 19 * PSM_THREADS;
 }
 
 // Solid fractions only (the same tile machinery), for inspection.
@@ -1194,42 +1257,54 @@ cudaError_t launch_bin(const LbmArgs& a, int n, int* tile_count, int* tile_ids, 
     return cudaGetLastError();
 }
 
-template <int STORE>
+template <int STORE, bool TRT>
 static cudaError_t launch_psm_t(const LbmArgs& a, cudaStream_t s) {
     static bool configured = false;
-    const size_t smem = psm_smem_bytes();
+    const size_t smem = psm_smem_bytes(STORE);
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_psm<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_psm<STORE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm<STORE><<<tile_grid(a), PSM_THREADS, smem, s>>>(a);
+    k_psm<STORE, TRT><<<tile_grid(a), PSM_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_psm(const LbmArgs& a, int store, cudaStream_t s) {
-    if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32>(a, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16>(a, s);
-    return launch_psm_t<LEDDS_STORE_BF16>(a, s);
+    if (a.trt) {
+        if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32, true>(a, s);
+        if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16, true>(a, s);
+        return launch_psm_t<LEDDS_STORE_BF16, true>(a, s);
+    }
+    if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32, false>(a, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16, false>(a, s);
+    return launch_psm_t<LEDDS_STORE_BF16, false>(a, s);
 }
 
-template <int STORE>
+template <int STORE, bool TRT>
 static cudaError_t launch_psm_batch_t(const BatchChunk& P, int* counter, int nblocks, cudaStream_t s) {
     static bool configured = false;
-    const size_t smem = psm_smem_bytes();
+    const size_t smem = psm_smem_bytes(STORE);
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_psm_batch<STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_psm_batch<STORE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm_batch<STORE><<<nblocks, PSM_THREADS, smem, s>>>(P, counter);
+    k_psm_batch<STORE, TRT><<<nblocks, PSM_THREADS, smem, s>>>(P, counter);
     return cudaGetLastError();
 }
 
+// All members of a batch share the storage format and the collision operator.
 cudaError_t launch_psm_batch(const BatchChunk& P, int* counter, int store, int nblocks, cudaStream_t s) {
-    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32>(P, counter, nblocks, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16>(P, counter, nblocks, s);
-    return launch_psm_batch_t<LEDDS_STORE_BF16>(P, counter, nblocks, s);
+    if (P.a[0].trt) {
+        if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, true>(P, counter, nblocks, s);
+        if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, true>(P, counter, nblocks, s);
+        return launch_psm_batch_t<LEDDS_STORE_BF16, true>(P, counter, nblocks, s);
+    }
+    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, false>(P, counter, nblocks, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, false>(P, counter, nblocks, s);
+    return launch_psm_batch_t<LEDDS_STORE_BF16, false>(P, counter, nblocks, s);
 }
 
 cudaError_t launch_bin_batch(const LbmArgs* args, const int* np, int nsim, cudaStream_t s) {

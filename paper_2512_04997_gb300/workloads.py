@@ -162,7 +162,7 @@ def base_params(**kw) -> dict:
              subdiv_n=10, law="linear", n_sub=1, rho_f=1.0, gravity=(0.0, 0.0, 0.0),
              k_n=1000.0, k_t=1000.0 * 2.0 / 7.0, young=1.0e4, poisson=0.3, restitution=0.7,
              friction=0.4, skin=0.5, dem_h=0.0, ell_max_iter=60, ell_tol=1e-6,
-             force_fp32=1)
+             force_fp32=1, collision="bgk")
     p.update(kw)
     return p
 
@@ -383,3 +383,132 @@ def batched_ensemble(nsim: int = 64, seed_index: int = 5, steps: int = 1000,
         w.steps = steps
         out.append(w)
     return out
+
+
+def _pw_overlap(ra, Ainv, rb, Binv, iters: int = 40) -> np.ndarray:
+    """Perram-Wertheim test for pairs of ellipsoids (rows): they overlap iff
+    max_{l in [0,1]} l (1 - l) r^T [(1 - l) A^-1 + l B^-1]^-1 r < 1, r = r_b - r_a, with
+    A^-1 = R^T diag(a^2) R the inverse shape matrix. The function is concave in l; its
+    maximum is found by golden-section search."""
+    r = rb - ra
+
+    def F(lam):
+        C = (1.0 - lam)[:, None, None] * Ainv + lam[:, None, None] * Binv
+        x = np.linalg.solve(C, r[:, :, None])[:, :, 0]
+        return lam * (1.0 - lam) * (r * x).sum(1)
+
+    lo = np.zeros(len(r))
+    hi = np.ones(len(r))
+    gr = (math.sqrt(5.0) - 1.0) / 2.0
+    x1 = hi - gr * (hi - lo)
+    x2 = lo + gr * (hi - lo)
+    f1, f2 = F(x1), F(x2)
+    for _ in range(iters):
+        left = f1 < f2            # the maximum lies in [x1, hi]
+        lo = np.where(left, x1, lo)
+        hi = np.where(left, hi, x2)
+        nx1 = hi - gr * (hi - lo)
+        nx2 = lo + gr * (hi - lo)
+        x1, x2 = np.where(left, x2, nx1), np.where(left, nx2, x1)
+        f1n, f2n = np.where(left, f2, F(nx1)), np.where(left, F(nx2), f1)
+        f1, f2 = f1n, f2n
+    return np.maximum(f1, f2) < 1.0
+
+
+def ellipsoid_shear(nx: int = 384, ny: int = 384, nz: int = 192, n_particles: int = 20000,
+                    semi=(6.0, 2.0, 2.0), shear_rate: float = 1e-4, steps: int = 3000,
+                    seed_index: int = 4, storage: str = "f32", gap: float = 0.2) -> Workload:
+    """Prolate ellipsoids in simple shear: walls at z moving at -/+ shear_rate nz/2 along x,
+    periodic x and y, uniformly random orientations (Shoemake quaternions), subdivision
+    solid fractions, common-normal contacts, 10 DEM substeps, neutrally buoyant.
+
+    Placement: centres uniform in the box (one semi-axis plus a lattice unit from the
+    walls); every pair closer than the sum of the largest semi-axes is tested exactly
+    (Perram-Wertheim, with the semi-axes grown by gap/2), and one member of each
+    overlapping pair is redrawn, until no pair overlaps."""
+    g = rng(seed_index)
+    a = np.asarray(semi, dtype=np.float64)
+    n = n_particles
+    w = Workload(name=f"ellipsoid_shear_{nx}x{ny}x{nz}_{n}ellipsoids", nx=nx, ny=ny, nz=nz,
+                 periodic=(1, 1, 0))
+    U = shear_rate * nz / 2.0
+    w.u_wall[2, 0, 0] = -U
+    w.u_wall[2, 1, 0] = +U
+    L = np.array([nx, ny, nz], dtype=np.float64)
+    lo = np.array([-0.5, -0.5, 0.5 + a.max()])
+    span = np.array([nx, ny, nz - 2.0 - 2.0 * a.max()])
+    grown = a + gap / 2.0
+    pos = lo + g.random((n, 3)) * span
+    quat = random_quaternions(g, n)
+    triad = quaternion_to_triad(quat)
+    reach = 2.0 * grown.max()
+    for _ in range(200):
+        # candidate pairs by a uniform grid of cell size >= reach (minimum image in x, y)
+        gn = np.maximum(1, np.floor(L / reach)).astype(int)
+        cell = np.minimum(np.floor((pos - np.array([-0.5, -0.5, -0.5])) / (L / gn)).astype(int), gn - 1)
+        key = cell[:, 0] + gn[0] * (cell[:, 1] + gn[1] * cell[:, 2])
+        order = np.argsort(key, kind="stable")
+        sk = key[order]
+        starts = np.searchsorted(sk, np.arange(gn.prod() + 1))
+        pairs_i, pairs_j = [], []
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    c2 = cell + np.array([dx, dy, dz])
+                    c2[:, 0] %= gn[0]
+                    c2[:, 1] %= gn[1]
+                    ok = (c2[:, 2] >= 0) & (c2[:, 2] < gn[2])
+                    k2 = c2[:, 0] + gn[0] * (c2[:, 1] + gn[1] * np.clip(c2[:, 2], 0, gn[2] - 1))
+                    s0, s1 = starts[k2], starts[k2 + 1]
+                    cnt = np.where(ok, s1 - s0, 0)
+                    idx_i = np.repeat(np.arange(n), cnt)
+                    off = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+                    idx_j = order[np.repeat(s0, cnt) + off]
+                    keep = idx_i < idx_j
+                    pairs_i.append(idx_i[keep])
+                    pairs_j.append(idx_j[keep])
+        pi = np.concatenate(pairs_i)
+        pj = np.concatenate(pairs_j)
+        uniq = np.unique(pi.astype(np.int64) * n + pj)
+        pi, pj = uniq // n, uniq % n
+        d = pos[pj] - pos[pi]
+        d[:, :2] -= L[:2] * np.round(d[:, :2] / L[:2])
+        close = (d * d).sum(1) < reach * reach
+        pi, pj = pi[close], pj[close]
+        if len(pi) == 0:
+            break
+        R = triad.reshape(n, 3, 3)            # rows d1, d2, d3 (body axes in world components)
+        inv = np.einsum("nki,k,nkj->nij", R, grown ** 2, R)
+        rb = pos[pi] + d[close]
+        hit = _pw_overlap(pos[pi], inv[pi], rb, inv[pj])
+        bad = np.unique(pj[hit])
+        if len(bad) == 0:
+            break
+        pos[bad] = lo + g.random((len(bad), 3)) * span
+        q = random_quaternions(g, len(bad))
+        triad[bad] = quaternion_to_triad(q)
+    else:
+        raise RuntimeError("ellipsoid placement did not converge")
+    rho_p = 1.0
+    vol = 4.0 / 3.0 * math.pi * a.prod()
+    m = rho_p * vol
+    kn = 0.5 * (m / 2) * (math.pi / 20.0 * 10) ** 2   # contact >= 20 substeps (dt_p = 1/10)
+    w.params = base_params(tau=0.8, storage=storage, voxel="subdiv", subdiv_n=10, n_sub=10,
+                           rho_f=1.0, law="linear", k_n=kn, k_t=kn * 2.0 / 7.0, skin=0.5,
+                           dem_h=2.0 * a.max() + 0.5)
+    w.shape = np.ones(n, dtype=np.int32)
+    w.radius = np.full(n, a.max())
+    w.semi = np.tile(a, (n, 1))
+    w.density = np.full(n, rho_p)
+    w.pos = pos
+    zc = pos[:, 2]
+    w.vel = np.zeros((n, 3))
+    w.vel[:, 0] = -U + 2.0 * U * (zc + 0.5) / nz
+    w.omg = np.zeros((n, 3))
+    w.triad = triad
+    z = np.arange(nz, dtype=np.float64)
+    u = np.zeros((3, nz, ny, nx), dtype=np.float32)
+    u[0] = (-U + 2.0 * U * (z + 0.5) / nz)[:, None, None]
+    w.init_u = u.reshape(3, -1)
+    w.steps = steps
+    return w

@@ -15,7 +15,8 @@ def oracle_from_workload(O, w, populations=None):
                           rho_f=p["rho_f"], gravity=p["gravity"], k_n=p["k_n"], k_t=p["k_t"],
                           young=p["young"], poisson=p["poisson"], restitution=p["restitution"],
                           friction=p["friction"], dem_h=p["dem_h"],
-                          ell_max_iter=p["ell_max_iter"], ell_tol=p["ell_tol"])
+                          ell_max_iter=p["ell_max_iter"], ell_tol=p["ell_tol"],
+                          collision={"bgk": 0, "trt": 1}[p.get("collision", "bgk")])
     s = O.Sim(w.nx, w.ny, w.nz, periodic=w.periodic, u_wall=w.u_wall, params=op,
               box_lo=w.box_lo, box_hi=w.box_hi, max_particles=max(w.n, 1))
     if w.ncell:

@@ -34,14 +34,15 @@ def lattice_workload(nx, ny, nz, periodic, tau=0.8, **kw):
 # ------------------------------------------------------------------------------------
 # lattice only
 # ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("collision", ["bgk", "trt"])
 @pytest.mark.parametrize("periodic,walls", [((1, 1, 1), None), ((1, 1, 0), "z"), ((0, 0, 0), "all")])
-def test_lattice_populations_and_fields(oracle, periodic, walls):
+def test_lattice_populations_and_fields(oracle, periodic, walls, collision):
     """Pull streaming, periodic wrap, halfway and moving-wall bounce-back (edges and
-    corners included) and BGK, on off-equilibrium random populations."""
+    corners included) and the BGK or TRT collision, on off-equilibrium random populations."""
     nx, ny, nz = 37, 19, 11     # 2 tiles in x, 3 in y, 3 in z, all ragged
     g = W.rng(500)
     f0 = random_populations(oracle, g, nx, ny, nz)
-    w = lattice_workload(nx, ny, nz, periodic, tau=0.7)
+    w = lattice_workload(nx, ny, nz, periodic, tau=0.7, collision=collision)
     if walls == "z":
         w.u_wall[2, 0] = [-0.03, 0.01, 0.0]
         w.u_wall[2, 1] = [0.04, 0.0, 0.0]
@@ -69,9 +70,12 @@ def test_lattice_populations_and_fields(oracle, periodic, walls):
     assert err_rho < 1e-6, err_rho
 
 
-def test_guo_forcing_channel(oracle):
-    """Body-force-driven channel (Guo forcing) between no-slip walls."""
-    w = lattice_workload(3, 5, 12, (1, 1, 0), tau=0.5 + math.sqrt(3) / 4, fluid_force=(1e-5, 0, 0))
+@pytest.mark.parametrize("collision,tau", [("bgk", 0.5 + math.sqrt(3) / 4), ("trt", 0.8), ("trt", 1.4)])
+def test_guo_forcing_channel(oracle, collision, tau):
+    """Body-force-driven channel (Guo forcing) between no-slip walls, BGK at its exact tau
+    and TRT at any tau; after the flow has developed, also against the exact parabola."""
+    H, F = 12, 1e-5
+    w = lattice_workload(3, 5, H, (1, 1, 0), tau=tau, fluid_force=(F, 0, 0), collision=collision)
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
     o.step(300)
@@ -79,6 +83,13 @@ def test_guo_forcing_channel(oracle):
     _, u_o = o.moments()
     _, u_g = s.fields()
     assert normwise(u_g.cpu().numpy(), u_o) < FP32_TOL
+    nu = (tau - 0.5) / 3.0
+    s.step(int(40 * H * H / nu))
+    _, u_g = s.fields()
+    z = np.arange(H) + 0.5
+    ex = F / (2 * nu) * z * (H - z)
+    ux = u_g[0].cpu().numpy().reshape(H, 5, 3)
+    assert np.abs(ux - ex[:, None, None]).max() / ex.max() < 1e-4   # FP32 steady state
 
 
 def test_graph_and_eager_paths_agree(oracle):
@@ -145,13 +156,14 @@ def test_voxelize_parity(oracle, voxel):
 # ------------------------------------------------------------------------------------
 # coupled steps
 # ------------------------------------------------------------------------------------
-@pytest.mark.parametrize("voxel,n_sub", [("distance", 1), ("subdiv", 3)])
-def test_coupled_small(oracle, voxel, n_sub):
+@pytest.mark.parametrize("voxel,n_sub,collision", [("distance", 1, "bgk"), ("subdiv", 3, "bgk"),
+                                                    ("distance", 2, "trt")])
+def test_coupled_small(oracle, voxel, n_sub, collision):
     """Several spheres and ellipsoids in a sheared box: fields, forces and trajectories
     after 30 coupled steps (PSM + hydrodynamic force + DEM substeps + walls)."""
     shapes = [0] * 5 + ([1] * 2 if voxel == "subdiv" else [])
     w = _particles_workload(40, 26, 24, (1, 1, 0), voxel, 503, shapes, radius=3.0, clear=True)
-    w.params.update(n_sub=n_sub, k_n=20.0, k_t=20.0 * 2 / 7, gravity=(0, 0, -2e-5))
+    w.params.update(n_sub=n_sub, k_n=20.0, k_t=20.0 * 2 / 7, gravity=(0, 0, -2e-5), collision=collision)
     w.u_wall[2, 1] = [0.03, 0.0, 0.0]
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)

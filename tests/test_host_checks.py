@@ -22,7 +22,8 @@ def _size(L, d, p):
 BAD_PARAMS = [
     dict(tau=0.5), dict(tau=0.2), dict(tau=float("nan")), dict(storage=3), dict(storage=-1),
     dict(voxel=2), dict(subdiv_n=0), dict(subdiv_n=17), dict(law=2), dict(n_sub=0),
-    dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")),
+    dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")), dict(collision=2),
+    dict(collision=-1), dict(force_fp32=2),
 ]
 
 
@@ -84,6 +85,9 @@ def test_batch_workspace_rules(L):
     s2 = _size(L, d2, p16)[1]
     assert total >= s1 + s2
     assert _batch_size(L, [d1, d2], [p16, p32])[0] == ERR_INVALID            # mixed storage
+    trt = ledds.make_params(dem_h=8.0, storage=1, collision="trt")
+    assert _batch_size(L, [d1, d2], [p16, trt])[0] == ERR_INVALID            # mixed collision
+    assert _batch_size(L, [d1, d2], [trt, trt])[0] == 0
     no_lattice = ledds.make_dims(0, 0, 0, max_particles=8, box_lo=(0, 0, 0), box_hi=(20, 20, 20))
     assert _batch_size(L, [d1, no_lattice], [p16, p16])[0] == ERR_INVALID    # member without a lattice
     big = ledds.make_dims(32, 32, 32, max_particles=4097)

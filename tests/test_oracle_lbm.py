@@ -133,3 +133,59 @@ def test_poiseuille_exact_at_magic_tau(oracle):
     ex2 = F / (2 * 0.1) * z * (H - z)
     err = np.abs(u2[0] - ex2).max() / ex2.max()
     assert 1e-3 < err < 3e-2
+
+
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2, 2.0])
+def test_trt_poiseuille_exact_for_any_tau(oracle, tau):
+    """TRT (Eq. TRT) with the paper's 1/tau- = 8 (2 - 1/tau+)/(8 - 1/tau+), i.e. the
+    combination (tau+ - 1/2)(tau- - 1/2) = 3/16: the halfway-wall Poiseuille parabola is the
+    exact discrete steady state for every tau (BGK reaches it only at one tau)."""
+    H, F = 8, 1e-6
+    z = np.arange(H) + 0.5
+    s = oracle.Sim(1, 1, H, periodic=(1, 1, 0),
+                   params=oracle.default_params(tau=tau, fluid_force=(F, 0, 0),
+                                                collision=oracle.COLLIDE_TRT))
+    nu = (tau - 0.5) / 3.0
+    s.step(int(40 * H * H / nu) + 2000)
+    _, uu = s.moments()
+    ex = F / (2 * nu) * z * (H - z)
+    assert np.abs(uu[0] - ex).max() / ex.max() < 1e-9
+
+
+def test_trt_reduces_to_bgk_when_rates_coincide(oracle):
+    """1/tau- = 1/tau+ where w^2 - 16 w + 16 = 0, w = 8 - 4 sqrt(3): there TRT is BGK
+    (checked on random off-equilibrium cells, with and without solids and forcing)."""
+    g = np.random.default_rng(77)
+    tau = 1.0 / (8.0 - 4.0 * math.sqrt(3.0))
+    for trial in range(20):
+        f = oracle.lattice_tables()[1] * (1.0 + 0.05 * g.standard_normal(19))
+        B = list(g.uniform(0, 0.6, trial % 3))
+        uk = g.normal(0, 0.02, (len(B), 3))
+        arm = g.normal(0, 2, (len(B), 3))
+        force = g.normal(0, 1e-4, 3) if trial % 2 else (0, 0, 0)
+        a = oracle.cell_collide(f, tau, B, uk, arm, force, collision=oracle.COLLIDE_BGK)
+        b = oracle.cell_collide(f, tau, B, uk, arm, force, collision=oracle.COLLIDE_TRT)
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=0, atol=1e-15)
+
+
+def test_trt_conserves_mass_and_momentum(oracle):
+    """The TRT operator changes neither the density nor the momentum of a fluid cell, and
+    relaxes the symmetric and antisymmetric non-equilibrium parts at 1/tau+ and 1/tau-."""
+    g = np.random.default_rng(78)
+    c, t, opp = oracle.lattice_tables()
+    for tau in (0.55, 0.8, 1.5):
+        f = t * (1.0 + 0.05 * g.standard_normal(19))
+        fs, _, _ = oracle.cell_collide(f, tau, collision=oracle.COLLIDE_TRT)
+        assert abs(fs.sum() - f.sum()) < 1e-15
+        assert np.abs(c.T @ fs - c.T @ f).max() < 1e-15
+        rho = f.sum()
+        u = (c.T @ f) / rho
+        feq = oracle.equilibrium(rho, u)
+        wp = 1.0 / tau
+        wm = 8.0 * (2.0 - wp) / (8.0 - wp)
+        neq, neq_out = f - feq, fs - feq
+        sym_in, asym_in = 0.5 * (neq + neq[opp]), 0.5 * (neq - neq[opp])
+        sym_out, asym_out = 0.5 * (neq_out + neq_out[opp]), 0.5 * (neq_out - neq_out[opp])
+        assert np.allclose(sym_out, (1 - wp) * sym_in, rtol=0, atol=1e-15)
+        assert np.allclose(asym_out, (1 - wm) * asym_in, rtol=0, atol=1e-15)
