@@ -153,6 +153,7 @@ def ensemble_measure(args, device, stream):
     cells = sum(w.ncell for w in ws)
     b = ledds.batch_from_workloads(ws, device=device)
     b.step(args.warmup)
+    choice = b.autotune(steps_per_trial=2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -187,7 +188,9 @@ def ensemble_measure(args, device, stream):
             "sims": len(ws), "cells": cells, "particles": int(sum(w.n for w in ws)),
             "separate_sims_MLUPS": cells * args.steps / (serial_ms * 1e-3) / 1e6,
             "speedup_vs_separate_sims": serial_ms / ms,
-            "launches_per_step": 4, "status": bad}
+            "launches_per_step": 4, "autotune_choice": {"psm_ctas_per_sm": choice // 2 + 1,
+                                                         "order": ["member", "largest_first"][choice % 2]},
+            "status": bad}
 
 
 def settling_measure(device, stream):
@@ -290,6 +293,40 @@ def ellipsoid_measure(args, device, stream):
         torch.cuda.empty_cache()
     out["bf16_speedup_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
     return out
+
+
+def fluidised_sweep(device, stream, phis=(0.0, 0.1, 0.2, 0.3, 0.41), steps=10, warmup=3):
+    """The paper's performance workload shape (500x200x800, spheres of diameter 20, n_sub 10,
+    distance fractions, FP32 storage) at increasing solid fraction: MLUPS and stage split."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    rows = []
+    for phi in phis:
+        w = W.fluidised_bed(phi)
+        s = ledds.from_workload(w, device=device)
+        s.step(warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.set_profiling(True)
+        s.step(3)
+        sm_, ps_, _ = s.read_profile()
+        st = s.status()
+        rows.append({"phi": round(w.n * 4.0 / 3.0 * math.pi * 1000.0 / w.ncell, 3), "spheres": w.n,
+                     "value": w.ncell * steps / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+                     "psm_ms": sm_[3] / ps_, "dem_ms": (sm_[0] + sm_[1] + sm_[4]) / ps_,
+                     "overflow": st["tile_overflow"] + st["cand_overflow"] + st["solids_overflow"]})
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+    return {"workload": "fluidised bed 500x200x800 (80 M cells), spheres of diameter 20, density ratio "
+                        "1.1, periodic x and z, walls on y, n_sub 10, distance fractions, FP32",
+            "steps": steps, "sweep": rows,
+            "mlups_ratio_phi0_to_max": rows[0]["value"] / rows[-1]["value"] if rows else None}
 
 
 def oracle_sample(steps):
@@ -453,6 +490,7 @@ def main():
         variants["settling_sphere"] = settling_measure(f"cuda:{local}", stream)
         variants["granular_dem"] = granular_measure(f"cuda:{local}", stream)
         variants["ellipsoid_shear"] = ellipsoid_measure(args, f"cuda:{local}", stream)
+        variants["fluidised_bed"] = fluidised_sweep(f"cuda:{local}", stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

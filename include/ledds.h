@@ -253,6 +253,15 @@ int ledds_batch_step(ledds_batch_t b, int n_steps);
 /* Release the batch and its members' host objects (the workspace stays the caller's). */
 int ledds_batch_destroy(ledds_batch_t b);
 
+/* Autotuner of the batched launch: tries every combination of resident PSM CTAs per SM
+ * (1 up to the compiled register budget) and PSM work order (member order, or largest
+ * members first), times steps_per_trial steps of each with CUDA events after two warm-up
+ * steps, and keeps the fastest. The trial steps are real steps: they advance every member
+ * (each candidate computes the same step). *choice (may be NULL) receives the index
+ * (ctas_per_sm - 1) * 2 + order of the choice. Synchronous. The tile shape (32 x 8 x 16) is
+ * fixed at compile time. Errors: INVALID_ARG, CUDA, and those of ledds_batch_step. */
+int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice);
+
 /* Cell keys and (key, id)-sorted particle ids of the DEM grid, computed without any
  * device allocation. The paper has no counterpart: this entry point exists for callers
  * that cannot allocate device memory themselves, such as code running under a memory

@@ -1003,6 +1003,28 @@ static int ellipsoid_geom(or_sim* s, int i, int j, contact_geom* g) {
     }
     double dist = vnorm(d);
     if (!((s->bound[i] + s->bound[j]) - dist > 0.0)) return 0;
+    /* Separating plane across the centre line (reading: an exact pre-test, Sec. 2.1 does not
+     * say how pairs are screened): the support of an ellipsoid along a unit vector n is
+     * |diag(s) R n| (R rows = body axes). If the supports of i and j along the centre line
+     * do not reach across the centre distance, the plane between them separates the two and
+     * there is no contact; the iteration runs for the other pairs only. */
+    {
+        double n[3], h[2];
+        for (int a = 0; a < 3; ++a) n[a] = d[a] / dist;
+        for (int k = 0; k < 2; ++k) {
+            const int q = k == 0 ? i : j;
+            const double* R = s->triad + 9 * q;
+            const double* sm = s->semi + 3 * q;
+            double t = 0.0;
+            for (int m = 0; m < 3; ++m) {
+                double b = R[3 * m] * n[0] + R[3 * m + 1] * n[1] + R[3 * m + 2] * n[2];
+                double v = sm[m] * b;
+                t = t + v * v;
+            }
+            h[k] = sqrt(t);
+        }
+        if ((h[0] + h[1]) < dist * (1.0 - 1e-12)) return 0;
+    }
     double en[3], cp[3], rho_i, rho_j, delta;
     int iters;
     int rc = or_ellipsoid_contact(s->pos + 3 * i, s->triad + 9 * i, s->semi + 3 * i, rj_img,

@@ -32,6 +32,7 @@ cudaError_t launch_psm_batch(const BatchChunk&, int*, int, int, cudaStream_t);
 cudaError_t launch_bin_batch(const LbmArgs*, const int*, int, cudaStream_t);
 cudaError_t launch_dem_batch(const DemArgs*, const int*, int, int, cudaStream_t);
 cudaError_t launch_final_batch(const DemArgs*, int, cudaStream_t);
+int psm_batch_ctas_per_sm();
 }  // namespace ledds
 
 using namespace ledds;
@@ -69,6 +70,7 @@ struct ledds_sim_s {
     double* whist = nullptr;
     DevStatus* status = nullptr;
     double max_bound = 0.0;  // largest bounding radius of the current particles
+    int any_ellipsoid = 0;   // some current particle is an ellipsoid
     // state
     double uw[3][2][3];
     int parity = 0;          // pop[parity], cand[parity] hold the current data
@@ -323,6 +325,7 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     a.Fh = s->P.Fh;
     a.Mh = s->P.Mh;
     a.voxel = s->p.voxel;
+    a.subdiv_any = s->p.voxel == LEDDS_VOXEL_SUBDIV || s->any_ellipsoid;
     a.subdiv_n = s->p.subdiv_n;
     a.Rc = (float)cbrt(3.0 / (4.0 * kPi));
     a.inv2Rc = (float)(1.0 / (2.0 * cbrt(3.0 / (4.0 * kPi))));
@@ -681,6 +684,8 @@ int ledds_set_particles(ledds_sim_t s, int n, const ledds_particle* h) {
     }
     s->P.n = n;
     s->max_bound = bmax;
+    s->any_ellipsoid = 0;
+    for (int k = 0; k < n; ++k) s->any_ellipsoid |= shape[k] == LEDDS_ELLIPSOID;
     drop_graphs(s);
     if (n > 0) {
         int rc;
@@ -901,6 +906,8 @@ struct CkptHeader {
     long long steps;
     double uw[3][2][3];
     size_t ws_used;
+    double max_bound;  // derived from the particles at upload; not recomputed on load
+    int any_ellipsoid;
 };
 
 int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes) {
@@ -914,8 +921,8 @@ int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes) {
     if (*bytes < need) return LEDDS_ERR_INVALID_ARG;
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "LEDDSCK1", 8);
-    hd.version = 1;
+    memcpy(hd.magic, "LEDDSCK2", 8);
+    hd.version = 2;
     hd.d = s->d;
     hd.p = s->p;
     hd.n = s->P.n;
@@ -923,6 +930,8 @@ int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes) {
     hd.steps = s->steps;
     memcpy(hd.uw, s->uw, sizeof(hd.uw));
     hd.ws_used = used;
+    hd.max_bound = s->max_bound;
+    hd.any_ellipsoid = s->any_ellipsoid;
     memcpy(h_buf, &hd, sizeof(hd));
     if (cudaMemcpyAsync((char*)h_buf + sizeof(hd), s->ws, used, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
@@ -936,7 +945,7 @@ int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     CkptHeader hd;
     memcpy(&hd, h_buf, sizeof(hd));
     size_t used = layout(nullptr, &s->d, &s->p, nullptr) - 256;
-    if (memcmp(hd.magic, "LEDDSCK1", 8) != 0 || hd.ws_used != used || bytes < sizeof(hd) + used ||
+    if (memcmp(hd.magic, "LEDDSCK2", 8) != 0 || hd.ws_used != used || bytes < sizeof(hd) + used ||
         memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0 || hd.p.storage != s->p.storage)
         return LEDDS_ERR_INVALID_ARG;
     if (cudaMemcpyAsync(s->ws, (const char*)h_buf + sizeof(hd), used, cudaMemcpyHostToDevice, s->stream) !=
@@ -948,6 +957,8 @@ int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     s->parity = hd.parity;
     s->steps = hd.steps;
     memcpy(s->uw, hd.uw, sizeof(hd.uw));
+    s->max_bound = hd.max_bound;
+    s->any_ellipsoid = hd.any_ellipsoid;
     drop_graphs(s);
     return LEDDS_OK;
 }
@@ -966,6 +977,8 @@ struct ledds_batch_s {
     int *d_tile_start = nullptr, *d_np = nullptr, *d_poff = nullptr, *d_counter = nullptr;
     int nchunks = 0;
     std::vector<BatchChunk> chunks[2];  // PSM launch arguments per batch parity
+    int ctas_per_sm = 0, sms = 1;        // persistent PSM grid = ctas_per_sm x SMs
+    int order = 0;                       // PSM work order: 0 member order, 1 largest first
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
     std::vector<long long> versions;
 };
@@ -1056,7 +1069,9 @@ int ledds_batch_create(int nsim, const ledds_dims* dims, const ledds_params* par
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->nblocks = 2 * (sms > 0 ? sms : 1);
+    b->sms = sms > 0 ? sms : 1;
+    b->ctas_per_sm = psm_batch_ctas_per_sm();
+    b->nblocks = b->ctas_per_sm * b->sms;  // one wave of resident CTAs
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         ledds_batch_destroy(b);
         return LEDDS_ERR_CUDA;
@@ -1091,6 +1106,13 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
         ts[n + 1 + i] = s->P.n;
         ts[2 * n + 1 + i] = off;
     }
+    // PSM work order: member order, or largest members first (their tiles are taken
+    // first and the small members' tiles fill the tail of the persistent launch)
+    std::vector<int> perm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    if (b->order == 1)
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](int x, int y) { return b->sims[x]->ntiles > b->sims[y]->ntiles; });
     for (int q = 0; q < 2; ++q)
         for (int c = 0; c < b->nchunks; ++c) {
             BatchChunk& ch = b->chunks[q][c];
@@ -1098,8 +1120,9 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
             ch.nsim = cnt;
             ch.tile_start[0] = 0;
             for (int k = 0; k < cnt; ++k) {
-                ch.a[k] = la[q * n + first + k];
-                ch.tile_start[k + 1] = ch.tile_start[k] + b->sims[first + k]->ntiles;
+                const int m = perm[first + k];
+                ch.a[k] = la[q * n + m];
+                ch.tile_start[k + 1] = ch.tile_start[k] + b->sims[m]->ntiles;
             }
         }
     CK(cudaMemcpyAsync(b->d_largs[0], la.data(), sizeof(LbmArgs) * 2 * n, cudaMemcpyHostToDevice, b->stream));
@@ -1161,6 +1184,48 @@ int ledds_batch_step(ledds_batch_t b, int n_steps) {
         }
     }
     return LEDDS_OK;
+}
+
+// Try every (resident PSM CTAs per SM, work order) and keep the fastest, timed with
+// events over steps_per_trial steps after two warm-up steps per candidate (these steps
+// advance the members like ledds_batch_step; every candidate computes the same step).
+int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice) {
+    if (!b || steps_per_trial < 1) return LEDDS_ERR_INVALID_ARG;
+    const int max_cps = psm_batch_ctas_per_sm();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LEDDS_ERR_CUDA;
+    float best = 0.0f;
+    int best_cps = max_cps, best_order = 0, best_id = -1, rc = LEDDS_OK;
+    for (int cps = 1; cps <= max_cps && rc == LEDDS_OK; ++cps)
+        for (int order = 0; order < 2 && rc == LEDDS_OK; ++order) {
+            b->ctas_per_sm = cps;
+            b->nblocks = cps * b->sms;
+            b->order = order;
+            b->versions.clear();  // forces re-upload and fresh graphs
+            if ((rc = ledds_batch_step(b, 2)) != LEDDS_OK) break;
+            float ms = 0.0f;
+            if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = LEDDS_ERR_CUDA; break; }
+            if ((rc = ledds_batch_step(b, steps_per_trial)) != LEDDS_OK) break;
+            if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = LEDDS_ERR_CUDA;
+                break;
+            }
+            if (best_id < 0 || ms < best) {
+                best = ms;
+                best_cps = cps;
+                best_order = order;
+                best_id = (cps - 1) * 2 + order;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ctas_per_sm = best_cps;
+    b->nblocks = best_cps * b->sms;
+    b->order = best_order;
+    b->versions.clear();
+    if (choice) *choice = best_id;
+    return rc;
 }
 
 }  // extern "C"

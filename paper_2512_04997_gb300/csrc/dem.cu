@@ -429,6 +429,23 @@ __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& 
     }
     double dist = norm3(dd);
     if (!((A.P.bound[a] + A.P.bound[b]) - dist > 0.0)) return false;
+    {   // separating plane across the centre line: supports |diag(s) R n| that do not reach
+        // across the centre distance mean no contact (same arithmetic as the reference)
+        double n[3], h[2];
+        for (int c = 0; c < 3; ++c) n[c] = dd[c] / dist;
+        for (int k = 0; k < 2; ++k) {
+            const int q = k == 0 ? a : b;
+            double t = 0.0;
+            for (int m = 0; m < 3; ++m) {
+                double bm = stv(A, st, ST + 3 * m, q) * n[0] + stv(A, st, ST + 3 * m + 1, q) * n[1] +
+                            stv(A, st, ST + 3 * m + 2, q) * n[2];
+                double v = A.P.semi[(long long)m * A.P.cap + q] * bm;
+                t = t + v * v;
+            }
+            h[k] = sqrt(t);
+        }
+        if ((h[0] + h[1]) < dist * (1.0 - 1e-12)) return false;
+    }
     double ra[3], rb[3], Ra_[9], Rb_[9], sa[3], sb[3];
     for (int c = 0; c < 3; ++c) {
         ra[c] = stv(A, st, SP + c, a);

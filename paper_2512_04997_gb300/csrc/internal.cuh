@@ -150,6 +150,7 @@ struct LbmArgs {
     const int* shape;
     double *Fh, *Mh;
     int voxel, subdiv_n;
+    int subdiv_any;               // subdivision fractions requested or some particle an ellipsoid
     float Rc, inv2Rc;
     DevStatus* status;
 };

@@ -323,6 +323,8 @@ struct TileCache {
     double p[3][MAX_TILE_CAP];    // centre (FP64) for the exact subdivision path
     float m[9][MAX_TILE_CAP];     // ellipsoid rows fl32(d_j / semi_j)
     double acc[6][MAX_TILE_CAP];  // force and torque sums of this tile
+    float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
+    float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
 };
 
 __device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
@@ -344,6 +346,10 @@ __device__ __forceinline__ float min_image_f(float d, int per, float L) {
 
 __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int cnt, int x0, int y0,
                           int z0) {
+    if (threadIdx.x < 16) {
+        const int n = a.subdiv_n;
+        tc.so[threadIdx.x] = (int)threadIdx.x < n ? __fdiv_rn((float)(2 * (int)threadIdx.x + 1 - n), (float)(2 * n)) : 0.0f;
+    }
     const double org[3] = {(double)x0, (double)y0, (double)z0};
     const double Ls[3] = {(double)a.nx, (double)a.ny, (double)a.nz};
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
@@ -369,75 +375,66 @@ __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int cnt, in
                 for (int c = 0; c < 3; ++c)
                     tc.m[3 * j + c][e] = __double2float_rn(
                         a.st[(ST + 3 * j + c) * a.pcap + k] / a.semi[j * a.pcap + k]);
+            const double smin = fmin(a.semi[k], fmin(a.semi[a.pcap + k], a.semi[2 * a.pcap + k]));
+            tc.ims[e] = (float)(1.0 / smin);
         }
         for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0;
     }
 }
 
-// Subdivision count: n^3 sample points (2m+1-n)/(2n) around the node, strictly inside
-// the solid. FP32 with explicit round-to-nearest intrinsics (no contraction), in the
-// evaluation order documented for the method, so counts are exact integers. Kept out of
-// line: it runs only for nodes the exact early-outs cannot decide.
-__device__ __noinline__ int subdiv_count(const TileCache& tc, int e, float px, float py, float pz,
-                                         int n) {
-    float o[16];
-    for (int q = 0; q < n; ++q) o[q] = __fdiv_rn((float)(2 * q + 1 - n), (float)(2 * n));
+// Subdivision count (Sec. 2.4): n^3 sample points (2m+1-n)/(2n) around the node, strictly
+// inside the solid, for the node at offset (px, py, pz) from cached particle e. Computed by
+// the whole warp (every lane passes the same arguments): lane l takes the sample columns
+// (j, q) = l, l + 32, ... for every i, and the counts are summed exactly. FP32 with explicit
+// round-to-nearest intrinsics (no contraction) in the evaluation order documented for the
+// method, so the count is exact and independent of the split.
+__device__ __forceinline__ int subdiv_count_warp(const TileCache& tc, int e, float px, float py, float pz,
+                                                 int n) {
+    const int lane = threadIdx.x & 31;
+    const int nn = n * n;
     int count = 0;
     if (tc.shape[e] == LEDDS_SPHERE) {
         const float R2 = tc.R2[e];
-        for (int i = 0; i < n; ++i) {
-            float dx = __fadd_rn(px, o[i]);
-            float xx = __fmul_rn(dx, dx);
-            for (int j = 0; j < n; ++j) {
-                float dy = __fadd_rn(py, o[j]);
-                float s01 = __fadd_rn(xx, __fmul_rn(dy, dy));
-                for (int q = 0; q < n; ++q) {
-                    float dz = __fadd_rn(pz, o[q]);
-                    count += __fadd_rn(s01, __fmul_rn(dz, dz)) < R2;
-                }
+        for (int jq = lane; jq < nn; jq += 32) {
+            const int j = jq / n, q = jq - j * n;
+            const float dy = __fadd_rn(py, tc.so[j]);
+            const float dz = __fadd_rn(pz, tc.so[q]);
+            const float yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+            for (int i = 0; i < n; ++i) {
+                const float dx = __fadd_rn(px, tc.so[i]);
+                count += __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), yy), zz) < R2;
             }
         }
     } else {
         float mm[9];
-        for (int q = 0; q < 9; ++q) mm[q] = tc.m[q][e];
-        for (int i = 0; i < n; ++i) {
-            float dx = __fadd_rn(px, o[i]);
-            float a0 = __fmul_rn(mm[0], dx), a1 = __fmul_rn(mm[3], dx), a2 = __fmul_rn(mm[6], dx);
-            for (int j = 0; j < n; ++j) {
-                float dy = __fadd_rn(py, o[j]);
-                float t0 = __fadd_rn(a0, __fmul_rn(mm[1], dy));
-                float t1 = __fadd_rn(a1, __fmul_rn(mm[4], dy));
-                float t2 = __fadd_rn(a2, __fmul_rn(mm[7], dy));
-                for (int q = 0; q < n; ++q) {
-                    float dz = __fadd_rn(pz, o[q]);
-                    float q0 = __fadd_rn(t0, __fmul_rn(mm[2], dz));
-                    float q1 = __fadd_rn(t1, __fmul_rn(mm[5], dz));
-                    float q2 = __fadd_rn(t2, __fmul_rn(mm[8], dz));
-                    float s = __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2));
-                    count += s < 1.0f;
-                }
+        for (int k = 0; k < 9; ++k) mm[k] = tc.m[k][e];
+        for (int jq = lane; jq < nn; jq += 32) {
+            const int j = jq / n, q = jq - j * n;
+            const float dy = __fadd_rn(py, tc.so[j]);
+            const float dz = __fadd_rn(pz, tc.so[q]);
+            for (int i = 0; i < n; ++i) {
+                const float dx = __fadd_rn(px, tc.so[i]);
+                const float t0 = __fadd_rn(__fmul_rn(mm[0], dx), __fmul_rn(mm[1], dy));
+                const float t1 = __fadd_rn(__fmul_rn(mm[3], dx), __fmul_rn(mm[4], dy));
+                const float t2 = __fadd_rn(__fmul_rn(mm[6], dx), __fmul_rn(mm[7], dy));
+                const float q0 = __fadd_rn(t0, __fmul_rn(mm[2], dz));
+                const float q1 = __fadd_rn(t1, __fmul_rn(mm[5], dz));
+                const float q2 = __fadd_rn(t2, __fmul_rn(mm[8], dz));
+                count += __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2)) < 1.0f;
             }
         }
     }
-    return count;
+    return __reduce_add_sync(0xffffffffu, count);
 }
 
-// Exact subdivision path: node minus centre in FP64 (minimum image), rounded to FP32.
-__device__ __noinline__ float beta_subdiv_exact(const LbmArgs& a, const TileCache& tc, int e, int x,
-                                                int y, int z) {
-    const int n = a.subdiv_n;
-    float px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
-    float py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
-    float pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
-    int cnt = subdiv_count(tc, e, px, py, pz, n);
-    return (float)cnt / (float)(n * n * n);
-}
-
-// Solid fraction of cached particle e at node (x,y,z); (dx,dy,dz) = node - centre (FP32).
-__device__ __forceinline__ float beta_of(const LbmArgs& a, const TileCache& tc, int e, int x, int y,
-                                         int z, float dx, float dy, float dz, float R) {
+// Solid fraction of cached particle e at a node, (dx,dy,dz) = node - centre (FP32), where
+// it follows from the distance (Eq. naiveSolidFrac) or from the exact early-outs of the
+// subdivision method; *exact is set when the subdivision count itself is needed.
+__device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& tc, int e, float dx, float dy,
+                                            float dz, float R, bool* exact) {
     const int sh = tc.shape[e];
     const float d2 = dx * dx + dy * dy + dz * dz;
+    *exact = false;
     if (sh == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) {
         // Eq. (naiveSolidFrac): (R + R_c - d) / (2 R_c), clamped
         float dsc = R + a.Rc - sqrtf(d2);
@@ -453,6 +450,17 @@ __device__ __forceinline__ float beta_of(const LbmArgs& a, const TileCache& tc, 
         const float nearr = R - hd - 1e-3f;
         if (nearr > 0.0f && d2 < nearr * nearr) return 1.0f;  // ... or every sample is
     } else {
+        // normalised radius |M p| of the node (M rows d_j / semi_j, |M| = 1/min semi-axis):
+        // samples within hd of the node lie within hd |M| of it, so beyond the surface by
+        // more than that (plus margins far above FP32 rounding) none is inside, and inside
+        // by more than that every one is
+        const float q0 = tc.m[0][e] * dx + tc.m[1][e] * dy + tc.m[2][e] * dz;
+        const float q1 = tc.m[3][e] * dx + tc.m[4][e] * dy + tc.m[5][e] * dz;
+        const float q2 = tc.m[6][e] * dx + tc.m[7][e] * dy + tc.m[8][e] * dz;
+        const float rn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+        const float ext = hd * tc.ims[e] * 1.001f + 1e-3f;
+        if (rn - ext > 1.0f) return 0.0f;
+        if (rn + ext < 1.0f) return 1.0f;
         // every corner of the sample box strictly inside (convexity) => all samples are
         bool all_in = true;
 #pragma unroll
@@ -467,7 +475,8 @@ __device__ __forceinline__ float beta_of(const LbmArgs& a, const TileCache& tc, 
         }
         if (all_in) return 1.0f;
     }
-    return beta_subdiv_exact(a, tc, e, x, y, z);
+    *exact = true;
+    return 0.0f;
 }
 
 // Row prefilter: which cached particles can touch the x-row (ly, lz) of this tile.
@@ -502,9 +511,36 @@ __device__ __forceinline__ bool ranks_before(const TileCache& tc, float b, int e
     return b > bw || (b == bw && tc_pid(tc, e) < tc_pid(tc, ew));
 }
 
+// Exact subdivision counts for the lanes in `need`, one node after the other, each counted
+// by the whole warp; the node minus the centre is taken in FP64 (minimum image) and rounded
+// to FP32. Out of line, entered by every lane together: it keeps the hot loop small.
+__device__ __noinline__ float subdiv_lanes(const LbmArgs& a, const TileCache& tc, int e, unsigned need,
+                                           bool exact, int x, int y, int z, float b) {
+    const int lane = threadIdx.x & 31;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (exact) {
+        px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
+        py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
+        pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
+    }
+    const int n = a.subdiv_n;
+    while (need) {
+        const int l = __ffs(need) - 1;
+        need &= need - 1;
+        const float qx = __shfl_sync(0xffffffffu, px, l);
+        const float qy = __shfl_sync(0xffffffffu, py, l);
+        const float qz = __shfl_sync(0xffffffffu, pz, l);
+        const int c = subdiv_count_warp(tc, e, qx, qy, qz, n);
+        if (lane == l) b = (float)c / (float)(n * n * n);
+    }
+    return b;
+}
+
+// Called by the whole warp (the row mask is uniform); lanes with valid false take no part
+// beyond the warp-wide subdivision counts.
 __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
                                             unsigned long long mask, int lx, int ly, int lz, int x,
-                                            int y, int z, Two& t) {
+                                            int y, int z, bool valid, Two& t) {
     t.ns = 0;
     t.total = 0;
     t.e0 = t.e1 = 0;
@@ -516,7 +552,12 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& t
         float dx = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
         float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
         float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
-        float b = beta_of(a, tc, e, x, y, z, dx, dy, dz, ps.w);
+        bool exact = false;
+        float b = valid ? beta_quick(a, tc, e, dx, dy, dz, ps.w, &exact) : 0.0f;
+        if (a.subdiv_any) {  // uniform: distance-fraction spheres never need counts
+            const unsigned need = __ballot_sync(0xffffffffu, exact);
+            if (need) b = subdiv_lanes(a, tc, e, need, exact, x, y, z, b);  // uniform branch
+        }
         if (!(b > 0.0f)) continue;
         t.total++;
         if (t.ns == 0) {
@@ -987,7 +1028,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         Two t;
         t.ns = 0;
         t.total = 0;
-        if (valid && mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, t);
+        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
         if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
 
         // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
@@ -1114,8 +1155,12 @@ __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const 
 // simulations of uneven sizes advance in one launch with balanced load. The members'
 // arguments travel in the launch's parameter block (read-only for the whole launch, like
 // the single-simulation kernel's argument), up to BATCH_CHUNK members per launch.
+// The batched kernel indexes its members' arguments at run time and runs best with the
+// larger register budget (2 resident CTAs per SM) for every storage format.
+constexpr int PSM_BATCH_MINB = 2;
+
 template <int STORE, bool TRT>
-__global__ void __launch_bounds__(PSM_THREADS, 2) k_psm_batch(const __grid_constant__ BatchChunk P,
+__global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const __grid_constant__ BatchChunk P,
                                                                           int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item, s_sim;
@@ -1183,6 +1228,8 @@ __global__ void k_bin_batch(const LbmArgs* args, const int* np) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) bin_particle(a, k, tcount, tids);
 }
 
+int psm_batch_ctas_per_sm() { return PSM_BATCH_MINB; }
+
 size_t psm_smem_bytes(int store) {
     const int stages = store == LEDDS_STORE_F32 ? PsmCfg<LEDDS_STORE_F32>::stages : PsmCfg<LEDDS_STORE_F16>::stages;
     return ((sizeof(TileCache) + 15) & ~(size_t)15) + sizeof(uint32_t) * stages * 19 * PSM_THREADS;
@@ -1202,11 +1249,12 @@ __global__ void __launch_bounds__(256) k_voxelize(const LbmArgs a, float* beta, 
         const int z = z0 + iz;
         if (y >= a.ny || z >= a.nz) break;
         const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
-        if (x >= a.nx) continue;
+        const bool valid = x < a.nx;
         Two t;
         t.ns = 0;
         t.total = 0;
-        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, t);
+        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+        if (!valid) continue;
         long long cell = x + (long long)a.nx * (y + (long long)a.ny * z);
         beta[2 * cell] = t.ns > 0 ? t.b0 : 0.f;
         beta[2 * cell + 1] = t.ns > 1 ? t.b1 : 0.f;

@@ -91,6 +91,7 @@ _SIGS = {
     "ledds_batch_sim": (C.c_int, [VP, C.c_int, C.POINTER(VP)]),
     "ledds_batch_step": (C.c_int, [VP, C.c_int]),
     "ledds_batch_destroy": (C.c_int, [VP]),
+    "ledds_batch_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -409,6 +410,12 @@ class Batch:
 
     def sync(self):
         self.torch.cuda.synchronize()
+
+    def autotune(self, steps_per_trial=4):
+        """Choose the persistent launch shape and work order by timing (advances the members)."""
+        c = C.c_int(-1)
+        check("ledds_batch_autotune", lib().ledds_batch_autotune(self.h, int(steps_per_trial), C.byref(c)))
+        return c.value
 
     def close(self):
         if getattr(self, "h", None):

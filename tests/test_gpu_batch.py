@@ -73,3 +73,27 @@ def test_batch_fp16_storage_error():
         _, u16 = m16.fields()
         _, u32 = m32.fields()
         assert normwise(u16.cpu().numpy(), u32.cpu().numpy()) < 2e-3
+
+
+def test_batch_autotune_keeps_the_step():
+    """The autotuner's trial steps are ordinary steps: after it (and more steps), every
+    member still matches the same simulation stepped on its own as often."""
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=6, seed_index=58, storage="f32")
+    b = ledds.batch_from_workloads(ws)
+    choice = b.autotune(steps_per_trial=2)
+    assert 0 <= choice < 8
+    b.step(3)
+    steps = b.members[0].status()["steps"]
+    assert steps >= 4 + 3
+    for w, m in zip(ws, b.members):
+        assert m.status()["steps"] == steps
+        s = gpu_from_workload(w)
+        s.step(steps)
+        _, u_b = m.fields()
+        _, u_s = s.fields()
+        assert normwise(u_b.cpu().numpy(), u_s.cpu().numpy()) < 1e-6
+        if w.n:
+            pb, _, _, _ = m.particles()
+            ps, _, _, _ = s.particles()
+            assert np.abs(pb - ps).max() < 1e-6

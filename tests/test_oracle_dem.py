@@ -369,3 +369,38 @@ def test_eccentric_ellipsoids_energy(oracle):
         out.append(abs(E1 - E0) / E0)
     assert 0.3 * c["energy_change_reported"] < out[0] < 5 * c["energy_change_reported"]
     assert abs(out[1] / out[0] - 1.0) < 0.1
+
+
+def test_ellipsoid_contact_decision_matches_perram_wertheim(oracle):
+    """The contact decision for ellipsoid pairs (bounding spheres, the separating-plane
+    pre-test, then the common-normal iteration) agrees with the exact Perram-Wertheim
+    overlap criterion on random pairs at random orientations; pairs within 2 % of
+    tangency (contact function within [0.98, 1.02]) are left out."""
+    g = np.random.default_rng(91)
+    semi = np.array([1.5, 0.6, 0.5])
+    agree = checked = contacts = 0
+    for _ in range(300):
+        q = W.random_quaternions(g, 2)
+        tri = W.quaternion_to_triad(q)
+        d = g.normal(size=3)
+        d *= g.uniform(0.5, 3.2) / np.linalg.norm(d)
+        pos = np.array([[5.0, 5.0, 5.0], 5.0 + d])
+        # Perram-Wertheim contact function maximum by dense scan (independent of the oracle)
+        R = tri.reshape(2, 3, 3)
+        Ainv = [Rk.T @ np.diag(semi ** 2) @ Rk for Rk in R]
+        lam = np.linspace(1e-4, 1 - 1e-4, 4001)
+        Fmax = max(l * (1 - l) * d @ np.linalg.solve((1 - l) * Ainv[0] + l * Ainv[1], d) for l in lam)
+        if 0.98 < Fmax < 1.02:
+            continue
+        p = oracle.default_params(law=oracle.LAW_HERTZ, young=10.0, rho_f=0.0, dem_h=3.2,
+                                  ell_max_iter=400, ell_tol=1e-10)
+        s = oracle.Sim(params=p, box_lo=(0, 0, 0), box_hi=(10, 10, 10), periodic=(1, 1, 1),
+                       max_particles=2)
+        s.set_particles(np.ones(2, dtype=np.int32), np.full(2, semi.max()), np.tile(semi, (2, 1)),
+                        np.ones(2), pos, triad=tri)
+        c = s.contacts()
+        checked += 1
+        contacts += len(c) > 0
+        agree += (len(c) > 0) == (Fmax < 1.0)
+    assert checked > 150 and contacts > 30
+    assert agree == checked
