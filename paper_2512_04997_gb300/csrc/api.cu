@@ -63,6 +63,9 @@ struct ledds_sim_s {
     int G = 1;
     uint32_t *keys = nullptr, *cell_count = nullptr, *cell_start = nullptr, *scan_partial = nullptr;
     uint32_t *pair_cnt = nullptr, *pair_off = nullptr;
+    uint32_t* cp_list = nullptr;  // canonical pair list (pair-once evaluation)
+    double* cp_res = nullptr;     // per-pair force and torques
+    long long cp_stride = 0;
     int *rank = nullptr, *sorted = nullptr;
     int* cand[2] = {nullptr, nullptr};
     int* ncand[2] = {nullptr, nullptr};
@@ -207,6 +210,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
     double* h0 = c.take<double>((size_t)capc * ccap * 3);
     double* h1 = c.take<double>((size_t)capc * ccap * 3);
     double* wh = c.take<double>((size_t)capc * 18);
+    uint32_t* cplist = c.take<uint32_t>((size_t)capc * ccap);
+    double* cpres = c.take<double>((size_t)capc * ccap * 9);
     DevStatus* status = c.take<DevStatus>(1);
     size_t total = c.off + 256;
     if (s && base) {
@@ -258,6 +263,9 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
         s->hist[0] = h0;
         s->hist[1] = h1;
         s->whist = wh;
+        s->cp_list = cplist;
+        s->cp_res = cpres;
+        s->cp_stride = (long long)capc * ccap;
         s->status = status;
         for (int a = 0; a < 3; ++a) {
             s->gn[a] = gn[a];
@@ -369,6 +377,12 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     A.ell_max_iter = s->p.ell_max_iter;
     A.ell_tol = s->p.ell_tol;
     A.force_f32 = s->p.force_fp32;
+    A.pair_once = s->any_ellipsoid;
+    A.cp_cnt = s->pair_cnt;
+    A.cp_off = s->pair_off;
+    A.cp_list = s->cp_list;
+    A.cp_res = s->cp_res;
+    A.cp_stride = s->cp_stride;
     A.ccap = s->ccap;
     A.keys = s->keys;
     A.rank = s->rank;
@@ -417,12 +431,13 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
     if (n > 0) {
         CK(launch_predict_first(A, st));
         *launches += 1;
+        const int contact_launches = A.pair_once ? 2 : 1;  // pair forces + gather, or one kernel
         for (int sub = 1; sub < nsub; ++sub) {
             CK(launch_substep(A, (sub - 1) & 1, sub & 1, p ^ 1, 1, 1, st));
-            *launches += 2;
+            *launches += contact_launches + 1;
         }
         CK(launch_substep(A, last, last, p ^ 1, 0, 0, st));
-        *launches += 1;
+        *launches += contact_launches;
     }
     if (ev) CK(cudaEventRecord(ev[2], st));
     if (s->lattice) {

@@ -875,6 +875,236 @@ __device__ void wall_contrib_f(const DemArgs& A, const double* st, int i, int fa
     }
 }
 
+// ------------------------------------------------------------------------------------
+// Pair-once evaluation (simulations with ellipsoids, whose common-normal geometry is
+// costly): the canonical pairs (i < j) of the candidate lists are listed once per rebuild;
+// each substep evaluates every pair once, one thread per pair, and each particle then
+// gathers +/-F and its torque. Both members receive exactly opposite forces.
+// ------------------------------------------------------------------------------------
+// First slot of particle i's (ascending) candidate list whose id exceeds v.
+__device__ __forceinline__ int first_above(const int* cl, int nc, int v) {
+    int lo = 0, hi = nc;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cl[mid] <= v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_cpair_count(DemArgs A, int cb, uint32_t* cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.P.n) return;
+    const int nc = A.ncand[cb][i];
+    cnt[i] = (uint32_t)(nc - first_above(A.cand[cb] + (long long)i * A.ccap, nc, i));
+}
+
+// pair code = i * MAX_CAND_CAP + slot
+__global__ void k_cpair_emit(DemArgs A, int cb, const uint32_t* off, uint32_t* pim) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.P.n) return;
+    const int nc = A.ncand[cb][i];
+    uint32_t o = off[i];
+    for (int m = first_above(A.cand[cb] + (long long)i * A.ccap, nc, i); m < nc; ++m)
+        pim[o++] = (uint32_t)i * MAX_CAND_CAP + (uint32_t)m;
+}
+
+// Canonical pair (a, slot m of a, partner b > a): force on a and the torques on a and b,
+// FP64 contact arithmetic; updates the slot's tangential history. False if no contact.
+__device__ bool pair_force_d(const DemArgs& A, const double* st, int cb, int a, int m, double F[3],
+                             double Ma[3], double Mb[3]) {
+    const int b = A.cand[cb][(long long)a * A.ccap + m];
+    double* hl = A.hist[cb] + ((long long)a * A.ccap + m) * 3;
+    Geo g;
+    if (!pair_geo(A, st, a, b, g)) {
+        hl[0] = hl[1] = hl[2] = 0.0;
+        return false;
+    }
+    double va[3], wa[3], vb[3], wb[3], h[3], Ft[3];
+    ld3(A, st, SV, a, va);
+    ld3(A, st, SW, a, wa);
+    ld3(A, st, SV, b, vb);
+    ld3(A, st, SW, b, wb);
+    for (int c = 0; c < 3; ++c) h[c] = hl[c];
+    double Rstar = 1.0 / (1.0 / g.Ra + 1.0 / g.Rb);
+    double mstar = 1.0 / (1.0 / A.P.mass[a] + 1.0 / A.P.mass[b]);
+    spring_dashpot(A, g, Rstar, mstar, va, wa, vb, wb, h, F, Ft);
+    for (int c = 0; c < 3; ++c) hl[c] = h[c];
+    if (g.sphere) {
+        double mr[3];
+        cross3(g.en, Ft, mr);
+        for (int c = 0; c < 3; ++c) {
+            Ma[c] = -g.Ra * mr[c];
+            Mb[c] = -g.Rb * mr[c];
+        }
+    } else {
+        double mF[3] = {-F[0], -F[1], -F[2]};
+        cross3(g.rca, F, Ma);
+        cross3(g.rcb, mF, Mb);
+    }
+    return true;
+}
+
+// The same with FP32 contact arithmetic.
+__device__ bool pair_force_f(const DemArgs& A, const double* st, int cb, int a, int m, float F[3], float Ma[3],
+                             float Mb[3]) {
+    const int b = A.cand[cb][(long long)a * A.ccap + m];
+    double* hl = A.hist[cb] + ((long long)a * A.ccap + m) * 3;
+    GeoF g;
+    bool hit_;
+    if (A.P.shape[a] == LEDDS_SPHERE && A.P.shape[b] == LEDDS_SPHERE) {
+        double dd[3];
+        for (int c = 0; c < 3; ++c) dd[c] = min_image(A, c, stv(A, st, SP + c, a) - stv(A, st, SP + c, b));
+        hit_ = sphere_geo_f(dd, A.P.radius[a], A.P.radius[b], g);
+    } else {
+        hit_ = pair_geo_f_general(A, st, a, b, g);
+    }
+    if (!hit_) {
+        hl[0] = hl[1] = hl[2] = 0.0;
+        return false;
+    }
+    float dv[3], wa[3], wb[3], h[3], Ft[3];
+    for (int c = 0; c < 3; ++c) {
+        dv[c] = (float)(stv(A, st, SV + c, a) - stv(A, st, SV + c, b));
+        wa[c] = (float)stv(A, st, SW + c, a);
+        wb[c] = (float)stv(A, st, SW + c, b);
+        h[c] = (float)hl[c];
+    }
+    const float Rstar = g.Ra * g.Rb / (g.Ra + g.Rb);
+    const float ma = (float)A.P.mass[a], mb = (float)A.P.mass[b];
+    const float mstar = ma * mb / (ma + mb);
+    spring_dashpot_f(A, g, Rstar, mstar, dv, wa, wb, h, F, Ft);
+    for (int c = 0; c < 3; ++c) hl[c] = (double)h[c];
+    if (g.sphere) {
+        float mr[3];
+        cross3f(g.en, Ft, mr);
+        for (int c = 0; c < 3; ++c) {
+            Ma[c] = -g.Ra * mr[c];
+            Mb[c] = -g.Rb * mr[c];
+        }
+    } else {
+        float mF[3] = {-F[0], -F[1], -F[2]};
+        cross3f(g.rca, F, Ma);
+        cross3f(g.rcb, mF, Mb);
+    }
+    return true;
+}
+
+// One thread per canonical pair: results [9][pcap] (F, Ma, Mb), FP32 values with FP32
+// contact arithmetic, FP64 values otherwise (a pair out of contact stores zeros).
+__global__ void __launch_bounds__(128) k_pair_forces(DemArgs A, int in, int cb, const uint32_t* off,
+                                                     const uint32_t* pim, void* res, long long pcap) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= (long long)off[A.P.n]) return;
+    const uint32_t code = pim[p];
+    const int a = (int)(code / MAX_CAND_CAP), m = (int)(code % MAX_CAND_CAP);
+    const double* st = A.P.st[in];
+    if (A.force_f32) {
+        float F[3] = {0.f, 0.f, 0.f}, Ma[3] = {0.f, 0.f, 0.f}, Mb[3] = {0.f, 0.f, 0.f};
+        pair_force_f(A, st, cb, a, m, F, Ma, Mb);
+        float* r = static_cast<float*>(res);
+        for (int c = 0; c < 3; ++c) {
+            r[c * pcap + p] = F[c];
+            r[(3 + c) * pcap + p] = Ma[c];
+            r[(6 + c) * pcap + p] = Mb[c];
+        }
+    } else {
+        double F[3] = {0.0, 0.0, 0.0}, Ma[3] = {0.0, 0.0, 0.0}, Mb[3] = {0.0, 0.0, 0.0};
+        pair_force_d(A, st, cb, a, m, F, Ma, Mb);
+        double* r = static_cast<double*>(res);
+        for (int c = 0; c < 3; ++c) {
+            r[c * pcap + p] = F[c];
+            r[(3 + c) * pcap + p] = Ma[c];
+            r[(6 + c) * pcap + p] = Mb[c];
+        }
+    }
+}
+
+// Index of particle i's pair with candidate slot q (partner j) in the pair list, or -1
+// when j's list does not hold i (possible only after a candidate-list overflow, which
+// the status reports; the candidate relation is otherwise symmetric).
+__device__ __forceinline__ long long pair_index(const DemArgs& A, int cb, const uint32_t* off, int i, int q,
+                                                int j, int first_i, bool* owner) {
+    if (j > i) {
+        *owner = true;
+        return (long long)off[i] + (q - first_i);
+    }
+    *owner = false;
+    const int* lj = A.cand[cb] + (long long)j * A.ccap;
+    const int ncj = A.ncand[cb][j];
+    const int slot = first_above(lj, ncj, i) - 1;
+    if (slot < 0 || lj[slot] != i) return -1;
+    return (long long)off[j] + (slot - first_above(lj, ncj, j));
+}
+
+// Warp per particle: gather the pair results and the wall contacts (Fc, Mc).
+__global__ void __launch_bounds__(128, 6) k_contacts_gather(DemArgs A, int in, int cb, const uint32_t* off,
+                                                            const void* res, long long pcap) {
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (k >= A.P.n) return;  // uniform across the warp
+    const int lane = threadIdx.x & 31;
+    const int nc = A.ncand[cb][k];
+    const int* cl = A.cand[cb] + (long long)k * A.ccap;
+    const int first_k = first_above(cl, nc, k);
+    const double* st = A.P.st[in];
+    double Fd[3], Md[3];
+    if (A.force_f32) {
+        const float* r = static_cast<const float*>(res);
+        F2 f[3], mo[3];
+        for (int c = 0; c < 3; ++c) f[c] = mo[c] = F2{0.0f, 0.0f};
+        for (int q = lane; q < nc; q += 32) {
+            bool own;
+            const long long p = pair_index(A, cb, off, k, q, cl[q], first_k, &own);
+            if (p < 0) continue;
+            for (int c = 0; c < 3; ++c) {
+                const float fv = r[c * pcap + p];
+                f[c] = f2_add(f[c], own ? fv : -fv);
+                mo[c] = f2_add(mo[c], r[((own ? 3 : 6) + c) * pcap + p]);
+            }
+        }
+        if (lane < 6) wall_contrib_f(A, st, k, lane, f, mo);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F2 of{__shfl_xor_sync(0xffffffffu, f[c].hi, o), __shfl_xor_sync(0xffffffffu, f[c].lo, o)};
+                F2 om{__shfl_xor_sync(0xffffffffu, mo[c].hi, o), __shfl_xor_sync(0xffffffffu, mo[c].lo, o)};
+                f[c] = f2_add(f[c], of);
+                mo[c] = f2_add(mo[c], om);
+            }
+        for (int c = 0; c < 3; ++c) {
+            Fd[c] = (double)f[c].hi + (double)f[c].lo;
+            Md[c] = (double)mo[c].hi + (double)mo[c].lo;
+        }
+    } else {
+        const double* r = static_cast<const double*>(res);
+        for (int c = 0; c < 3; ++c) Fd[c] = Md[c] = 0.0;
+        for (int q = lane; q < nc; q += 32) {
+            bool own;
+            const long long p = pair_index(A, cb, off, k, q, cl[q], first_k, &own);
+            if (p < 0) continue;
+            for (int c = 0; c < 3; ++c) {
+                const double fv = r[c * pcap + p];
+                Fd[c] += own ? fv : -fv;
+                Md[c] += r[((own ? 3 : 6) + c) * pcap + p];
+            }
+        }
+        if (lane < 6) wall_contrib(A, st, k, lane, Fd, Md);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Fd[c] += __shfl_xor_sync(0xffffffffu, Fd[c], o);
+                Md[c] += __shfl_xor_sync(0xffffffffu, Md[c], o);
+            }
+    }
+    if (lane != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        A.P.Fc[(long long)a * A.P.cap + k] = Fd[a];
+        A.P.Mc[(long long)a * A.P.cap + k] = Md[a];
+    }
+}
+
 // Warp-cooperative contact sum of particle i: lane l evaluates candidate slots l, l+32
 // and wall face l (l < 6); a fixed butterfly sums the lanes (deterministic order): in
 // FP64 with FP64 contact arithmetic, in compensated FP32 pairs (converted to FP64 at the
@@ -1280,6 +1510,13 @@ cudaError_t launch_rebuild(const DemArgs& A, int ob, int nb, uint32_t* scan_part
     k_segsort<<<nblk(A.G, 128), 128, 0, s>>>(A);
     k_candidates<<<nblk(n, CAND_WARPS), 32 * CAND_WARPS, 0, s>>>(A, ob, nb);
     *launches += 7;
+    if (A.pair_once) {  // canonical pair list of the new candidate lists
+        k_cpair_count<<<nblk(n, 128), 128, 0, s>>>(A, nb, A.cp_cnt);
+        e = launch_scan(A.cp_cnt, n, A.cp_off, scan_partial, s);
+        if (e != cudaSuccess) return e;
+        k_cpair_emit<<<nblk(n, 128), 128, 0, s>>>(A, nb, A.cp_off, A.cp_list);
+        *launches += 5;
+    }
     return cudaGetLastError();
 }
 
@@ -1293,7 +1530,14 @@ cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
 // do_step = 0: contact forces only.
 cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
-    k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
+    if (A.pair_once) {
+        const long long maxp = (long long)A.P.n * A.ccap;  // every slot may hold an owned pair
+        k_pair_forces<<<(unsigned)((maxp + 127) / 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_list, A.cp_res,
+                                                                     A.cp_stride);
+        k_contacts_gather<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_res, A.cp_stride);
+    } else {
+        k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
+    }
     if (do_step) k_integrate<<<nblk(A.P.n, 32), 32, 0, s>>>(A, in, out);
     return cudaGetLastError();
 }

@@ -184,6 +184,12 @@ struct DemArgs {
     int ell_max_iter;
     double ell_tol;
     int force_f32;  // FP32 contact arithmetic, FP64 sums
+    // pair-once evaluation (simulations with ellipsoids): canonical pair counts, offsets
+    // (n + 1), list (i * MAX_CAND_CAP + slot) and results [9][cp_stride]
+    int pair_once;
+    uint32_t *cp_cnt, *cp_off, *cp_list;
+    void* cp_res;
+    long long cp_stride;
     // lists
     int ccap;
     uint32_t* keys;

@@ -1049,6 +1049,25 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         const float usq = ux * ux + uy * uy + uz * uz;
         const float base = drho - rho * 1.5f * usq;
 
+        const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
+        // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
+        g[0] -= TW(0) * base;
+        // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
+        // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
+        if (!__any_sync(FULL, t.ns > 0)) {
+            // no lane of the warp meets a solid at this node (uniform): plain BGK/TRT, and
+            // nothing to add to the held force sums
+            const float keep = TRT ? 1.0f - 0.5f * (omega + a.omega_m) : 1.0f - omega;
+            const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
+            SolidSums m;
+            m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
+            CollidePairs<SS, 1, false, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep, kB,
+                                                 a.guo_pref_m, m, pout + pl.cell, valid);
+            float out0 = TW(0) * base + (1.0f - omega) * g[0];
+            if (a.has_force) out0 += a.guo_pref * TW(0) * (-3.0f * Fu);
+            if (valid) SS::store(pout + pl.cell, out0, a.scale);
+            continue;
+        }
         // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
         SolidAt q0, q1;
         q0.B = q1.B = 0.f;
@@ -1058,23 +1077,16 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
         if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
         const float Btot = fminf(q0.B + q1.B, 1.0f);
-        // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
-        // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
         const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
         const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
         const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
         const float force_w = (1.0f - Btot) * a.guo_pref;
         const float force_wa = (1.0f - Btot) * a.guo_pref_m;
-        const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
         // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
         const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
         const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
-
-        // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
-        g[0] -= TW(0) * base;
         SolidSums m;
-        const bool any_solid = __any_sync(FULL, t.ns > 0);
-        if (any_solid) {
+        {
             const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
             const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
             m.Bs = q0.B + q1.B;
@@ -1088,13 +1100,9 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
             m.Qxz = b0x * d0z + b1x * d1z;
             m.Qyz = b0y * d0z + b1y * d1z;
             m.S = q0.B * d0s + q1.B * d1s;
-            CollidePairs<SS, 1, true, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
-                                                pout + pl.cell, valid);
-        } else {
-            m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
-            CollidePairs<SS, 1, false, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
-                                                 pout + pl.cell, valid);
         }
+        CollidePairs<SS, 1, true, TRT>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB, force_wa, m,
+                                            pout + pl.cell, valid);
         {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
             float out0 = TW(0) * base + keep0 * g[0];
             if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
