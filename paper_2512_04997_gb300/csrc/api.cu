@@ -21,7 +21,7 @@ cudaError_t launch_rebase(const LbmArgs&, int, const float (*)[2][3], cudaStream
 cudaError_t launch_bin(const LbmArgs&, int, int*, int*, cudaStream_t);
 cudaError_t launch_psm(const LbmArgs&, int, cudaStream_t);
 cudaError_t launch_voxelize(const LbmArgs&, float*, int*, int*, cudaStream_t);
-cudaError_t launch_rebuild(const DemArgs&, int, int, uint32_t*, cudaStream_t, int*);
+cudaError_t launch_rebuild(const DemArgs&, int, int, int, uint32_t*, cudaStream_t, int*);
 cudaError_t launch_predict_first(const DemArgs&, cudaStream_t);
 cudaError_t launch_substep(const DemArgs&, int, int, int, int, int, cudaStream_t);
 cudaError_t launch_final(const DemArgs&, int, int, cudaStream_t);
@@ -44,6 +44,12 @@ struct ledds_sim_s {
     ledds_dims d;
     ledds_params p;
     cudaStream_t stream = nullptr, cap_stream = nullptr;
+    // The neighbour rebuild for the next step runs on a side stream beside the fluid step
+    // (it needs only the positions after the last substep); lists_ready: the current step's
+    // candidate lists were built that way, at the current positions.
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool lists_ready = false;
     char* ws = nullptr;
     size_t ws_bytes = 0;
     // lattice
@@ -422,10 +428,13 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
     const int nsub = s->p.n_sub;
     const int last = (nsub - 1) & 1;
     DemArgs A = dem_args(s);
+    // With a lattice (and not profiling), the rebuild for the next step runs beside the
+    // binning and the PSM kernel; this step's lists then come from the previous step.
+    const bool overlap = s->lattice && n > 0 && !ev;
     if (ev) CK(cudaEventRecord(ev[0], st));
-    if (n > 0) {
+    if (n > 0 && !overlap) {
         // particle/grid stage: neighbour rebuild (keys, counting sort, candidates)
-        CK(launch_rebuild(A, p, p ^ 1, s->scan_partial, st, launches));
+        CK(launch_rebuild(A, p, p ^ 1, 0, s->scan_partial, st, launches));
     }
     if (ev) CK(cudaEventRecord(ev[1], st));
     if (n > 0) {
@@ -440,6 +449,14 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
         *launches += contact_launches;
     }
     if (ev) CK(cudaEventRecord(ev[2], st));
+    if (overlap) {
+        // lists of the next step (parity p ^ 1 reads buffer p): the histories are final
+        // after this step's last contact sums, the positions after its last predictor
+        CK(cudaEventRecord(s->fork_ev, st));
+        CK(cudaStreamWaitEvent(s->side, s->fork_ev, 0));
+        CK(launch_rebuild(A, p ^ 1, p, last, s->scan_partial, s->side, launches));
+        CK(cudaEventRecord(s->join_ev, s->side));
+    }
     if (s->lattice) {
         LbmArgs la = lbm_args(s, p, p ^ 1, last);
         CK(cudaMemsetAsync(s->tile_count, 0, sizeof(int) * (size_t)s->ntiles, st));
@@ -455,6 +472,7 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
         CK(cudaEventRecord(ev[3], st));
     }
     if (ev) CK(cudaEventRecord(ev[4], st));
+    if (overlap) CK(cudaStreamWaitEvent(st, s->join_ev, 0));
     if (n > 0) {
         CK(launch_final(A, last, s->lattice ? 1 : 0, st));
         *launches += 1;
@@ -551,7 +569,14 @@ int ledds_create(const ledds_dims* d, const ledds_params* p, void* d_workspace, 
     memset(s->uw, 0, sizeof(s->uw));
     domain(d, s->lo, s->hi, s->L);
     layout(s, d, p, s->ws);
-    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+        if (s->side) cudaStreamDestroy(s->side);
+        if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+        if (s->join_ev) cudaEventDestroy(s->join_ev);
         delete s;
         return LEDDS_ERR_CUDA;
     }
@@ -563,6 +588,9 @@ int ledds_create(const ledds_dims* d, const ledds_params* p, void* d_workspace, 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
         cudaStreamDestroy(s->cap_stream);
+        cudaStreamDestroy(s->side);
+        cudaEventDestroy(s->fork_ev);
+        cudaEventDestroy(s->join_ev);
         delete s;
         return LEDDS_ERR_CUDA;
     }
@@ -577,6 +605,9 @@ int ledds_destroy(ledds_sim_t s) {
     if (s->ev_made)
         for (int q = 0; q <= NSTAGE; ++q) cudaEventDestroy(s->ev[q]);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    if (s->side) cudaStreamDestroy(s->side);
+    if (s->fork_ev) cudaEventDestroy(s->fork_ev);
+    if (s->join_ev) cudaEventDestroy(s->join_ev);
     delete s;
     return LEDDS_OK;
 }
@@ -699,6 +730,7 @@ int ledds_set_particles(ledds_sim_t s, int n, const ledds_particle* h) {
     }
     s->P.n = n;
     s->max_bound = bmax;
+    s->lists_ready = false;
     s->any_ellipsoid = 0;
     for (int k = 0; k < n; ++k) s->any_ellipsoid |= shape[k] == LEDDS_ELLIPSOID;
     drop_graphs(s);
@@ -734,6 +766,7 @@ int ledds_write_kinematics(ledds_sim_t s, const double* state, int on_device) {
     if (!s || !state) return LEDDS_ERR_INVALID_ARG;
     if (s->P.n == 0) return LEDDS_OK;
     int rc = upload_rows(s, s->P.st[0], state, 18, s->P.n, on_device);
+    s->lists_ready = false;  // new positions: the next step builds its lists first
     if (rc == LEDDS_OK && !on_device && cudaStreamSynchronize(s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
     return rc;
 }
@@ -762,8 +795,17 @@ int ledds_step(ledds_sim_t s, int n_steps) {
             s->parity ^= 1;
             s->steps++;
         }
+        s->lists_ready = false;  // profiled steps rebuild at their start, not for the next one
         return LEDDS_OK;
     }
+    if (n_steps > 0 && s->lattice && s->P.n > 0 && !s->lists_ready) {
+        // the first step after new positions: its lists, as a step of the serial order builds them
+        DemArgs A = dem_args(s);
+        int launches = 0;
+        if (launch_rebuild(A, s->parity, s->parity ^ 1, 0, s->scan_partial, s->stream, &launches) != cudaSuccess)
+            return LEDDS_ERR_CUDA;
+    }
+    s->lists_ready = true;  // every graph step ends with the rebuild for the next
     int left = n_steps;
     while (left > 0) {
         int p = s->parity;
@@ -974,6 +1016,7 @@ int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     memcpy(s->uw, hd.uw, sizeof(hd.uw));
     s->max_bound = hd.max_bound;
     s->any_ellipsoid = hd.any_ellipsoid;
+    s->lists_ready = false;
     drop_graphs(s);
     return LEDDS_OK;
 }

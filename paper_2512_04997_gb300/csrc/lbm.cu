@@ -640,19 +640,16 @@ __device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float v
 constexpr int PSM_THREADS = TILE_X * TILE_Y;
 
 // Per storage format: resident CTAs per SM the PSM kernel is compiled for (its register
-// budget), depth of the asynchronous pull pipeline (planes in flight + 1) and the form of
-// the wall path (wall_in_slots: the pulled values stay in registers). Chosen by timing
-// the variants on GB300: FP32 runs best with more registers and a deeper pipeline, the
-// 16-bit formats with more resident CTAs.
+// budget) and depth of the asynchronous pull pipeline (planes in flight + 1). Chosen by
+// timing the variants on GB300: FP32 runs best with more registers and a deeper
+// pipeline, the 16-bit formats with more resident CTAs.
 template <int STORE>
 struct PsmCfg {
     static constexpr int minb = 3, stages = 3;
-    static constexpr bool wall_in_slots = false;
 };
 template <>
 struct PsmCfg<LEDDS_STORE_F32> {
     static constexpr int minb = 2, stages = 4;
-    static constexpr bool wall_in_slots = true;
 };
 
 __device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src, bool pred) {
@@ -677,33 +674,49 @@ __device__ __forceinline__ long long pull_addr(const LbmArgs& a, const Nbr& nb, 
     return wall ? (long long)OPP(I) * a.N + nb.cell : (long long)I * a.N + src;
 }
 
-// Per-plane pull plan of one node. Away from walls every source is node - off_i plus a
-// periodic-wrap correction on the axes where the node sits on the first or last layer;
-// next to a wall the general path (halfway bounce-back) is taken.
+// Per-plane pull plan of one node: the source of direction I is node - off_I, plus a
+// periodic-wrap correction on an axis where the node sits on the first or last layer; a
+// link that leaves the lattice through a wall (bit of bw: x low/high 1/2, y 4/8, z 16/32)
+// pulls the node's own opposite population instead (halfway bounce-back).
 struct Plan {
     int cell;
-    bool wall;                 // some link of this node crosses a wall
+    unsigned bw;                       // wall faces next to this node
     int wxm, wxp, wym, wyp, wzm, wzp;  // wrap corrections for c = +1 (m) and c = -1 (p)
 };
 
 __device__ __forceinline__ void make_plan(const LbmArgs& a, int x, int y, int z, Plan& p) {
     const int nxy = a.nx * a.ny;
     p.cell = x + a.nx * y + nxy * z;
-    bool w = false;
+    unsigned b = 0;
     p.wxm = p.wxp = p.wym = p.wyp = p.wzm = p.wzp = 0;
-    if (x == 0) { if (a.per[0]) p.wxm = a.nx; else w = true; }
-    if (x == a.nx - 1) { if (a.per[0]) p.wxp = -a.nx; else w = true; }
-    if (y == 0) { if (a.per[1]) p.wym = nxy; else w = true; }
-    if (y == a.ny - 1) { if (a.per[1]) p.wyp = -nxy; else w = true; }
-    if (z == 0) { if (a.per[2]) p.wzm = (int)a.N; else w = true; }
-    if (z == a.nz - 1) { if (a.per[2]) p.wzp = -(int)a.N; else w = true; }
-    p.wall = w;
+    if (x == 0) { if (a.per[0]) p.wxm = a.nx; else b |= 1u; }
+    if (x == a.nx - 1) { if (a.per[0]) p.wxp = -a.nx; else b |= 2u; }
+    if (y == 0) { if (a.per[1]) p.wym = nxy; else b |= 4u; }
+    if (y == a.ny - 1) { if (a.per[1]) p.wyp = -nxy; else b |= 8u; }
+    if (z == 0) { if (a.per[2]) p.wzm = (int)a.N; else b |= 16u; }
+    if (z == a.nz - 1) { if (a.per[2]) p.wzp = -(int)a.N; else b |= 32u; }
+    p.bw = b;
 }
 
-// element index of the population pulled in direction I (no wall on the link)
+// Walls crossed by the link of direction I (the axis flags of wall_term).
 template <int I>
+__device__ __forceinline__ void link_walls(const Plan& p, bool& wx, bool& wy, bool& wz) {
+    constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+    wx = (cx == 1 && (p.bw & 1u)) || (cx == -1 && (p.bw & 2u));
+    wy = (cy == 1 && (p.bw & 4u)) || (cy == -1 && (p.bw & 8u));
+    wz = (cz == 1 && (p.bw & 16u)) || (cz == -1 && (p.bw & 32u));
+}
+
+// element index of the population pulled in direction I; WALLS: some link of the warp
+// may cross a wall (uniform choice of the caller)
+template <int I, bool WALLS>
 __device__ __forceinline__ int fast_elem(const LbmArgs& a, const Plan& p) {
     constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+    if constexpr (WALLS) {
+        bool wx, wy, wz;
+        link_walls<I>(p, wx, wy, wz);
+        if (wx || wy || wz) return a.pN[OPP(I)] + p.cell;
+    }
     int src = p.cell - a.off[I];
     if (cx == 1) src += p.wxm;
     if (cx == -1) src += p.wxp;
@@ -714,127 +727,33 @@ __device__ __forceinline__ int fast_elem(const LbmArgs& a, const Plan& p) {
     return a.pN[I] + src;
 }
 
-// Runtime-indexed copies of the velocity set for the out-of-line wall path.
-__constant__ int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-__constant__ int kCY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-__constant__ int kCZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-__constant__ float kTW[19] = {1.f / 3, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18, 1.f / 18,
-                              1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36,
-                              1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36, 1.f / 36};
-
-// General pull of direction i at node (x,y,z): element index, plus the moving-wall term
-// when the link crosses a wall (halfway bounce-back reads the node's own opposite value).
-__device__ __forceinline__ int general_elem(const LbmArgs& a, int i, int x, int y, int z, float* wterm) {
-    const int cx = kCX[i], cy = kCY[i], cz = kCZ[i];
-    int sx = x - cx, sy = y - cy, sz = z - cz;
-    bool wx = false, wy = false, wz = false;
-    if (sx < 0 || sx >= a.nx) { if (a.per[0]) sx = sx < 0 ? sx + a.nx : sx - a.nx; else wx = true; }
-    if (sy < 0 || sy >= a.ny) { if (a.per[1]) sy = sy < 0 ? sy + a.ny : sy - a.ny; else wy = true; }
-    if (sz < 0 || sz >= a.nz) { if (a.per[2]) sz = sz < 0 ? sz + a.nz : sz - a.nz; else wz = true; }
-    const int cell = x + a.nx * (y + a.ny * z);
-    *wterm = 0.f;
-    if (wx || wy || wz) {
-        const int ax = wz ? 2 : (wy ? 1 : 0);
-        const int cc = ax == 2 ? cz : (ax == 1 ? cy : cx);
-        const int side = cc == 1 ? 0 : 1;
-        float u0, u1, u2;
-        // constant-index selection (no dynamic indexing of the parameter block)
-        if (ax == 2) { u0 = side ? a.uw[2][1][0] : a.uw[2][0][0]; u1 = side ? a.uw[2][1][1] : a.uw[2][0][1]; u2 = side ? a.uw[2][1][2] : a.uw[2][0][2]; }
-        else if (ax == 1) { u0 = side ? a.uw[1][1][0] : a.uw[1][0][0]; u1 = side ? a.uw[1][1][1] : a.uw[1][0][1]; u2 = side ? a.uw[1][1][2] : a.uw[1][0][2]; }
-        else { u0 = side ? a.uw[0][1][0] : a.uw[0][0][0]; u1 = side ? a.uw[0][1][1] : a.uw[0][0][1]; u2 = side ? a.uw[0][1][2] : a.uw[0][0][2]; }
-        *wterm = 6.0f * kTW[i] * ((float)cx * u0 + (float)cy * u1 + (float)cz * u2);
-        const int o = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
-        return a.pN[o] + cell;
-    }
-    return a.pN[i] + sx + a.nx * (sy + a.ny * sz);
-}
-
-template <class SS>
-__device__ __noinline__ void issue_general(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
-                                           uint32_t* slot) {
-    for (int i = 0; i < 19; ++i) {
-        float wt;
-        int elem = general_elem(a, i, x, y, z, &wt);
-        uintptr_t q = reinterpret_cast<uintptr_t>(pin + elem);
-        if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
-        cp_async4(slot + i * PSM_THREADS, reinterpret_cast<const void*>(q), true);
-    }
-}
-
-// Wall-adjacent node, reading into g directly (out of line; g then lives in local memory,
-// which costs less than the spills of keeping it in registers under an 80-register budget).
-template <class SS>
-__device__ __noinline__ void read_general(const LbmArgs& a, int x, int y, int z, const uint32_t* slot, float* g) {
-    for (int i = 0; i < 19; ++i) {
-        float wt;
-        int elem = general_elem(a, i, x, y, z, &wt);
-        const uint32_t w = slot[i * PSM_THREADS];
-        float v;
-        if (sizeof(typename SS::T) == 4) {
-            v = __uint_as_float(w);
-        } else {
-            v = SS::from_bits((elem & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), a.inv_scale);
-        }
-        g[i] = v + wt;
-    }
-}
-
-// Wall-adjacent node: decode its 19 pulled words and add the moving-wall terms, writing
-// the results back into the thread's own stage slots as FP32 bits. Out of line (rare
-// nodes), and it takes no pointer to the node's value array, which therefore stays in
-// registers on every path.
-template <class SS>
-__device__ __noinline__ void fix_general_slots(const LbmArgs& a, int x, int y, int z, uint32_t* slot) {
-    for (int i = 0; i < 19; ++i) {
-        float wt;
-        const int elem = general_elem(a, i, x, y, z, &wt);
-        const uint32_t w = slot[i * PSM_THREADS];
-        float v;
-        if (sizeof(typename SS::T) == 4) {
-            v = __uint_as_float(w);
-        } else {
-            v = SS::from_bits((elem & 1) ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), a.inv_scale);
-        }
-        slot[i * PSM_THREADS] = __float_as_uint(v + wt);
-    }
-}
-
-template <int I>
-struct ReadFloats {
-    static __device__ __forceinline__ void run(const uint32_t* slot, float* g) {
-        g[I] = __uint_as_float(slot[I * PSM_THREADS]);
-        ReadFloats<I + 1>::run(slot, g);
-    }
-};
-template <>
-struct ReadFloats<19> {
-    static __device__ __forceinline__ void run(const uint32_t*, float*) {}
-};
-
-template <class SS, int I>
+template <class SS, int I, bool WALLS>
 struct IssueAll {
     static __device__ __forceinline__ void run(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
                                                uint32_t* slot) {
-        uintptr_t q = reinterpret_cast<uintptr_t>(pin + fast_elem<I>(a, p));
+        uintptr_t q = reinterpret_cast<uintptr_t>(pin + fast_elem<I, WALLS>(a, p));
         if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
         cp_async4(slot + I * PSM_THREADS, reinterpret_cast<const void*>(q), true);
-        IssueAll<SS, I + 1>::run(a, pin, p, slot);
+        IssueAll<SS, I + 1, WALLS>::run(a, pin, p, slot);
     }
 };
-template <class SS>
-struct IssueAll<SS, 19> {
+template <class SS, bool WALLS>
+struct IssueAll<SS, 19, WALLS> {
     static __device__ __forceinline__ void run(const LbmArgs&, const typename SS::T*, const Plan&, uint32_t*) {}
 };
 
-// Issue the 19 pulls of node (x,y,z) into its shared-memory slots (nothing if !pred).
+// Issue the 19 pulls of node (x,y,z) into its shared-memory slots (nothing if !pred). Every
+// lane of the warp calls it; warps without a wall link take the plain addressing.
 template <class SS>
 __device__ __forceinline__ void issue_node(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
                                            bool pred, uint32_t* slot) {
-    if (!pred) return;
     Plan p;
     make_plan(a, x, y, z, p);
-    if (!p.wall) IssueAll<SS, 0>::run(a, pin, p, slot);
-    else issue_general<SS>(a, pin, x, y, z, slot);
+    if (__any_sync(FULL, pred && p.bw != 0u)) {
+        if (pred) IssueAll<SS, 0, true>::run(a, pin, p, slot);
+    } else if (pred) {
+        IssueAll<SS, 0, false>::run(a, pin, p, slot);
+    }
 }
 
 template <class SS>
@@ -843,20 +762,29 @@ __device__ __forceinline__ float decode(uint32_t w, int odd, float inv) {
     return SS::from_bits(odd ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), inv);
 }
 
-template <class SS, int I>
+template <class SS, int I, bool WALLS>
 struct ReadAll {
     static __device__ __forceinline__ void run(const LbmArgs& a, const Plan& p, const uint32_t* slot, float* g) {
         const uint32_t w = slot[I * PSM_THREADS];
+        bool wx = false, wy = false, wz = false;
+        if constexpr (WALLS) link_walls<I>(p, wx, wy, wz);
+        const bool wl = wx || wy || wz;
         // 16-bit storage: which half of the copied word holds the value. With nx even every
-        // offset and wrap correction except c_x is even, so the parity is that of x - c_x.
+        // offset and wrap correction except c_x is even, so the parity is that of x - c_x
+        // (of x itself for a bounced link).
         int odd = 0;
-        if (sizeof(typename SS::T) == 2) odd = a.nx_even ? ((p.cell ^ CX(I)) & 1) : (fast_elem<I>(a, p) & 1);
-        g[I] = decode<SS>(w, odd, a.inv_scale);
-        ReadAll<SS, I + 1>::run(a, p, slot, g);
+        if (sizeof(typename SS::T) == 2)
+            odd = a.nx_even ? ((p.cell ^ (wl ? 0 : CX(I))) & 1) : (fast_elem<I, WALLS>(a, p) & 1);
+        float v = decode<SS>(w, odd, a.inv_scale);
+        if constexpr (WALLS) {
+            if (wl) v += wall_term<I>(a.uw, wx, wy, wz);  // moving-wall bounce-back
+        }
+        g[I] = v;
+        ReadAll<SS, I + 1, WALLS>::run(a, p, slot, g);
     }
 };
-template <class SS>
-struct ReadAll<SS, 19> {
+template <class SS, bool WALLS>
+struct ReadAll<SS, 19, WALLS> {
     static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const uint32_t*, float*) {}
 };
 
@@ -1009,19 +937,14 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
 
         float g[19];
         Plan pl;
-        pl.cell = 0;
-        if (valid) {
-            make_plan(a, x, y, z, pl);
-            uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
-            if (!pl.wall) {
-                ReadAll<SS, 0>::run(a, pl, slot, g);
-            } else if constexpr (PsmCfg<STORE>::wall_in_slots) {
-                fix_general_slots<SS>(a, x, y, z, slot);
-                ReadFloats<0>::run(slot, g);
-            } else {
-                read_general<SS>(a, x, y, z, slot, g);
-            }
-        } else {
+        make_plan(a, valid ? x : 0, y, z, pl);
+        const uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
+        if (__any_sync(FULL, valid && pl.bw != 0u)) {
+            if (valid) ReadAll<SS, 0, true>::run(a, pl, slot, g);
+        } else if (valid) {
+            ReadAll<SS, 0, false>::run(a, pl, slot, g);
+        }
+        if (!valid) {
 #pragma unroll
             for (int i = 0; i < 19; ++i) g[i] = 0.f;
         }
