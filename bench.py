@@ -329,6 +329,44 @@ def fluidised_sweep(device, stream, phis=(0.0, 0.1, 0.2, 0.3, 0.41), steps=10, w
             "mlups_ratio_phi0_to_max": rows[0]["value"] / rows[-1]["value"] if rows else None}
 
 
+def rheology_measure(device, stream, phis=(0.0, 0.1, 0.2, 0.3), steps=20000, every=250):
+    """Effective viscosity of the sheared suspension at reduced size (96^3, spheres of
+    diameter 10, walls at -/+0.05): the x-y averaged u_x profile sampled every `every` steps
+    over the second half of the run, the wall shear rate from the parabola through the wall
+    value and the first two nodes, eta/eta0 = wall shear rate / nominal shear rate 2U/H,
+    beside the Krieger-Dougherty law (1 - phi/0.64)^(-2.5 * 0.64)."""
+    import torch
+    from paper_2512_04997_gb300 import ledds, workloads as W
+    rows = []
+    t0 = time.perf_counter()
+    for phi in phis:
+        w = W.rheology_suspension(phi)
+        n, U = w.nz, w.u_wall[2, 1, 0]
+        s = ledds.from_workload(w, device=device)
+        s.step(steps // 2)
+        prof = torch.zeros(n, dtype=torch.float64, device=device)
+        samples = 0
+        for _ in range(steps // 2 // every):
+            s.step(every)
+            _, u = s.fields()
+            prof += u[0].view(n, -1).double().mean(1)
+            samples += 1
+        prof = (prof / samples).cpu().numpy()
+        st = s.status()
+        s.close()
+        phi_real = w.n * 4.0 / 3.0 * math.pi * 125.0 / n ** 3
+        eta = W.wall_shear_rate(prof, U) / (2.0 * U / n)
+        kd = (1.0 - phi_real / 0.64) ** (-2.5 * 0.64)
+        rows.append({"phi": round(phi_real, 3), "spheres": w.n, "eta_rel": eta, "krieger_dougherty": kd,
+                     "rel_diff": eta / kd - 1.0,
+                     "status": {k: st[k] for k in ("skin_violation", "nan_detected", "cand_overflow")}})
+        torch.cuda.empty_cache()
+    return {"workload": "sheared suspension 96^3, spheres of diameter 10, walls at -/+0.05 (nominal shear rate "
+                        "1.04e-3), tau 0.8, n_sub 10, friction 0.45, restitution 0.95, "
+                        f"{steps} steps, profiles averaged over the second half",
+            "seconds": time.perf_counter() - t0, "points": rows}
+
+
 def oracle_sample(steps):
     """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
     slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps."""
@@ -491,6 +529,7 @@ def main():
         variants["granular_dem"] = granular_measure(f"cuda:{local}", stream)
         variants["ellipsoid_shear"] = ellipsoid_measure(args, f"cuda:{local}", stream)
         variants["fluidised_bed"] = fluidised_sweep(f"cuda:{local}", stream)
+        variants["rheology"] = rheology_measure(f"cuda:{local}", stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

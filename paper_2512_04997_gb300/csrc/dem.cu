@@ -1235,99 +1235,6 @@ __device__ void correct(const DemArgs& A, int k, const double F[3], const double
     }
 }
 
-// ------------------------------------------------------------------------------------
-// The integrator on four lanes per particle (lanes 4k .. 4k+3 of a warp): role c < 3 holds
-// the c-th component of the vectors and row c of the triad, role 3 only takes part in the
-// shuffles. Each value is computed with the same expressions as predict/correct above;
-// the quad exchanges operands by shuffles, which shortens the dependent FP64 chain of each
-// particle about threefold and puts four times as many warps on the GPU. Every lane of the
-// warp executes the shuffles; lanes without a particle (live false) load and store nothing.
-// ------------------------------------------------------------------------------------
-__device__ __forceinline__ double qsh(double v, int role) {
-    return __shfl_sync(0xffffffffu, v, ((int)threadIdx.x & 31 & ~3) + role);
-}
-
-// predictor (Eq. advance-r, triad update, Gram-Schmidt) of one particle
-__device__ void predict_quad(const DemArgs& A, int k, int c, bool live, double& rc, double vc, double accc,
-                             double wc, double d[3]) {
-    const double dt = A.dt, h2 = dt * dt / 2.0;
-    if (c < 3) {
-        rc = __fma_rn(h2, accc, __fma_rn(dt, vc, rc));
-        if (A.per[c]) {
-            const double q = rc - A.lo[c];
-            if (q < 0.0 || q >= 0.999999 * A.L[c]) rc = rc - A.L[c] * floor(q / A.L[c]);
-        }
-    }
-    const double w[3] = {qsh(wc, 0), qsh(wc, 1), qsh(wc, 2)};
-    if (c < 3) {
-        double wxd[3], ds[3], mid[3], wxm[3];
-        cross3_fma(w, d, wxd);
-        for (int a = 0; a < 3; ++a) ds[a] = __fma_rn(dt, wxd[a], d[a]);
-        for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (d[a] + ds[a]);
-        cross3_fma(w, mid, wxm);
-        for (int a = 0; a < 3; ++a) d[a] = __fma_rn(dt, wxm[a], d[a]);
-    }
-    if (c == 0) {
-        const double i1 = rsqrt(dot3_fma(d, d));
-        for (int a = 0; a < 3; ++a) d[a] *= i1;
-    }
-    const double d1[3] = {qsh(d[0], 0), qsh(d[1], 0), qsh(d[2], 0)};
-    if (c == 1) {
-        const double pr = dot3_fma(d, d1);
-        for (int a = 0; a < 3; ++a) d[a] = __fma_rn(-pr, d1[a], d[a]);
-        const double i2 = rsqrt(dot3_fma(d, d));
-        for (int a = 0; a < 3; ++a) d[a] *= i2;
-    }
-    const double d2[3] = {qsh(d[0], 1), qsh(d[1], 1), qsh(d[2], 1)};
-    if (c == 2) cross3_fma(d1, d2, d);
-    double e = 0.0;
-    if (c < 3 && live) e = min_image(A, c, rc - A.P.pos_build[(long long)c * A.P.cap + k]);
-    const double e0 = qsh(e, 0), e1 = qsh(e, 1), e2 = qsh(e, 2);
-    const double disp2 = __fma_rn(e2, e2, __fma_rn(e1, e1, e0 * e0));
-    if (live && c == 0 && disp2 > 0.25 * A.skin * A.skin) atomicAdd(&A.status->skin_violation, 1);
-    if (live && c < 3 && !isfinite(rc)) atomicAdd(&A.status->nan_detected, 1);
-}
-
-// corrector (a', body-frame Euler equations, v and w updates) of one particle; acc and alpha
-// (role c's component) are read and replaced
-__device__ void correct_quad(const DemArgs& A, int k, int c, bool live, double Fc, double Mc, const double d[3],
-                             double& vc, double& wc) {
-    const double hdt = A.dt / 2.0;
-    const double m = live ? A.P.mass[k] : 1.0, gf = live ? A.P.gfac[k] : 0.0;
-    const double im = 1.0 / m;
-    const double an = c < 3 ? __fma_rn(Fc, im, A.gravity[c] * gf) : 0.0;
-    const double w[3] = {qsh(wc, 0), qsh(wc, 1), qsh(wc, 2)};
-    const double M[3] = {qsh(Mc, 0), qsh(Mc, 1), qsh(Mc, 2)};
-    double I[3] = {1.0, 1.0, 1.0};
-    if (live)
-        for (int q = 0; q < 3; ++q) I[q] = A.P.inertia[(long long)q * A.P.cap + k];
-    const double D = 1.0 / (I[0] * I[1] * I[2]);
-    const double iI[3] = {I[1] * I[2] * D, I[0] * I[2] * D, I[0] * I[1] * D};
-    // body components of w and M: role c owns row c of the triad
-    const double wb_c = c < 3 ? dot3_fma(d, w) : 0.0;
-    const double Mb_c = c < 3 ? dot3_fma(d, M) : 0.0;
-    const double wb[3] = {qsh(wb_c, 0), qsh(wb_c, 1), qsh(wb_c, 2)};
-    const double Mb[3] = {qsh(Mb_c, 0), qsh(Mb_c, 1), qsh(Mb_c, 2)};
-    double Iw[3], gyr[3], ab[3];
-    for (int q = 0; q < 3; ++q) Iw[q] = I[q] * wb[q];
-    cross3_fma(wb, Iw, gyr);
-    for (int q = 0; q < 3; ++q) ab[q] = (Mb[q] - gyr[q]) * iI[q];
-    // world components of alpha: column c of the triad
-    double col[3];
-    for (int q = 0; q < 3; ++q) {
-        const double x = qsh(d[0], q), y = qsh(d[1], q), z = qsh(d[2], q);
-        col[q] = c == 0 ? x : (c == 1 ? y : z);
-    }
-    const double al = __fma_rn(ab[0], col[0], __fma_rn(ab[1], col[1], ab[2] * col[2]));
-    if (c < 3 && live) {
-        const long long o = (long long)c * A.P.cap + k;
-        vc = __fma_rn(hdt, A.P.acc[o] + an, vc);
-        wc = __fma_rn(hdt, A.P.alpha[o] + al, wc);
-        A.P.acc[o] = an;
-        A.P.alpha[o] = al;
-    }
-}
-
 __device__ __forceinline__ void load_state(const DemArgs& A, const double* st, int k, double r[3],
                                            double v[3], double w[3], double d[9]) {
     ld3(A, st, SP, k, r);
@@ -1345,85 +1252,57 @@ __device__ __forceinline__ void store_state(const DemArgs& A, double* st, int k,
     for (int m = 0; m < 9; ++m) st[(long long)(ST + m) * A.P.cap + k] = d[m];
 }
 
-// Quad-lane forms of the integrator kernels (see predict_quad / correct_quad).
-__device__ __forceinline__ void quad_of(int n, int& k, int& c, bool& live) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    k = (int)(t >> 2);
-    c = (int)(t & 3);
-    live = k < n;
-    if (!live) k = 0;
-}
-__device__ __forceinline__ double qload(const DemArgs& A, const double* st, int comp, int k, int c, bool live) {
-    return (live && c < 3) ? st[(long long)(comp + c) * A.P.cap + k] : 0.0;
-}
-__device__ __forceinline__ void qload_row(const DemArgs& A, const double* st, int k, int c, bool live, double d[3]) {
-    for (int a = 0; a < 3; ++a) d[a] = (live && c < 3) ? st[(long long)(ST + 3 * c + a) * A.P.cap + k] : 0.0;
-}
-__device__ __forceinline__ void qstore(const DemArgs& A, double* st, int k, int c, bool live, double r, double v,
-                                       double w, const double d[3]) {
-    if (!live || c >= 3) return;
-    st[(long long)(SP + c) * A.P.cap + k] = r;
-    st[(long long)(SV + c) * A.P.cap + k] = v;
-    st[(long long)(SW + c) * A.P.cap + k] = w;
-    for (int a = 0; a < 3; ++a) st[(long long)(ST + 3 * c + a) * A.P.cap + k] = d[a];
+// First substep predictor, in place on buffer 0.
+__global__ void k_predict_first(DemArgs A) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], acc[3];
+    load_state(A, A.P.st[0], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+    predict(A, k, r, v, acc, w, d);
+    for (int a = 0; a < 3; ++a) A.P.st[0][(long long)(SP + a) * A.P.cap + k] = r[a];
+    for (int m = 0; m < 9; ++m) A.P.st[0][(long long)(ST + m) * A.P.cap + k] = d[m];
 }
 
-__global__ void k_predict_first_q(DemArgs A) {
-    int k, c;
-    bool live;
-    quad_of(A.P.n, k, c, live);
-    const double* st = A.P.st[0];
-    double r = qload(A, st, SP, k, c, live), v = qload(A, st, SV, k, c, live), w = qload(A, st, SW, k, c, live);
-    double d[3];
-    qload_row(A, st, k, c, live, d);
-    const double acc = (live && c < 3) ? A.P.acc[(long long)c * A.P.cap + k] : 0.0;
-    predict_quad(A, k, c, live, r, v, acc, w, d);
-    if (live && c < 3) {
-        A.P.st[0][(long long)(SP + c) * A.P.cap + k] = r;
-        for (int a = 0; a < 3; ++a) A.P.st[0][(long long)(ST + 3 * c + a) * A.P.cap + k] = d[a];
+// End of a substep for one particle (thread per particle): the corrector with the held
+// hydrodynamic force, then the predictor of the next substep, from buffer `in` to `out`.
+__global__ void k_integrate(DemArgs A, int in, int out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], Ft[3], Mt[3], acc[3];
+    load_state(A, A.P.st[in], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) {
+        long long o = (long long)a * A.P.cap + k;
+        Ft[a] = A.P.Fc[o] + A.P.Fhp[o];
+        Mt[a] = A.P.Mc[o] + A.P.Mhp[o];
     }
+    correct(A, k, Ft, Mt, d, v, w);
+    for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
+    predict(A, k, r, v, acc, w, d);
+    store_state(A, A.P.st[out], k, r, v, w, d);
 }
 
-__global__ void k_integrate_q(DemArgs A, int in, int out) {
-    int k, c;
-    bool live;
-    quad_of(A.P.n, k, c, live);
-    const double* st = A.P.st[in];
-    double r = qload(A, st, SP, k, c, live), v = qload(A, st, SV, k, c, live), w = qload(A, st, SW, k, c, live);
-    double d[3];
-    qload_row(A, st, k, c, live, d);
-    double F = 0.0, M = 0.0;
-    if (live && c < 3) {
-        const long long o = (long long)c * A.P.cap + k;
-        F = A.P.Fc[o] + A.P.Fhp[o];
-        M = A.P.Mc[o] + A.P.Mhp[o];
-    }
-    correct_quad(A, k, c, live, F, M, d, v, w);
-    const double acc = (live && c < 3) ? A.P.acc[(long long)c * A.P.cap + k] : 0.0;
-    predict_quad(A, k, c, live, r, v, acc, w, d);
-    qstore(A, A.P.st[out], k, c, live, r, v, w, d);
-}
-
-__global__ void k_final_q(DemArgs A, int in, int use_hydro) {
-    int k, c;
-    bool live;
-    quad_of(A.P.n, k, c, live);
-    const double* st = A.P.st[in];
-    double r = qload(A, st, SP, k, c, live), v = qload(A, st, SV, k, c, live), w = qload(A, st, SW, k, c, live);
-    double d[3];
-    qload_row(A, st, k, c, live, d);
-    double F = 0.0, M = 0.0;
-    if (live && c < 3) {
-        const long long o = (long long)c * A.P.cap + k;
-        const double fh = use_hydro ? A.P.Fh[o] : 0.0, mh = use_hydro ? A.P.Mh[o] : 0.0;
-        F = A.P.Fc[o] + fh;
-        M = A.P.Mc[o] + mh;
+// Velocity update of the last substep (flowchart: after the fluid forces are reduced):
+// corrector with the fresh hydrodynamic force (or none for DEM-only), result in buffer 0;
+// the hydrodynamic force is held for the next step's substeps.
+__global__ void k_final(DemArgs A, int in, int use_hydro) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= A.P.n) return;
+    double r[3], v[3], w[3], d[9], F[3], M[3];
+    load_state(A, A.P.st[in], k, r, v, w, d);
+    for (int a = 0; a < 3; ++a) {
+        long long o = (long long)a * A.P.cap + k;
+        double fh = use_hydro ? A.P.Fh[o] : 0.0, mh = use_hydro ? A.P.Mh[o] : 0.0;
+        F[a] = A.P.Fc[o] + fh;
+        M[a] = A.P.Mc[o] + mh;
         A.P.Fhp[o] = fh;
         A.P.Mhp[o] = mh;
     }
-    correct_quad(A, k, c, live, F, M, d, v, w);
-    if (live && c < 3 && !(isfinite(v) && isfinite(w))) atomicAdd(&A.status->nan_detected, 1);
-    qstore(A, A.P.st[0], k, c, live, r, v, w, d);
+    correct(A, k, F, M, d, v, w);
+    bool bad = false;
+    for (int a = 0; a < 3; ++a) bad |= !isfinite(v[a]) || !isfinite(w[a]);
+    if (bad) atomicAdd(&A.status->nan_detected, 1);
+    store_state(A, A.P.st[0], k, r, v, w, d);
 }
 
 
@@ -1648,7 +1527,7 @@ cudaError_t launch_rebuild(const DemArgs& A, int ob, int nb, int pst, uint32_t* 
 
 cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
-    k_predict_first_q<<<nblk(4 * A.P.n, 128), 128, 0, s>>>(A);
+    k_predict_first<<<nblk(A.P.n, 128), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -1664,13 +1543,13 @@ cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_ste
     } else {
         k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
     }
-    if (do_step) k_integrate_q<<<nblk(4 * A.P.n, 128), 128, 0, s>>>(A, in, out);
+    if (do_step) k_integrate<<<nblk(A.P.n, 32), 32, 0, s>>>(A, in, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_final(const DemArgs& A, int in, int use_hydro, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
-    k_final_q<<<nblk(4 * A.P.n, 128), 128, 0, s>>>(A, in, use_hydro);
+    k_final<<<nblk(A.P.n, 128), 128, 0, s>>>(A, in, use_hydro);
     return cudaGetLastError();
 }
 

@@ -297,27 +297,38 @@ def population_noise(g: np.random.Generator, ncell: int, amp: float = 1e-3) -> n
 def _place_greedy(g: np.random.Generator, radii: np.ndarray, lo, hi, periodic, gap: float,
                   draws: int = 256):
     """Random sequential addition with a bounded number of draws per sphere: each sphere
-    takes the first of ``draws`` uniform candidates that clears every kept sphere by
-    ``gap`` (minimum image on periodic axes), or is dropped. Returns (positions, radii)."""
+    takes the first uniform candidate (drawn in batches of 64, 512, then ``draws``) that
+    clears every kept sphere by ``gap`` (minimum image on periodic axes), or is dropped.
+    Returns (positions, radii)."""
     L = hi - lo
     per = np.array([bool(x) for x in periodic])
     keep_p, keep_r = [], []
+    P = np.zeros((0, 3))
+    Rk = np.zeros(0)
     for R in radii:
-        u = g.random((draws, 3))
         lo_c = np.where(per, lo, lo + R)
         span = np.where(per, L, L - 2 * R)
-        cand = lo_c + u * span
-        if keep_p:
-            P = np.array(keep_p)
-            d = cand[:, None, :] - P[None, :, :]
-            d = np.where(per, d - L * np.round(d / L), d)
-            ok = ((d ** 2).sum(-1) >= (R + np.array(keep_r) + gap) ** 2).all(1)
-        else:
-            ok = np.ones(draws, dtype=bool)
-        idx = np.flatnonzero(ok)
-        if idx.size:
-            keep_p.append(cand[idx[0]])
-            keep_r.append(R)
+        placed = False
+        for batch in (64, 512, draws):   # small batches first: most spheres fit at once
+            cand = lo_c + g.random((batch, 3)) * span
+            if len(P):
+                d = cand[:, None, :] - P[None, :, :]
+                d = np.where(per, d - L * np.round(d / L), d)
+                ok = ((d ** 2).sum(-1) >= (R + Rk + gap) ** 2).all(1)
+            else:
+                ok = np.ones(batch, dtype=bool)
+            idx = np.flatnonzero(ok)
+            if idx.size:
+                keep_p.append(cand[idx[0]])
+                keep_r.append(R)
+                P = np.array(keep_p)
+                Rk = np.array(keep_r)
+                placed = True
+                break
+            if batch >= draws:
+                break
+        if not placed:
+            continue
     return np.array(keep_p).reshape(-1, 3), np.array(keep_r)
 
 
@@ -559,3 +570,54 @@ def fluidised_bed(phi: float, nx: int = 500, ny: int = 200, nz: int = 800, diame
     w.triad = identity_triads(n)
     w.steps = steps
     return w
+
+
+def rheology_suspension(phi: float, n: int = 96, radius: float = 5.0, u_wall: float = 0.05,
+                        seed_index: int = 7, storage: str = "f32") -> Workload:
+    """Sheared suspension for the effective viscosity (Sec. 4.8 setup at reduced size):
+    n^3 lattice, walls at z moving at -/+ u_wall along x, periodic x and y, neutrally
+    buoyant spheres of radius 5 (10 cells per diameter, as in the paper) at solid fraction
+    phi placed at random (bounded draws; the fraction reached is n_spheres * volume / n^3),
+    fluid and particles on the linear profile, 10 DEM substeps, linear law lasting 20
+    substeps, friction 0.45, restitution 0.95, distance-based solid fractions."""
+    g = rng(seed_index)
+    w = Workload(name=f"rheology_{n}^3_phi{phi:.2f}", nx=n, ny=n, nz=n, periodic=(1, 1, 0))
+    w.u_wall[2, 0, 0] = -u_wall
+    w.u_wall[2, 1, 0] = +u_wall
+    vol = 4.0 / 3.0 * math.pi * radius ** 3
+    target = int(round(phi * n ** 3 / vol))
+    lo = np.array([-0.5, -0.5, 0.5])
+    hi = np.array([n - 0.5, n - 0.5, n - 1.5])
+    pos, radii = _place_greedy(g, np.full(target, radius), lo, hi, (1, 1, 0), gap=0.2, draws=2048)
+    k = len(radii)
+    m = vol
+    kn = 0.5 * (m / 2) * (math.pi / 2.0) ** 2   # contact >= 20 substeps of 1/10
+    w.params = base_params(tau=0.8, storage=storage, voxel="distance", n_sub=10, rho_f=1.0,
+                           law="linear", k_n=kn, k_t=kn * 2.0 / 7.0, restitution=0.95, friction=0.45,
+                           skin=0.5, dem_h=2 * radius + 0.5)
+    w.shape = np.zeros(k, dtype=np.int32)
+    w.radius = radii
+    w.semi = np.tile(radii[:, None], (1, 3))
+    w.density = np.ones(k)
+    w.pos = pos
+    w.vel = np.zeros((k, 3))
+    w.vel[:, 0] = -u_wall + 2.0 * u_wall * (pos[:, 2] + 0.5) / n
+    w.omg = np.zeros((k, 3))
+    w.omg[:, 1] = u_wall / n      # the rotation of the undisturbed shear flow (du/dz / 2)
+    w.triad = identity_triads(k)
+    z = np.arange(n, dtype=np.float64)
+    u = np.zeros((3, n, n, n), dtype=np.float32)
+    u[0] = (-u_wall + 2.0 * u_wall * (z + 0.5) / n)[:, None, None]
+    w.init_u = u.reshape(3, -1)
+    w.steps = 20000
+    return w
+
+
+def wall_shear_rate(ux_profile: np.ndarray, u_wall: float) -> float:
+    """Shear rate at the walls of a z-profile of u_x between halfway walls at -1/2 (moving at
+    -u_wall) and nz - 1/2 (+u_wall): slope at the wall of the parabola through the wall value
+    and the first two fluid nodes (Sec. 4.8), averaged over both walls."""
+    u = np.asarray(ux_profile, dtype=np.float64)
+    bottom = -8.0 / 3.0 * (-u_wall) + 3.0 * u[0] - u[1] / 3.0
+    top = -8.0 / 3.0 * u_wall + 3.0 * u[-1] - u[-2] / 3.0
+    return 0.5 * (bottom - top)

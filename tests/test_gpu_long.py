@@ -127,3 +127,31 @@ def test_checkpoint_resume_coupled():
     pa, va, _, _ = a.particles()
     pb, vb, _, _ = b.particles()
     assert np.abs(pa - pb).max() < 1e-7
+
+
+def _eta_rel(w, steps=8000, every=250):
+    from paper_2512_04997_gb300 import ledds
+    torch = pytest.importorskip("torch")
+    n, U = w.nz, w.u_wall[2, 1, 0]
+    s = ledds.from_workload(w)
+    s.step(steps // 2)
+    prof = torch.zeros(n, dtype=torch.float64, device="cuda")
+    k = 0
+    for _ in range(steps // 2 // every):
+        s.step(every)
+        _, u = s.fields()
+        prof += u[0].view(n, -1).double().mean(1)
+        k += 1
+    return W.wall_shear_rate((prof / k).cpu().numpy(), U) / (2.0 * U / n)
+
+
+def test_effective_viscosity_method():
+    """The wall-stress estimate of the effective viscosity (Sec. 4.8): exactly 1 for the
+    particle-free sheared box (a linear profile), and above 1, of the order of the
+    Krieger-Dougherty value (1.31), at solid fraction 0.1 on a short run."""
+    w0 = W.rheology_suspension(0.0, n=64)
+    assert abs(_eta_rel(w0, steps=2000) - 1.0) < 1e-3
+    w1 = W.rheology_suspension(0.1, n=64)
+    eta = _eta_rel(w1, steps=8000)
+    print(f"eta/eta0 at phi 0.1 (64^3, 8000 steps): {eta:.3f}")
+    assert 1.05 < eta < 1.8, eta
