@@ -774,13 +774,14 @@ __device__ __noinline__ bool wall_geo_f_general(const DemArgs& A, const double* 
 }
 
 // pair_contrib with FP32 contact arithmetic (ellipsoid geometry stays FP64).
+template <bool SPHERES>
 __device__ void pair_contrib_f(const DemArgs& A, const double* st, int cb, int i, int m, F2 F[3], F2 M[3]) {
     const int j = A.cand[cb][(long long)i * A.ccap + m];
     double* hl = A.hist[cb] + ((long long)i * A.ccap + m) * 3;
     const int a = i < j ? i : j, b = i < j ? j : i;
     GeoF g;
     bool hit_;
-    if (A.P.shape[a] == LEDDS_SPHERE && A.P.shape[b] == LEDDS_SPHERE) {
+    if (SPHERES || (A.P.shape[a] == LEDDS_SPHERE && A.P.shape[b] == LEDDS_SPHERE)) {
         double dd[3];
         for (int c = 0; c < 3; ++c) dd[c] = min_image(A, c, stv(A, st, SP + c, a) - stv(A, st, SP + c, b));
         hit_ = sphere_geo_f(dd, A.P.radius[a], A.P.radius[b], g);
@@ -823,6 +824,7 @@ __device__ void pair_contrib_f(const DemArgs& A, const double* st, int cb, int i
 }
 
 // wall_contrib with FP32 contact arithmetic.
+template <bool SPHERES>
 __device__ void wall_contrib_f(const DemArgs& A, const double* st, int i, int face, F2 F[3], F2 M[3]) {
     const int ax = face >> 1, side = face & 1;
     double* wh = A.whist + ((long long)i * 6 + face) * 3;
@@ -831,7 +833,7 @@ __device__ void wall_contrib_f(const DemArgs& A, const double* st, int i, int fa
         return;
     }
     GeoF g;
-    if (A.P.shape[i] == LEDDS_SPHERE) {
+    if (SPHERES || A.P.shape[i] == LEDDS_SPHERE) {
         const double R = A.P.radius[i];
         const double r = stv(A, st, SP + ax, i);
         const double dist = side == 0 ? r - A.lo[ax] : A.hi[ax] - r;
@@ -1062,7 +1064,7 @@ __global__ void __launch_bounds__(128, 6) k_contacts_gather(DemArgs A, int in, i
                 mo[c] = f2_add(mo[c], r[((own ? 3 : 6) + c) * pcap + p]);
             }
         }
-        if (lane < 6) wall_contrib_f(A, st, k, lane, f, mo);
+        if (lane < 6) wall_contrib_f<false>(A, st, k, lane, f, mo);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -1116,8 +1118,8 @@ __device__ void contact_sum_warp(const DemArgs& A, const double* st, int cb, int
     if (A.force_f32) {
         F2 f[3], m[3];
         for (int c = 0; c < 3; ++c) f[c] = m[c] = F2{0.0f, 0.0f};
-        for (int q = lane; q < nc; q += 32) pair_contrib_f(A, st, cb, i, q, f, m);
-        if (lane < 6) wall_contrib_f(A, st, i, lane, f, m);
+        for (int q = lane; q < nc; q += 32) pair_contrib_f<false>(A, st, cb, i, q, f, m);
+        if (lane < 6) wall_contrib_f<false>(A, st, i, lane, f, m);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -1262,6 +1264,34 @@ __global__ void k_predict_first(DemArgs A) {
     predict(A, k, r, v, acc, w, d);
     for (int a = 0; a < 3; ++a) A.P.st[0][(long long)(SP + a) * A.P.cap + k] = r[a];
     for (int m = 0; m < 9; ++m) A.P.st[0][(long long)(ST + m) * A.P.cap + k] = d[m];
+}
+
+// k_contacts for the common case (only spheres, FP32 contact arithmetic): the same
+// sums without the ellipsoid and FP64 branches, which keeps its registers low.
+__global__ void __launch_bounds__(128) k_contacts_spheres(DemArgs A, int in, int cb) {
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (k >= A.P.n) return;  // uniform across the warp
+    const int lane = threadIdx.x & 31;
+    const double* st = A.P.st[in];
+    const int nc = A.ncand[cb][k];
+    F2 f[3], m[3];
+    for (int c = 0; c < 3; ++c) f[c] = m[c] = F2{0.0f, 0.0f};
+    for (int q = lane; q < nc; q += 32) pair_contrib_f<true>(A, st, cb, k, q, f, m);
+    if (lane < 6) wall_contrib_f<true>(A, st, k, lane, f, m);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            F2 of{__shfl_xor_sync(0xffffffffu, f[c].hi, off), __shfl_xor_sync(0xffffffffu, f[c].lo, off)};
+            F2 om{__shfl_xor_sync(0xffffffffu, m[c].hi, off), __shfl_xor_sync(0xffffffffu, m[c].lo, off)};
+            f[c] = f2_add(f[c], of);
+            m[c] = f2_add(m[c], om);
+        }
+    if (lane != 0) return;
+    for (int a = 0; a < 3; ++a) {
+        A.P.Fc[(long long)a * A.P.cap + k] = (double)f[a].hi + (double)f[a].lo;
+        A.P.Mc[(long long)a * A.P.cap + k] = (double)m[a].hi + (double)m[a].lo;
+    }
 }
 
 // End of a substep for one particle (thread per particle): the corrector with the held
@@ -1540,6 +1570,8 @@ cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_ste
         k_pair_forces<<<(unsigned)((maxp + 127) / 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_list, A.cp_res,
                                                                      A.cp_stride);
         k_contacts_gather<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_res, A.cp_stride);
+    } else if (A.force_f32) {  // no ellipsoid in the simulation (pair_once is off)
+        k_contacts_spheres<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
     } else {
         k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
     }

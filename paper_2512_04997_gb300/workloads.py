@@ -621,3 +621,39 @@ def wall_shear_rate(ux_profile: np.ndarray, u_wall: float) -> float:
     bottom = -8.0 / 3.0 * (-u_wall) + 3.0 * u[0] - u[1] / 3.0
     top = -8.0 / 3.0 * u_wall + 3.0 * u[-1] - u[-2] / 3.0
     return 0.5 * (bottom - top)
+
+
+def jeffery_ellipsoid(a: float = 12.0, b: float = 6.0, box=(96, 64, 96), u_wall: float = 0.05,
+                      angle: float = 0.0, tau: float = 0.8, steps: int = 9000) -> Workload:
+    """One neutrally buoyant prolate ellipsoid (semi-axes a, b, b) at the centre of a
+    sheared box (walls at z moving at -/+ u_wall along x, periodic x and y), its major axis
+    in the flow-gradient (x-z) plane at `angle` from the flow direction, started with the
+    fluid's rotation rate; subdivision solid fractions. Jeffery: the major axis turns by pi
+    in pi (a^2 + b^2) / (a b shear_rate)."""
+    nx, ny, nz = box
+    w = Workload(name=f"jeffery_{a:g}x{b:g}_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0))
+    w.u_wall[2, 0, 0] = -u_wall
+    w.u_wall[2, 1, 0] = +u_wall
+    shear = 2.0 * u_wall / nz
+    c, s = math.cos(angle), math.sin(angle)
+    d1 = np.array([c, 0.0, s])
+    d2 = np.array([0.0, 1.0, 0.0])
+    d3 = np.cross(d1, d2)
+    vol = 4.0 / 3.0 * math.pi * a * b * b
+    kn = 0.5 * vol * (math.pi / 2.0) ** 2
+    w.params = base_params(tau=tau, voxel="subdiv", subdiv_n=10, n_sub=10, rho_f=1.0, law="linear",
+                           k_n=kn, k_t=kn * 2.0 / 7.0, skin=0.5, dem_h=2.0 * a + 0.5)
+    w.shape = np.ones(1, dtype=np.int32)
+    w.radius = np.array([a])
+    w.semi = np.array([[a, b, b]])
+    w.density = np.ones(1)
+    w.pos = np.array([[nx / 2.0 - 0.5, ny / 2.0 - 0.5, nz / 2.0 - 0.5]])
+    w.vel = np.zeros((1, 3))
+    w.omg = np.array([[0.0, shear / 2.0, 0.0]])
+    w.triad = np.concatenate([d1, d2, d3])[None, :]
+    z = np.arange(nz, dtype=np.float64)
+    u = np.zeros((3, nz, ny, nx), dtype=np.float32)
+    u[0] = (-u_wall + 2.0 * u_wall * (z + 0.5) / nz)[:, None, None]
+    w.init_u = u.reshape(3, -1)
+    w.steps = steps
+    return w

@@ -1,6 +1,8 @@
 """Longer GPU parity runs and checkpoint resume: the 1000-step FP32 bound on a c3-shaped
 64^3 crop, the reduced-precision bounds (fields 2e-3, drag 0.5 %) on the settling sphere,
 and bit-identical resume from a checkpoint."""
+import math
+
 import numpy as np
 import pytest
 
@@ -155,3 +157,46 @@ def test_effective_viscosity_method():
     eta = _eta_rel(w1, steps=8000)
     print(f"eta/eta0 at phi 0.1 (64^3, 8000 steps): {eta:.3f}")
     assert 1.05 < eta < 1.8, eta
+
+
+def test_jeffery_orbit_period():
+    """A prolate ellipsoid (a = 12, b = 6: 12 cells across the minor axis) in shear: the
+    major axis turns by pi in pi (a^2 + b^2)/(a b shear_rate) (Jeffery); within 5 %. The
+    time is taken between the crossings of the flow direction (angle 0 and pi), where the
+    rotation is slowest and the crossing time sharpest."""
+    from paper_2512_04997_gb300 import ledds
+    a, b = 12.0, 6.0
+    w = W.jeffery_ellipsoid(a, b, angle=0.3)
+    s = ledds.from_workload(w)
+    shear = 2.0 * 0.05 / w.nz
+    T = math.pi * (a * a + b * b) / (a * b * shear)
+    every = 20
+    angles, times = [], []
+    prev = None
+    turn = 0.0
+    for k in range(int(1.6 * T / every)):
+        s.step(every)
+        d1 = s.particles()[3][0][:3]
+        ang = math.atan2(d1[2], d1[0])          # angle of the major axis in the x-z plane
+        if prev is not None:
+            da = ang - prev
+            da -= math.pi * round(da / math.pi)  # the axis is a line: unwrap modulo pi
+            turn += da
+        prev = ang
+        angles.append(turn)
+        times.append((k + 1) * every)
+    angles = np.array(angles)
+    times = np.array(times)
+    sense = np.sign(angles[-1])
+    psi = np.maximum.accumulate(np.abs(angles))   # angle turned so far
+    # the axis starts 0.3 rad from the flow direction and crosses it (slowest rotation)
+    # after turning 0.3 (clockwise seen along +y) or pi - 0.3, and again pi later
+    first = 0.3 if sense < 0 else math.pi - 0.3
+    t1 = np.interp(first, psi, times)
+    t2 = np.interp(first + math.pi, psi, times)
+    assert psi[-1] > first + math.pi, psi[-1]
+    T_meas = t2 - t1
+    print(f"Jeffery half period: measured {T_meas:.0f} steps, theory {T:.0f}")
+    assert abs(T_meas / T - 1.0) < 0.05, (T_meas, T)
+    st = s.status()
+    assert st["rc"] == 0 and st["nan_detected"] == 0, st

@@ -206,3 +206,24 @@ def test_coupled_step_momentum_budget(oracle):
     _, v1, _, _ = s.particles()
     assert np.abs(v1 - vel).max() > 1e-4          # the particles did exchange momentum
     assert np.allclose(b1, b0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("angle", [math.pi / 2, 0.0])
+def test_jeffery_rotation_rate(oracle, angle):
+    """A prolate ellipsoid (a = 6, b = 3, aspect ratio r = 2) in shear rotates about the
+    vorticity axis at Jeffery's rate shear (r^2 sin^2 phi + cos^2 phi)/(r^2 + 1), phi the
+    angle of the major axis from the flow direction: checked after 300 steps (the rate at the
+    orientation then reached) with the major axis started along the gradient (fastest) and
+    along the flow (slowest), within 8 %. The wrong sign of the solid surface velocity
+    (the printed u_k = v_k - w_k x r) would reverse the torque feedback and fail this."""
+    from _helpers import oracle_from_workload
+    w = W.jeffery_ellipsoid(a=6.0, b=3.0, box=(32, 24, 32), angle=angle, u_wall=0.02, steps=300)
+    o = oracle_from_workload(oracle, w)
+    o.step(w.steps)
+    _, _, omg, tri = o.particles()
+    d1 = tri[0][:3]
+    phi = math.atan2(d1[2], d1[0])
+    shear, r = 0.04 / 32, 2.0
+    jeffery = shear * (r * r * math.sin(phi) ** 2 + math.cos(phi) ** 2) / (r * r + 1.0)
+    assert omg[0][1] > 0.0
+    assert abs(omg[0][1] / jeffery - 1.0) < 0.08, (omg[0][1], jeffery)
