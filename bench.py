@@ -387,6 +387,22 @@ def oracle_sample(steps):
             "seconds": dt}
 
 
+def main_workload(args):
+    """The Couette suspension the main line is measured on (edge E, spheres scaled with E^3)."""
+    from paper_2512_04997_gb300 import workloads as W
+    E = args.edge
+    return W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
+                                storage=args.storage)
+
+
+def main_config(w, storage, world):
+    N = w.ncell
+    return {"workload": w.name, "cells": N, "particles": w.n, "storage": storage,
+            "n_sub": w.params["n_sub"], "tau": w.params["tau"], "voxel": w.params["voxel"],
+            "l2": f"inputs larger than L2 (populations 2 x 19 x {N / 1e6:.1f}M values)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -401,8 +417,7 @@ def run_reference(args):
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * res["seconds"] / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "couette_suspension_256x256x32_500spheres (slab sample of "
-                                   "couette_suspension_256x256x256_4000spheres)", "n_sub": 10},
+            "config": main_config(main_workload(args), args.storage, args.gpus),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
                              "value": res["value"], "unit": "MLUPS"},
             "e2e": {"value": res["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -430,9 +445,7 @@ def main():
         if rank == 0:
             print(json.dumps({"ensemble": ens, "steps": args.steps, "warmup": args.warmup}), flush=True)
         return
-    E = args.edge
-    w = W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
-                             storage=args.storage)
+    w = main_workload(args)
     N = w.ncell
     sim = ledds.from_workload(w, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
@@ -541,11 +554,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": w.name, "cells": N, "particles": w.n,
-                           "storage": args.storage, "n_sub": w.params["n_sub"],
-                           "tau": w.params["tau"], "voxel": w.params["voxel"],
-                           "l2": f"inputs larger than L2 (populations 2 x 19 x {N / 1e6:.1f}M values)",
-                           "parallelism": f"replicas x{world}"},
+                "config": main_config(w, args.storage, world),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": st["launches_per_step"] * args.steps,
                 "clocks": clk, "stages_ms_per_step": {k: v / psteps for k, v in zip(STAGES, stage_ms)},

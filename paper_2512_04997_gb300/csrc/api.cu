@@ -78,6 +78,7 @@ struct ledds_sim_s {
     double* hist[2] = {nullptr, nullptr};
     double* whist = nullptr;
     DevStatus* status = nullptr;
+    int sms = 1;             // multiprocessors of the device (launch shapes)
     double max_bound = 0.0;  // largest bounding radius of the current particles
     int any_ellipsoid = 0;   // some current particle is an ellipsoid
     // state
@@ -327,6 +328,8 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     a.ntx = s->ntx;
     a.nty = s->nty;
     a.ntz = s->ntz;
+    // fewer tiles than two waves of CTAs: split each tile's planes over four CTAs
+    a.zsplit = s->ntiles < 2 * s->sms ? 4 : 1;
     a.tile_cap = s->tile_cap;
     a.tile_count = s->tile_count;
     a.tile_ids = s->tile_ids;
@@ -569,6 +572,12 @@ int ledds_create(const ledds_dims* d, const ledds_params* p, void* d_workspace, 
     memset(s->uw, 0, sizeof(s->uw));
     domain(d, s->lo, s->hi, s->L);
     layout(s, d, p, s->ws);
+    {
+        int dev = 0, n_sm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0)
+            s->sms = n_sm;
+    }
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->fork_ev, cudaEventDisableTiming) != cudaSuccess ||

@@ -141,6 +141,7 @@ struct LbmArgs {
     int mi[3];                    // per axis: node-particle offsets may need a periodic wrap
     // tile lists
     int ntx, nty, ntz, tile_cap;
+    int zsplit;                   // CTAs per tile of the PSM kernel (1, or more for small lattices)
     const int* tile_count;
     const int* tile_ids;
     // particles (the state buffer the fluid step sees)

@@ -892,7 +892,8 @@ struct CollidePairs<SS, 19, SOLID, TRT> {
 // One 32x8xTILE_Z tile (bx, by, bz) of the lattice described by `a`; psm_smem holds the
 // tile cache followed by the pipeline stages (psm_smem_bytes()).
 template <int STORE, bool TRT>
-__device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, unsigned char* psm_smem) {
+__device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, int zlo, int zhi,
+                                         unsigned char* psm_smem) {
     using SS = Store<STORE>;
     using T = typename SS::T;
     constexpr int PSM_STAGES = PsmCfg<STORE>::stages;
@@ -907,11 +908,13 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
     const int x = x0 + lane, y = y0 + warp;
     const bool valid_xy = x < a.nx && y < a.ny;
 
-    // prologue: the first planes in flight while the tile's particles are cached
+    // prologue: the first planes (of this CTA's planes zlo .. zhi-1 of the tile) in flight
+    // while the tile's particles are cached
 #pragma unroll
     for (int q = 0; q < PSM_STAGES - 1; ++q) {
-        const int z = z0 + q;
-        issue_node<SS>(a, pin, x, y, z, valid_xy && z < a.nz, stage + (q * 19) * PSM_THREADS + tid);
+        const int z = z0 + zlo + q;
+        issue_node<SS>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
+                       stage + (q * 19) * PSM_THREADS + tid);
         cp_async_commit();
     }
     const int cnt = min(a.tile_count[tile], a.tile_cap);
@@ -921,11 +924,12 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
     const float tau = a.tau, omega = a.omega;
     int hkey = -1;                                   // solid held in the running sum
     float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // its force and torque so far
-    for (int iz = 0; iz < TILE_Z; ++iz) {
+    for (int iz = zlo; iz < zhi; ++iz) {
+        const int r = iz - zlo;  // position in the pipeline ring
         {   // keep PSM_STAGES - 1 planes ahead in flight
-            const int q = iz + PSM_STAGES - 1;
-            const int z = z0 + q;
-            issue_node<SS>(a, pin, x, y, z, q < TILE_Z && valid_xy && z < a.nz,
+            const int q = r + PSM_STAGES - 1;
+            const int z = z0 + zlo + q;
+            issue_node<SS>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
                            stage + ((q % PSM_STAGES) * 19) * PSM_THREADS + tid);
             cp_async_commit();
         }
@@ -938,7 +942,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         float g[19];
         Plan pl;
         make_plan(a, valid ? x : 0, y, z, pl);
-        const uint32_t* slot = stage + ((iz % PSM_STAGES) * 19) * PSM_THREADS + tid;
+        const uint32_t* slot = stage + ((r % PSM_STAGES) * 19) * PSM_THREADS + tid;
         if (__any_sync(FULL, valid && pl.bw != 0u)) {
             if (valid) ReadAll<SS, 0, true>::run(a, pl, slot, g);
         } else if (valid) {
@@ -1079,7 +1083,9 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
 template <int STORE, bool TRT>
 __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const LbmArgs a) {
     extern __shared__ __align__(16) unsigned char psm_smem[];
-    psm_tile<STORE, TRT>(a, blockIdx.x, blockIdx.y, blockIdx.z, psm_smem);
+    // small lattices: a.zsplit CTAs share a tile, each taking TILE_Z / zsplit of its planes
+    const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
+    psm_tile<STORE, TRT>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per, part * per + per, psm_smem);
 }
 
 // Batched form: persistent CTAs take (simulation, tile) work items from a queue, so many
@@ -1116,7 +1122,7 @@ __global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const
         const LbmArgs& a = P.a[sim];
         const int t = item - P.tile_start[sim];
         const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
-        psm_tile<STORE, TRT>(a, bx, by, bz, smem);
+        psm_tile<STORE, TRT>(a, bx, by, bz, 0, TILE_Z, smem);
         __syncthreads();
     }
 }
@@ -1245,7 +1251,7 @@ static cudaError_t launch_psm_t(const LbmArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm<STORE, TRT><<<tile_grid(a), PSM_THREADS, smem, s>>>(a);
+    k_psm<STORE, TRT><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a);
     return cudaGetLastError();
 }
 
