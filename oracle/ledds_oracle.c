@@ -643,9 +643,95 @@ void or_lbm_psm_step(or_sim* s) {
 /* DEM: integration (Sec. 2.2)                                                            */
 /* ------------------------------------------------------------------------------------ */
 
+/* Orientation as a unit quaternion q = (w, x, y, z) of the rotation that takes body
+ * components to world components: that rotation's matrix has the triad d1, d2, d3 as
+ * its columns (R, with the triad as rows, is its transpose). The matrix of q is the
+ * textbook one, e.g. its (0,1) entry is 2(xy - wz). */
+void or_triad_from_quat(const double q[4], double d[9]) {
+    const double w = q[0], x = q[1], y = q[2], z = q[3];
+    double m[3][3];
+    m[0][0] = 1.0 - 2.0 * (y * y + z * z);
+    m[0][1] = 2.0 * (x * y - w * z);
+    m[0][2] = 2.0 * (x * z + w * y);
+    m[1][0] = 2.0 * (x * y + w * z);
+    m[1][1] = 1.0 - 2.0 * (x * x + z * z);
+    m[1][2] = 2.0 * (y * z - w * x);
+    m[2][0] = 2.0 * (x * z - w * y);
+    m[2][1] = 2.0 * (y * z + w * x);
+    m[2][2] = 1.0 - 2.0 * (x * x + y * y);
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) d[3 * i + a] = m[a][i];   /* d_i = column i */
+}
+
+/* Inverse of or_triad_from_quat (Shepperd, J. Guid. Control 1, 1978): of the four
+ * quantities 4w^2, 4x^2, 4y^2, 4z^2 obtainable from the diagonal, take the largest
+ * from its square root and the other three from off-diagonal sums and differences;
+ * then normalise (the triad may carry rounding). */
+void or_quat_from_triad(const double d[9], double q[4]) {
+    double m[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) m[a][i] = d[3 * i + a];
+    const double tr = m[0][0] + m[1][1] + m[2][2];
+    double w, x, y, z;
+    if (tr >= m[0][0] && tr >= m[1][1] && tr >= m[2][2]) {
+        w = 0.5 * sqrt(1.0 + tr);
+        x = (m[2][1] - m[1][2]) / (4.0 * w);
+        y = (m[0][2] - m[2][0]) / (4.0 * w);
+        z = (m[1][0] - m[0][1]) / (4.0 * w);
+    } else if (m[0][0] >= m[1][1] && m[0][0] >= m[2][2]) {
+        x = 0.5 * sqrt(1.0 + m[0][0] - m[1][1] - m[2][2]);
+        w = (m[2][1] - m[1][2]) / (4.0 * x);
+        y = (m[0][1] + m[1][0]) / (4.0 * x);
+        z = (m[0][2] + m[2][0]) / (4.0 * x);
+    } else if (m[1][1] >= m[2][2]) {
+        y = 0.5 * sqrt(1.0 - m[0][0] + m[1][1] - m[2][2]);
+        w = (m[0][2] - m[2][0]) / (4.0 * y);
+        x = (m[0][1] + m[1][0]) / (4.0 * y);
+        z = (m[1][2] + m[2][1]) / (4.0 * y);
+    } else {
+        z = 0.5 * sqrt(1.0 - m[0][0] - m[1][1] + m[2][2]);
+        w = (m[1][0] - m[0][1]) / (4.0 * z);
+        x = (m[0][2] + m[2][0]) / (4.0 * z);
+        y = (m[1][2] + m[2][1]) / (4.0 * z);
+    }
+    const double nq = sqrt(w * w + x * x + y * y + z * z);
+    q[0] = w / nq;
+    q[1] = x / nq;
+    q[2] = y / nq;
+    q[3] = z / nq;
+}
+
+/* Quaternion orientation update (the option in place of the triad update): the body
+ * turns about the world axis w(t) by the angle |w(t)| dt, exactly,
+ *   q <- (cos(|w| dt/2), sin(|w| dt/2) w/|w|) (x) q,
+ * with the Hamilton product (a0, a) (x) (b0, b) = (a0 b0 - a.b, a0 b + b0 a + a x b),
+ * then q is normalised and the triad rebuilt from it. The triad update of Sec. 2.2 is
+ * the second-order Taylor expansion of the same rotation, so the two agree to
+ * O(dt^3) per step. */
+static void rotate_quat(double d[9], const double w[3], double dt) {
+    double q[4], dq[4], r[4];
+    or_quat_from_triad(d, q);
+    const double wn = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double c = 1.0, sn = 0.0;
+    if (wn > 0.0) {
+        c = cos(0.5 * dt * wn);
+        sn = sin(0.5 * dt * wn) / wn;
+    }
+    dq[0] = c;
+    for (int a = 0; a < 3; ++a) dq[1 + a] = sn * w[a];
+    double ab[3];
+    vcross(dq + 1, q + 1, ab);
+    r[0] = dq[0] * q[0] - vdot(dq + 1, q + 1);
+    for (int a = 0; a < 3; ++a) r[1 + a] = dq[0] * q[1 + a] + q[0] * dq[1 + a] + ab[a];
+    const double nr = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3]);
+    for (int m = 0; m < 4; ++m) r[m] /= nr;
+    or_triad_from_quat(r, d);
+}
+
 /* Predictor: Eq. (advance-r) for the position, then the orientation triad
  *   d_i* = d_i + dt w x d_i,   d_i <- d_i + dt w x (d_i + d_i*)/2,
- * re-orthonormalised; positions wrapped into the box on periodic axes. */
+ * re-orthonormalised (or, with orient = OR_ORIENT_QUAT, the exact rotation of
+ * rotate_quat); positions wrapped into the box on periodic axes. */
 static void predict(or_sim* s, double dt) {
     for (int k = 0; k < s->n; ++k) {
         double* r = s->pos + 3 * k;
@@ -655,6 +741,10 @@ static void predict(or_sim* s, double dt) {
             if (s->periodic[a]) r[a] = r[a] - s->L[a] * floor((r[a] - s->lo[a]) / s->L[a]);
         double* d = s->triad + 9 * k;
         const double* w = s->omg + 3 * k;
+        if (s->p.orient == OR_ORIENT_QUAT) {
+            rotate_quat(d, w, dt);
+            continue;
+        }
         for (int m = 0; m < 3; ++m) {
             double* dm = d + 3 * m;
             double wxd[3], ds[3], mid[3], wxm[3];

@@ -25,6 +25,7 @@ enum { OR_SPHERE = 0, OR_ELLIPSOID = 1 };
 enum { OR_VOXEL_DISTANCE = 0, OR_VOXEL_SUBDIV = 1 };
 enum { OR_LAW_LINEAR = 0, OR_LAW_HERTZ = 1 };
 enum { OR_COLLIDE_BGK = 0, OR_COLLIDE_TRT = 1 };
+enum { OR_ORIENT_TRIAD = 0, OR_ORIENT_QUAT = 1 };
 
 typedef struct {
     double tau;             /* BGK relaxation time, Eq. (tau)                                */
@@ -43,6 +44,7 @@ typedef struct {
     int ell_max_iter;       /* common-normal iteration cap (Sec. 2.1)                         */
     double ell_tol;         /* common-normal convergence tolerance, relative to min semi-axis */
     int collision;          /* OR_COLLIDE_BGK (Eq. BGK) or OR_COLLIDE_TRT (Eq. TRT)            */
+    int orient;             /* OR_ORIENT_TRIAD (Sec. 2.2 triad update) or OR_ORIENT_QUAT      */
 } or_params;
 
 typedef struct or_sim or_sim;
@@ -76,6 +78,10 @@ int or_set_particles(or_sim* s, int n, const int* shape, const double* radius,
 void or_get_particles(const or_sim* s, double* pos, double* vel, double* omg, double* triad);
 void or_get_forces(const or_sim* s, double* Fh, double* Mh, double* Fc, double* Mc);
 void or_get_accel(const or_sim* s, double* acc, double* alpha);
+/* Unit quaternion (w, x, y, z) of the body-to-world rotation whose columns are the
+ * triad d1, d2, d3 (Shepperd's method); and the triad of a unit quaternion. */
+void or_quat_from_triad(const double triad[9], double q[4]);
+void or_triad_from_quat(const double q[4], double triad[9]);
 
 /* One coupled (or DEM-only) time step, flowchart order of Sec. 3.2. */
 void or_step(or_sim* s, int nsteps);

@@ -15,6 +15,7 @@ SPHERE, ELLIPSOID = 0, 1
 VOXEL_DISTANCE, VOXEL_SUBDIV = 0, 1
 LAW_LINEAR, LAW_HERTZ = 0, 1
 COLLIDE_BGK, COLLIDE_TRT = 0, 1
+ORIENT_TRIAD, ORIENT_QUAT = 0, 1
 
 
 class Params(C.Structure):
@@ -37,6 +38,7 @@ class Params(C.Structure):
         ("ell_max_iter", C.c_int),
         ("ell_tol", C.c_double),
         ("collision", C.c_int),
+        ("orient", C.c_int),
     ]
 
 
@@ -66,6 +68,8 @@ def lib():
         L.or_get_particles.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.or_get_forces.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.or_get_accel.argtypes = [C.c_void_p, dp, dp]
+        L.or_quat_from_triad.argtypes = [dp, dp]
+        L.or_triad_from_quat.argtypes = [dp, dp]
         L.or_step.argtypes = [C.c_void_p, C.c_int]
         L.or_voxelize.argtypes = [C.c_void_p, dp, ip, ip]
         L.or_lbm_psm_step.argtypes = [C.c_void_p]
@@ -105,6 +109,7 @@ def default_params(**kw) -> Params:
     p.ell_max_iter = 60
     p.ell_tol = 1e-6
     p.collision = COLLIDE_BGK
+    p.orient = ORIENT_TRIAD
     for k, v in kw.items():
         if k in ("fluid_force", "gravity"):
             getattr(p, k)[:] = list(v)
@@ -255,6 +260,21 @@ def subdiv_count(rel, shape, radius, semi=(1, 1, 1), triad=None, n=10):
 
 def beta_distance(rel, radius):
     return lib().or_beta_distance(_d(rel, 3), float(radius))
+
+
+def quat_from_triad(triad):
+    """Unit quaternion (w, x, y, z) of the body-to-world rotation whose columns are the
+    triad rows d1, d2, d3 (Shepperd's method)."""
+    q = np.zeros(4)
+    lib().or_quat_from_triad(_d(triad, 9), q)
+    return q
+
+
+def triad_from_quat(q):
+    """Triad d1, d2, d3 (3x3, rows) of a unit quaternion (w, x, y, z)."""
+    d = np.zeros(9)
+    lib().or_triad_from_quat(_d(q, 4), d)
+    return d.reshape(3, 3)
 
 
 def cell_collide(f, tau, B=(), uk=(), arm=(), force=(0, 0, 0), collision=0):

@@ -404,3 +404,80 @@ def test_ellipsoid_contact_decision_matches_perram_wertheim(oracle):
         agree += (len(c) > 0) == (Fmax < 1.0)
     assert checked > 150 and contacts > 30
     assert agree == checked
+
+
+def _hamilton(a, b):
+    a0, av, b0, bv = a[0], np.asarray(a[1:]), b[0], np.asarray(b[1:])
+    return np.concatenate([[a0 * b0 - av @ bv], a0 * bv + b0 * av + np.cross(av, bv)])
+
+
+def _shoemake(g, n):
+    u = g.uniform(size=(n, 3))
+    return np.stack([np.sqrt(1 - u[:, 0]) * np.sin(2 * np.pi * u[:, 1]),
+                     np.sqrt(1 - u[:, 0]) * np.cos(2 * np.pi * u[:, 1]),
+                     np.sqrt(u[:, 0]) * np.sin(2 * np.pi * u[:, 2]),
+                     np.sqrt(u[:, 0]) * np.cos(2 * np.pi * u[:, 2])], axis=1)
+
+
+def test_quaternion_triad_conversions(oracle):
+    """Triad of a unit quaternion = the body axes e_i turned by the sandwich product
+    q (0, e_i) q*, and = Rodrigues' matrix of the quaternion's axis and angle; the
+    triad-to-quaternion conversion returns +-q, including half turns (w = 0), where
+    the trace branch cannot be used, and the identity."""
+    g = W.rng(411)
+    qs = list(_shoemake(g, 200))
+    for axis in np.eye(3):
+        qs.append(np.concatenate([[0.0], axis]))                          # half turns
+        qs.append(np.concatenate([[1e-9], axis]) / math.hypot(1e-9, 1.0))
+    qs.append(np.array([1.0, 0.0, 0.0, 0.0]))
+    for q in qs:
+        d = oracle.triad_from_quat(q)
+        qc = np.concatenate([[q[0]], -q[1:]])
+        for i in range(3):
+            e = np.concatenate([[0.0], np.eye(3)[i]])
+            assert np.allclose(d[i], _hamilton(_hamilton(q, e), qc)[1:], atol=1e-15)
+        if abs(q[0]) < 1.0:
+            ang = 2 * math.acos(max(-1.0, min(1.0, q[0])))
+            assert np.allclose(d, _rodrigues(q[1:], ang).T, atol=1e-14)
+        back = oracle.quat_from_triad(d.ravel())
+        assert min(np.abs(back - q).max(), np.abs(back + q).max()) < 1e-14
+
+
+@pytest.mark.parametrize("nsub", [1, 3])
+def test_free_rotation_quaternion_exact(oracle, nsub):
+    """With the quaternion orientation option a torque-free sphere spinning at w turns
+    by exactly |w| t about the world axis w, whatever dt (the triad update carries an
+    O(dt^2) error here), from any initial orientation: the rotation acts on the left
+    (world frame), so d_i(t) = Rod(w, |w| t) d_i(0)."""
+    g = W.rng(412)
+    q0 = _shoemake(g, 1)[0]
+    d0 = oracle.triad_from_quat(q0)
+    p = oracle.default_params(rho_f=0.0, dem_h=2.5, n_sub=nsub, orient=oracle.ORIENT_QUAT)
+    s = dem(oracle, 1, p, lo=(-50, -50, -50), hi=(50, 50, 50))
+    w = np.array([0.01, -0.02, 0.015])
+    s.set_particles([0], [1.0], [[1.0] * 3], [1.0], [[0, 0, 0]], omg=[w], triad=[d0.ravel()])
+    T = 100
+    s.step(T)
+    _, _, omg, tri = s.particles()
+    Rw = _rodrigues(w, np.linalg.norm(w) * T)
+    assert np.abs(tri[0].reshape(3, 3) - d0 @ Rw.T).max() < 1e-13
+    assert np.allclose(omg[0], w, atol=1e-16)
+
+
+def test_quaternion_and_triad_updates_agree_to_second_order(oracle):
+    """Torque-free asymmetric ellipsoid (gyroscopic term active): the quaternion and the
+    triad orientation updates differ by O(dt^3) per step, so the orientations after a
+    fixed time differ by O(dt^2): a quarter when dt halves."""
+    semi = [3.0, 2.0, 1.0]
+    diffs = []
+    for nsub in (10, 20):
+        tris = []
+        for orient in (oracle.ORIENT_TRIAD, oracle.ORIENT_QUAT):
+            p = oracle.default_params(rho_f=0.0, dem_h=7.0, n_sub=nsub, orient=orient)
+            s = dem(oracle, 1, p, lo=(-50, -50, -50), hi=(50, 50, 50))
+            s.set_particles([1], [3.0], [semi], [1.0], [[0, 0, 0]], omg=[[0.01, 0.002, 0.012]])
+            s.step(400)
+            tris.append(s.particles()[3][0])
+        diffs.append(np.abs(tris[0] - tris[1]).max())
+    assert 1e-9 < diffs[0] < 1e-4
+    assert 3.3 < diffs[0] / diffs[1] < 4.7
