@@ -47,6 +47,7 @@ enum { LEDDS_STORE_F32 = 0, LEDDS_STORE_F16 = 1, LEDDS_STORE_BF16 = 2 };
 enum { LEDDS_VOXEL_DISTANCE = 0, LEDDS_VOXEL_SUBDIV = 1 };
 enum { LEDDS_LAW_LINEAR = 0, LEDDS_LAW_HERTZ = 1 };
 enum { LEDDS_COLLIDE_BGK = 0, LEDDS_COLLIDE_TRT = 1 };
+enum { LEDDS_ORIENT_TRIAD = 0, LEDDS_ORIENT_QUAT = 1 };
 enum { LEDDS_SPHERE = 0, LEDDS_ELLIPSOID = 1 };
 
 /* Sizes fixed at creation. */
@@ -86,6 +87,11 @@ typedef struct {
                              /* 0: every DEM operation in FP64. Integration is always FP64.  */
     int collision;           /* LEDDS_COLLIDE_BGK (Eq. BGK) or LEDDS_COLLIDE_TRT (Eq. TRT,    */
                              /* 1/tau- = 8 (2 - 1/tau)/(8 - 1/tau)), weighted by 1 - B_tot    */
+    int orient;              /* orientation update of the predictor: LEDDS_ORIENT_TRIAD, the  */
+                             /* two-stage triad update of Sec. 2.2 with Gram-Schmidt, or      */
+                             /* LEDDS_ORIENT_QUAT, the exact rotation by |w| dt about w(t)    */
+                             /* through a unit quaternion (agrees with the triad update to    */
+                             /* O(dt^3) per step; the triad stays the stored orientation)     */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */
@@ -115,7 +121,7 @@ typedef struct ledds_sim_s* ledds_sim_t;
 
 /* Fill *p with defaults: tau 0.8, FP32 storage, distance voxels (subdiv_n 10), linear law,
  * n_sub 1, rho_f 1, no gravity/force, k_n 1000, k_t 2/7 k_n, restitution 0.7, friction
- * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
+ * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision, triad orientation update. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
 int ledds_params_default(ledds_params* p);
 
 /* Bytes of device workspace a simulation of these dimensions and parameters needs

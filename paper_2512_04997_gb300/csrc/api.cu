@@ -136,6 +136,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->skin < 0.0) return LEDDS_ERR_INVALID_ARG;
     if (p->force_fp32 < 0 || p->force_fp32 > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->collision < 0 || p->collision > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->orient < 0 || p->orient > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -386,6 +387,7 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     A.ell_max_iter = s->p.ell_max_iter;
     A.ell_tol = s->p.ell_tol;
     A.force_f32 = s->p.force_fp32;
+    A.quat = s->p.orient == LEDDS_ORIENT_QUAT;
     A.pair_once = s->any_ellipsoid;
     A.cp_cnt = s->pair_cnt;
     A.cp_off = s->pair_off;
@@ -545,6 +547,7 @@ int ledds_params_default(ledds_params* p) {
     p->ell_tol = 1e-6;
     p->force_fp32 = 1;
     p->collision = LEDDS_COLLIDE_BGK;
+    p->orient = LEDDS_ORIENT_TRIAD;
     return LEDDS_OK;
 }
 

@@ -1167,8 +1167,63 @@ __device__ __forceinline__ double dot3_fma(const double a[3], const double b[3])
     return __fma_rn(a[0], b[0], __fma_rn(a[1], b[1], a[2] * b[2]));
 }
 
-// Predictor: Eq. (advance-r) and the triad update with w(t), then Gram-Schmidt;
-// positions wrapped on periodic axes; displacement since the last rebuild checked.
+// Quaternion orientation update: the triad (rows d_i = columns of the body-to-world
+// rotation) becomes a unit quaternion by Shepperd's method (the largest of 4w^2, 4x^2,
+// 4y^2, 4z^2 from the diagonal, the rest from off-diagonal sums and differences), is
+// turned on the left by (cos(|w| dt/2), sin(|w| dt/2) w/|w|), i.e. by the angle |w| dt
+// about the world axis w exactly, normalised, and written back as a triad.
+__device__ void quat_turn(double d[9], const double w[3], double dt) {
+    // m[a][i] = d[3 i + a]
+    const double m00 = d[0], m11 = d[4], m22 = d[8];
+    const double m01 = d[3], m10 = d[1], m02 = d[6], m20 = d[2], m12 = d[7], m21 = d[5];
+    const double tr = m00 + m11 + m22;
+    double q0, q1, q2, q3;
+    if (tr >= m00 && tr >= m11 && tr >= m22) {
+        q0 = 0.5 * sqrt(1.0 + tr);
+        const double f = 0.25 / q0;
+        q1 = (m21 - m12) * f; q2 = (m02 - m20) * f; q3 = (m10 - m01) * f;
+    } else if (m00 >= m11 && m00 >= m22) {
+        q1 = 0.5 * sqrt(1.0 + m00 - m11 - m22);
+        const double f = 0.25 / q1;
+        q0 = (m21 - m12) * f; q2 = (m01 + m10) * f; q3 = (m02 + m20) * f;
+    } else if (m11 >= m22) {
+        q2 = 0.5 * sqrt(1.0 - m00 + m11 - m22);
+        const double f = 0.25 / q2;
+        q0 = (m02 - m20) * f; q1 = (m01 + m10) * f; q3 = (m12 + m21) * f;
+    } else {
+        q3 = 0.5 * sqrt(1.0 - m00 - m11 + m22);
+        const double f = 0.25 / q3;
+        q0 = (m10 - m01) * f; q1 = (m02 + m20) * f; q2 = (m12 + m21) * f;
+    }
+    const double wn = sqrt(dot3_fma(w, w));
+    double c = 1.0, sn = 0.0;
+    if (wn > 0.0) {
+        sincos(0.5 * dt * wn, &sn, &c);
+        sn /= wn;
+    }
+    const double p1 = sn * w[0], p2 = sn * w[1], p3 = sn * w[2];
+    // (c, p) (x) (q0, q): scalar c q0 - p.q, vector c q + q0 p + p x q
+    double r0 = c * q0 - (p1 * q1 + p2 * q2 + p3 * q3);
+    double r1 = c * q1 + q0 * p1 + (p2 * q3 - p3 * q2);
+    double r2 = c * q2 + q0 * p2 + (p3 * q1 - p1 * q3);
+    double r3 = c * q3 + q0 * p3 + (p1 * q2 - p2 * q1);
+    const double in = rsqrt(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    r0 *= in; r1 *= in; r2 *= in; r3 *= in;
+    // rotation matrix of r, stored by columns as the triad
+    d[0] = 1.0 - 2.0 * (r2 * r2 + r3 * r3);
+    d[1] = 2.0 * (r1 * r2 + r0 * r3);
+    d[2] = 2.0 * (r1 * r3 - r0 * r2);
+    d[3] = 2.0 * (r1 * r2 - r0 * r3);
+    d[4] = 1.0 - 2.0 * (r1 * r1 + r3 * r3);
+    d[5] = 2.0 * (r2 * r3 + r0 * r1);
+    d[6] = 2.0 * (r1 * r3 + r0 * r2);
+    d[7] = 2.0 * (r2 * r3 - r0 * r1);
+    d[8] = 1.0 - 2.0 * (r1 * r1 + r2 * r2);
+}
+
+// Predictor: Eq. (advance-r) and the triad update with w(t), then Gram-Schmidt (or,
+// with A.quat, quat_turn); positions wrapped on periodic axes; displacement since the
+// last rebuild checked.
 __device__ void predict(const DemArgs& A, int k, double r[3], const double v[3], const double acc[3],
                         const double w[3], double d[9]) {
     const double dt = A.dt, h2 = dt * dt / 2.0;
@@ -1179,24 +1234,28 @@ __device__ void predict(const DemArgs& A, int k, double r[3], const double v[3],
             const double q = r[a] - A.lo[a];
             if (q < 0.0 || q >= 0.999999 * A.L[a]) r[a] = r[a] - A.L[a] * floor(q / A.L[a]);
         }
-    for (int m = 0; m < 3; ++m) {
-        double* dm = d + 3 * m;
-        double wxd[3], ds[3], mid[3], wxm[3];
-        cross3_fma(w, dm, wxd);
-        for (int a = 0; a < 3; ++a) ds[a] = __fma_rn(dt, wxd[a], dm[a]);
-        for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (dm[a] + ds[a]);
-        cross3_fma(w, mid, wxm);
-        for (int a = 0; a < 3; ++a) dm[a] = __fma_rn(dt, wxm[a], dm[a]);
+    if (A.quat) {
+        quat_turn(d, w, dt);
+    } else {
+        for (int m = 0; m < 3; ++m) {
+            double* dm = d + 3 * m;
+            double wxd[3], ds[3], mid[3], wxm[3];
+            cross3_fma(w, dm, wxd);
+            for (int a = 0; a < 3; ++a) ds[a] = __fma_rn(dt, wxd[a], dm[a]);
+            for (int a = 0; a < 3; ++a) mid[a] = 0.5 * (dm[a] + ds[a]);
+            cross3_fma(w, mid, wxm);
+            for (int a = 0; a < 3; ++a) dm[a] = __fma_rn(dt, wxm[a], dm[a]);
+        }
+        double* d1 = d;
+        double* d2 = d + 3;
+        const double i1 = rsqrt(dot3_fma(d1, d1));
+        for (int a = 0; a < 3; ++a) d1[a] *= i1;
+        const double p = dot3_fma(d2, d1);
+        for (int a = 0; a < 3; ++a) d2[a] = __fma_rn(-p, d1[a], d2[a]);
+        const double i2 = rsqrt(dot3_fma(d2, d2));
+        for (int a = 0; a < 3; ++a) d2[a] *= i2;
+        cross3_fma(d1, d2, d + 6);
     }
-    double* d1 = d;
-    double* d2 = d + 3;
-    const double i1 = rsqrt(dot3_fma(d1, d1));
-    for (int a = 0; a < 3; ++a) d1[a] *= i1;
-    const double p = dot3_fma(d2, d1);
-    for (int a = 0; a < 3; ++a) d2[a] = __fma_rn(-p, d1[a], d2[a]);
-    const double i2 = rsqrt(dot3_fma(d2, d2));
-    for (int a = 0; a < 3; ++a) d2[a] *= i2;
-    cross3_fma(d1, d2, d + 6);
     double disp2 = 0.0;
     for (int a = 0; a < 3; ++a) {
         double e = min_image(A, a, r[a] - A.P.pos_build[(long long)a * A.P.cap + k]);

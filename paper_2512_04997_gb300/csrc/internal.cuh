@@ -185,6 +185,7 @@ struct DemArgs {
     int ell_max_iter;
     double ell_tol;
     int force_f32;  // FP32 contact arithmetic, FP64 sums
+    int quat;       // quaternion orientation update in the predictor
     // pair-once evaluation (simulations with ellipsoids): canonical pair counts, offsets
     // (n + 1), list (i * MAX_CAND_CAP + slot) and results [9][cp_stride]
     int pair_once;

@@ -322,7 +322,7 @@ struct TileCache {
     float R2[MAX_TILE_CAP];       // fl32(R*R) of the subdivision predicate
     double p[3][MAX_TILE_CAP];    // centre (FP64) for the exact subdivision path
     float m[9][MAX_TILE_CAP];     // ellipsoid rows fl32(d_j / semi_j)
-    double acc[6][MAX_TILE_CAP];  // force and torque sums of this tile
+    float acc[6][MAX_TILE_CAP];   // force and torque sums of this tile (FP32: native shared atomics)
     float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
     float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
 };
@@ -378,7 +378,7 @@ __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int cnt, in
             const double smin = fmin(a.semi[k], fmin(a.semi[a.pcap + k], a.semi[2 * a.pcap + k]));
             tc.ims[e] = (float)(1.0 / smin);
         }
-        for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0;
+        for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0f;
     }
 }
 
@@ -625,7 +625,7 @@ __device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float v
             for (int c = 0; c < 6; ++c) v[c] += __shfl_xor_sync(FULL, v[c], off);
         if (lane == 0)
 #pragma unroll
-            for (int c = 0; c < 6; ++c) atomicAdd(&tc.acc[c][kk], (double)v[c]);
+            for (int c = 0; c < 6; ++c) atomicAdd(&tc.acc[c][kk], v[c]);
         pending &= ~__ballot_sync(FULL, mine);
     }
 }
@@ -1040,8 +1040,9 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
         // Down a column a thread rarely meets a second particle within one tile, so it
         // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
-        // FP64 sums only when some lane meets a different particle (and at the end of the
-        // tile); a second solid in a node (rare) is flushed at once.
+        // FP32 sums (native shared atomics; the FP64 shared form cost 2-3% of the kernel)
+        // only when some lane meets a different particle (and at the end of the tile); a
+        // second solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
         {
             const int key0 = t.ns > 0 ? t.e0 : -1;
             float v0[6];
@@ -1072,7 +1073,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
     __syncthreads();
     for (int idx = tid; idx < 6 * cnt; idx += blockDim.x) {
         int e = idx / 6, c = idx % 6;
-        double v = tc.acc[c][e];
+        double v = (double)tc.acc[c][e];
         if (v != 0.0) {
             double* dst = c < 3 ? a.Fh + (long long)c * a.pcap : a.Mh + (long long)(c - 3) * a.pcap;
             atomicAdd(dst + tc_pid(tc, e), v);

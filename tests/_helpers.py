@@ -16,7 +16,8 @@ def oracle_from_workload(O, w, populations=None):
                           young=p["young"], poisson=p["poisson"], restitution=p["restitution"],
                           friction=p["friction"], dem_h=p["dem_h"],
                           ell_max_iter=p["ell_max_iter"], ell_tol=p["ell_tol"],
-                          collision={"bgk": 0, "trt": 1}[p.get("collision", "bgk")])
+                          collision={"bgk": 0, "trt": 1}[p.get("collision", "bgk")],
+                          orient={"triad": 0, "quat": 1}[p.get("orient", "triad")])
     s = O.Sim(w.nx, w.ny, w.nz, periodic=w.periodic, u_wall=w.u_wall, params=op,
               box_lo=w.box_lo, box_hi=w.box_hi, max_particles=max(w.n, 1))
     if w.ncell:

@@ -285,17 +285,17 @@ def test_dem_forces_and_trajectories(oracle, fp32):
     assert np.abs(vo).max() > 1e-3             # the pile is moving
 
 
-@pytest.mark.parametrize("fp32", [0, 1])
-def test_dem_ellipsoids_hertz(oracle, fp32):
+@pytest.mark.parametrize("fp32,orient", [(0, "triad"), (1, "triad"), (0, "quat"), (1, "quat")])
+def test_dem_ellipsoids_hertz(oracle, fp32, orient):
     """Ellipsoid contacts (common-normal iteration, FP64 in both modes) with the Hertz law
-    and walls."""
+    and walls; orientations integrated by the triad update or by the quaternion option."""
     g = W.rng(604)
     n = 500
     box = (30.0, 30.0, 30.0)
     w = W.Workload(name="ell", box_lo=(0, 0, 0), box_hi=box, periodic=(1, 0, 0))
     w.params = W.base_params(law="hertz", young=5.0, poisson=0.3, restitution=0.8, friction=0.3,
                              rho_f=0.0, gravity=(0, 0, -1e-3), dem_h=2 * 1.5 + 0.3, skin=0.3,
-                             force_fp32=fp32)
+                             force_fp32=fp32, orient=orient)
     semi = np.array([1.5, 0.8, 0.6])
     w.shape = np.ones(n, dtype=np.int32)
     w.semi = np.tile(semi, (n, 1))
@@ -319,8 +319,45 @@ def test_dem_ellipsoids_hertz(oracle, fp32):
     ftol = 1e-8 if fp32 == 0 else 1e-5
     assert normwise(Fc_g, Fc_o) < ftol
     assert normwise(Mc_g, Mc_o) < ftol
-    po, vo, _, _ = o.particles()
-    pg, vg, _, _ = s.particles()
+    po, vo, wo, to = o.particles()
+    pg, vg, wg, tg = s.particles()
     assert np.abs(vo).max() < 0.2          # a well-conditioned run
     # FP32 contact arithmetic: 1e-5 of the largest semi-axis (1.5) after 80 steps
     assert np.abs(pg - po).max() < (1e-8 if fp32 == 0 else 1.5e-5)
+    assert np.abs(tg - to).max() < (1e-8 if fp32 == 0 else 1e-4)
+    assert np.abs(wo).max() > 1e-3         # the orientations do change
+
+
+def test_quaternion_free_rotation_exact():
+    """Quaternion orientation option on the GPU, a property that holds at any size: 3000
+    torque-free spheres, far apart, each spinning at its own w from its own orientation,
+    turn by exactly |w| t about w (Rodrigues), to FP64 rounding, after 300 steps."""
+    g = W.rng(613)
+    n = 3000
+    box = (400.0, 400.0, 400.0)
+    w = W.Workload(name="spin", box_lo=(0, 0, 0), box_hi=box, periodic=(1, 1, 1))
+    w.params = W.base_params(rho_f=0.0, dem_h=2.5, skin=0.3, orient="quat", n_sub=2)
+    w.shape = np.zeros(n, dtype=np.int32)
+    w.radius = np.ones(n)
+    w.semi = np.ones((n, 3))
+    w.density = np.ones(n)
+    w.pos = W.rsa_spheres(g, n, np.ones(n), (0, 0, 0), box, (1, 1, 1), gap=1.0)
+    w.vel = np.zeros((n, 3))
+    w.omg = g.normal(0, 0.02, (n, 3))
+    q0 = W.random_quaternions(g, n)
+    w.triad = W.quaternion_to_triad(q0)
+    s = gpu_from_workload(w)
+    T = 300
+    s.step(T)
+    _, _, omg, tri = s.particles()
+    assert np.abs(omg - w.omg).max() < 1e-15   # the gyroscopic term of a sphere vanishes
+    d0 = w.triad.reshape(n, 3, 3)
+    err = 0.0
+    for k in range(n):
+        wk = w.omg[k]
+        ang = np.linalg.norm(wk) * T
+        kx = wk / np.linalg.norm(wk)
+        K = np.array([[0, -kx[2], kx[1]], [kx[2], 0, -kx[0]], [-kx[1], kx[0], 0]])
+        Rw = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+        err = max(err, np.abs(tri[k].reshape(3, 3) - d0[k] @ Rw.T).max())
+    assert err < 1e-12

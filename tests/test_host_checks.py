@@ -23,7 +23,7 @@ BAD_PARAMS = [
     dict(tau=0.5), dict(tau=0.2), dict(tau=float("nan")), dict(storage=3), dict(storage=-1),
     dict(voxel=2), dict(subdiv_n=0), dict(subdiv_n=17), dict(law=2), dict(n_sub=0),
     dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")), dict(collision=2),
-    dict(collision=-1), dict(force_fp32=2),
+    dict(collision=-1), dict(force_fp32=2), dict(orient=2), dict(orient=-1),
 ]
 
 
