@@ -82,7 +82,7 @@ def peaks():
 
 def psm_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm.cu", "internal.cuh"):
+    for f in ("lbm.cu", "psm.cuh", "psm_aa.cu", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2512_04997_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -512,8 +512,10 @@ def main():
         ref.step(args.warmup + args.steps)
         _, u_ref = ref.fields()
         del ref
-        for sto in ("f16", "bf16"):
-            v = ledds.from_workload(w, device=f"cuda:{local}", storage=sto)
+        # AA: one population array stepped in place (half the population memory)
+        for key, sto, pat in (("f16", "f16", "ab"), ("bf16", "bf16", "ab"), ("aa_f32", "f32", "aa"),
+                              ("aa_f16", "f16", "aa")):
+            v = ledds.from_workload(w, device=f"cuda:{local}", storage=sto, pattern=pat)
             v.step(args.warmup)
             torch.cuda.synchronize()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -529,9 +531,11 @@ def main():
             sm_, ps_, _ = v.read_profile()
             pms = sm_[3] / ps_
             ach = N * BYTES_PER_CELL[sto] / (pms * 1e-3) / 1e9
-            variants[sto] = {"value": N * args.steps / (vms * 1e-3) / 1e6, "unit": "MLUPS",
+            variants[key] = {"value": N * args.steps / (vms * 1e-3) / 1e6, "unit": "MLUPS",
+                             "storage": sto, "pattern": pat,
                              "speedup_vs_f32": (N * args.steps / (vms * 1e-3) / 1e6) / value * world,
-                             "field_error_vs_f32": err,
+                             "field_error_vs_f32": err, "psm_ms": pms,
+                             "workspace_gb": v.workspace.numel() / 1e9,
                              "roofline": {"achieved": ach, "frac": ach / hbm, "unit": "GB/s"}}
             del v
             torch.cuda.empty_cache()

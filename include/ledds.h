@@ -48,6 +48,7 @@ enum { LEDDS_VOXEL_DISTANCE = 0, LEDDS_VOXEL_SUBDIV = 1 };
 enum { LEDDS_LAW_LINEAR = 0, LEDDS_LAW_HERTZ = 1 };
 enum { LEDDS_COLLIDE_BGK = 0, LEDDS_COLLIDE_TRT = 1 };
 enum { LEDDS_ORIENT_TRIAD = 0, LEDDS_ORIENT_QUAT = 1 };
+enum { LEDDS_PATTERN_AB = 0, LEDDS_PATTERN_AA = 1 };
 enum { LEDDS_SPHERE = 0, LEDDS_ELLIPSOID = 1 };
 
 /* Sizes fixed at creation. */
@@ -92,6 +93,11 @@ typedef struct {
                              /* LEDDS_ORIENT_QUAT, the exact rotation by |w| dt about w(t)    */
                              /* through a unit quaternion (agrees with the triad update to    */
                              /* O(dt^3) per step; the triad stays the stored orientation)     */
+    int pattern;             /* population arrays: LEDDS_PATTERN_AB, two arrays (pull from   */
+                             /* one, write the other), or LEDDS_PATTERN_AA, one array updated */
+                             /* in place by alternating steps (half the population memory;   */
+                             /* identical results in FP32; not for batch members). Sec. 6     */
+                             /* names single-population schemes as a memory reduction        */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */
@@ -121,7 +127,7 @@ typedef struct ledds_sim_s* ledds_sim_t;
 
 /* Fill *p with defaults: tau 0.8, FP32 storage, distance voxels (subdiv_n 10), linear law,
  * n_sub 1, rho_f 1, no gravity/force, k_n 1000, k_t 2/7 k_n, restitution 0.7, friction
- * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision, triad orientation update. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
+ * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision, triad orientation update, two population arrays. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
 int ledds_params_default(ledds_params* p);
 
 /* Bytes of device workspace a simulation of these dimensions and parameters needs

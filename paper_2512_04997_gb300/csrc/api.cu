@@ -137,6 +137,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->force_fp32 < 0 || p->force_fp32 > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->collision < 0 || p->collision > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->orient < 0 || p->orient > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->pattern < 0 || p->pattern > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -184,7 +185,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
     grid_of(d, p, gn, gh, &G);
     int capc = cap > 0 ? cap : 1;
     void* pop0 = c.take<char>((size_t)N * 19 * sb);
-    void* pop1 = c.take<char>((size_t)N * 19 * sb);
+    // the AA pattern steps in place: one population array
+    void* pop1 = p->pattern == LEDDS_PATTERN_AA ? pop0 : c.take<char>((size_t)N * 19 * sb);
     int* tcount = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1));
     int* tids = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1) * tcap);
     double* st0 = c.take<double>(18 * (size_t)capc);
@@ -311,6 +313,10 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     a.inv_scale = (float)(1.0 / sc);
     a.pop_in = s->pop[in];
     a.pop_out = s->pop[out];
+    // AA: parity 0 holds the pre-collision f (the step from it collides in place), parity 1
+    // the post-collision f*_i in slot opp(i) (the step from it streams); the two pointers
+    // are the same array
+    a.aa = s->p.pattern != LEDDS_PATTERN_AA ? PSM_AB : (in == 0 ? PSM_AA_EVEN : PSM_AA_ODD);
     for (int i = 0; i < 19; ++i) {
         a.pN[i] = (int)(i * s->N);
         a.off[i] = CX(i) + s->d.nx * (CY(i) + s->d.ny * CZ(i));
@@ -548,6 +554,7 @@ int ledds_params_default(ledds_params* p) {
     p->force_fp32 = 1;
     p->collision = LEDDS_COLLIDE_BGK;
     p->orient = LEDDS_ORIENT_TRIAD;
+    p->pattern = LEDDS_PATTERN_AB;
     return LEDDS_OK;
 }
 
@@ -636,7 +643,8 @@ int ledds_set_wall_velocity(ledds_sim_t s, int axis, int side, const double u[3]
     if (s->lattice) {
         // the current pre-collision populations stay as they are
         LbmArgs a = lbm_args(s, s->parity, s->parity, 0);
-        if (launch_rebase(a, s->p.storage, old, s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
+        if (a.aa != PSM_AA_EVEN && launch_rebase(a, s->p.storage, old, s->stream) != cudaSuccess)
+            return LEDDS_ERR_CUDA;
     }
     return LEDDS_OK;
 }
@@ -1015,7 +1023,8 @@ int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     memcpy(&hd, h_buf, sizeof(hd));
     size_t used = layout(nullptr, &s->d, &s->p, nullptr) - 256;
     if (memcmp(hd.magic, "LEDDSCK2", 8) != 0 || hd.ws_used != used || bytes < sizeof(hd) + used ||
-        memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0 || hd.p.storage != s->p.storage)
+        memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0 || hd.p.storage != s->p.storage ||
+        hd.p.pattern != s->p.pattern)
         return LEDDS_ERR_INVALID_ARG;
     if (cudaMemcpyAsync(s->ws, (const char*)h_buf + sizeof(hd), used, cudaMemcpyHostToDevice, s->stream) !=
             cudaSuccess ||
@@ -1065,6 +1074,7 @@ static int batch_layout(int nsim, const ledds_dims* dims, const ledds_params* pa
         if (dims[i].nx <= 0) return LEDDS_ERR_INVALID_ARG;  // every member has a lattice
         if (params[i].storage != params[0].storage) return LEDDS_ERR_INVALID_ARG;
         if (params[i].collision != params[0].collision) return LEDDS_ERR_INVALID_ARG;
+        if (params[i].pattern != LEDDS_PATTERN_AB) return LEDDS_ERR_INVALID_ARG;  // batches use two lattices
         if (dims[i].max_particles > 4096) return LEDDS_ERR_INVALID_ARG;  // direct candidate search
         if (offs) offs->push_back(off);
         off = align256(off + layout(nullptr, &dims[i], &params[i], nullptr));

@@ -117,6 +117,10 @@ struct DevParticles {
     int* shape;
 };
 
+// Population array patterns, which are also the PSM kernel's step forms: the two-lattice
+// pull (AB), and the in-place AA pattern's two alternating steps.
+enum { PSM_AB = 0, PSM_AA_EVEN = 1, PSM_AA_ODD = 2 };
+
 // Offsets of the state buffer components.
 constexpr int SP = 0, SV = 3, SW = 6, ST = 9;
 
@@ -133,7 +137,7 @@ struct LbmArgs {
     float omega_m, guo_pref_m;    // 1/tau- and 1 - 1/(2 tau-)
     float scale, inv_scale;
     const void* pop_in;
-    void* pop_out;
+    void* pop_out;                // the same array as pop_in with the AA pattern
     int pN[19];                   // i * N: start of plane i (19 N < 2^31 is required)
     int off[19];                  // c_x + nx c_y + nx ny c_z: pull offset of direction i
     unsigned off_odd;             // bit i: off[i] is odd (16-bit word selection)
@@ -154,16 +158,22 @@ struct LbmArgs {
     int subdiv_any;               // subdivision fractions requested or some particle an ellipsoid
     float Rc, inv2Rc;
     DevStatus* status;
+    // (last: the PSM kernel is measurably faster with pN at the 16-byte-aligned offset it
+    // has without this field in front of it)
+    int aa;                       // pattern of the array: PSM_AB (two lattices), or one array
+                                  // (AA) holding PSM_AA_EVEN: pre-collision f, natural slots,
+                                  // or PSM_AA_ODD: post-collision f*_i in slot opp(i)
 };
 
 // Arguments of one batched PSM launch: up to BATCH_CHUNK members and the prefix sums of
-// their tile counts (passed by value: 64 x 456 bytes fit the 32 KB parameter limit).
+// their tile counts (passed by value: 64 x 488 bytes fit the 32 KB parameter limit).
 constexpr int BATCH_CHUNK = 64;
 struct BatchChunk {
     LbmArgs a[BATCH_CHUNK];
     int tile_start[BATCH_CHUNK + 1];
     int nsim;
 };
+static_assert(sizeof(BatchChunk) <= 32764, "a batch chunk must fit the kernel parameter space");
 
 struct DemArgs {
     DevParticles P;

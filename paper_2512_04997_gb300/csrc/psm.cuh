@@ -1,0 +1,857 @@
+// psm.cuh -- the fused PSM kernel of one lattice tile (Secs. 2.3-2.4, Table 1
+// "Compute solid fractions", "LBM-PSM collision and streaming", "Force reduction"),
+// shared by the translation units that instantiate it: lbm.cu (two-lattice pull) and
+// psm_aa.cu (the in-place AA pattern).
+#pragma once
+
+#include "internal.cuh"
+
+namespace ledds {
+
+size_t psm_smem_bytes(int store);                                  // lbm.cu
+cudaError_t launch_psm_aa(const LbmArgs& a, int store, cudaStream_t s);  // psm_aa.cu
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Moving-wall correction 6 t_i (c_i . u_w) (rho_w = 1) for a link that crossed walls;
+// with walls on two axes the wall of the higher axis (z, then y, then x) is used. The
+// side of each axis is fixed by the sign of c_i, so every parameter index is constant.
+template <int I>
+__device__ __forceinline__ float wall_term(const float (&uw)[3][2][3], bool wx, bool wy, bool wz) {
+    constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+    constexpr int sx = cx == 1 ? 0 : 1, sy = cy == 1 ? 0 : 1, sz = cz == 1 ? 0 : 1;
+    float u0 = wz ? uw[2][sz][0] : (wy ? uw[1][sy][0] : uw[0][sx][0]);
+    float u1 = wz ? uw[2][sz][1] : (wy ? uw[1][sy][1] : uw[0][sx][1]);
+    float u2 = wz ? uw[2][sz][2] : (wy ? uw[1][sy][2] : uw[0][sx][2]);
+    return 6.0f * TW(I) * ((float)cx * u0 + (float)cy * u1 + (float)cz * u2);
+}
+
+__device__ __forceinline__ float reach_of(const LbmArgs& a, int shape, double R, double Rb) {
+    // distance method: beta > 0 iff |x - r| < R + R_c; subdivision: samples lie within
+    // 0.78 of the node, use the bounding radius plus the cell half-diagonal.
+    if (shape == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) return (float)R + a.Rc + 1e-3f;
+    return (float)Rb + 0.8661f + 1e-3f;
+}
+
+// ------------------------------------------------------------------------------------
+// Per-tile particle cache and solid fractions (Sec. 2.4)
+// ------------------------------------------------------------------------------------
+// Per-tile particle cache. The hot fields are packed in float4 records so one 128-bit
+// shared load (a broadcast: every lane reads the same entry) fetches a whole record.
+struct TileCache {
+    float4 pos[MAX_TILE_CAP];     // centre minus tile origin (FP32, minimum image), radius
+    float4 vel[MAX_TILE_CAP];     // velocity, squared reach of the solid fraction
+    float4 spin[MAX_TILE_CAP];    // angular velocity, particle id (bits)
+    int shape[MAX_TILE_CAP];
+    float R2[MAX_TILE_CAP];       // fl32(R*R) of the subdivision predicate
+    double p[3][MAX_TILE_CAP];    // centre (FP64) for the exact subdivision path
+    float m[9][MAX_TILE_CAP];     // ellipsoid rows fl32(d_j / semi_j)
+    float acc[6][MAX_TILE_CAP];   // force and torque sums of this tile (FP32: native shared atomics)
+    float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
+    float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
+};
+
+__device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
+
+__device__ __forceinline__ double min_image_d(double d, int per, double L) {
+    if (per) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+__device__ __forceinline__ float min_image_f(float d, int per, float L) {
+    if (per) {
+        if (d > 0.5f * L) d -= L;
+        else if (d < -0.5f * L) d += L;
+    }
+    return d;
+}
+
+static __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int cnt, int x0, int y0,
+                          int z0) {
+    if (threadIdx.x < 16) {
+        const int n = a.subdiv_n;
+        tc.so[threadIdx.x] = (int)threadIdx.x < n ? __fdiv_rn((float)(2 * (int)threadIdx.x + 1 - n), (float)(2 * n)) : 0.0f;
+    }
+    const double org[3] = {(double)x0, (double)y0, (double)z0};
+    const double Ls[3] = {(double)a.nx, (double)a.ny, (double)a.nz};
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        int k = a.tile_ids[(long long)tile * a.tile_cap + e];
+        int sh = a.shape[k];
+        tc.shape[e] = sh;
+        float r[3], v[3], w[3];
+        for (int c = 0; c < 3; ++c) {
+            double pc = a.st[(SP + c) * a.pcap + k];
+            tc.p[c][e] = pc;
+            r[c] = (float)min_image_d(pc - org[c], a.per[c], Ls[c]);
+            v[c] = (float)a.st[(SV + c) * a.pcap + k];
+            w[c] = (float)a.st[(SW + c) * a.pcap + k];
+        }
+        double R = sh == LEDDS_SPHERE ? a.radius[k] : a.bound[k];
+        tc.R2[e] = __double2float_rn(R * R);
+        float reach = reach_of(a, sh, a.radius[k], a.bound[k]);
+        tc.pos[e] = make_float4(r[0], r[1], r[2], (float)R);
+        tc.vel[e] = make_float4(v[0], v[1], v[2], reach * reach);
+        tc.spin[e] = make_float4(w[0], w[1], w[2], __int_as_float(k));
+        if (sh == LEDDS_ELLIPSOID) {
+            for (int j = 0; j < 3; ++j)
+                for (int c = 0; c < 3; ++c)
+                    tc.m[3 * j + c][e] = __double2float_rn(
+                        a.st[(ST + 3 * j + c) * a.pcap + k] / a.semi[j * a.pcap + k]);
+            const double smin = fmin(a.semi[k], fmin(a.semi[a.pcap + k], a.semi[2 * a.pcap + k]));
+            tc.ims[e] = (float)(1.0 / smin);
+        }
+        for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0f;
+    }
+}
+
+// Subdivision count (Sec. 2.4): n^3 sample points (2m+1-n)/(2n) around the node, strictly
+// inside the solid, for the node at offset (px, py, pz) from cached particle e. Computed by
+// the whole warp (every lane passes the same arguments): lane l takes the sample columns
+// (j, q) = l, l + 32, ... for every i, and the counts are summed exactly. FP32 with explicit
+// round-to-nearest intrinsics (no contraction) in the evaluation order documented for the
+// method, so the count is exact and independent of the split.
+__device__ __forceinline__ int subdiv_count_warp(const TileCache& tc, int e, float px, float py, float pz,
+                                                 int n) {
+    const int lane = threadIdx.x & 31;
+    const int nn = n * n;
+    int count = 0;
+    if (tc.shape[e] == LEDDS_SPHERE) {
+        const float R2 = tc.R2[e];
+        for (int jq = lane; jq < nn; jq += 32) {
+            const int j = jq / n, q = jq - j * n;
+            const float dy = __fadd_rn(py, tc.so[j]);
+            const float dz = __fadd_rn(pz, tc.so[q]);
+            const float yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+            for (int i = 0; i < n; ++i) {
+                const float dx = __fadd_rn(px, tc.so[i]);
+                count += __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), yy), zz) < R2;
+            }
+        }
+    } else {
+        float mm[9];
+        for (int k = 0; k < 9; ++k) mm[k] = tc.m[k][e];
+        for (int jq = lane; jq < nn; jq += 32) {
+            const int j = jq / n, q = jq - j * n;
+            const float dy = __fadd_rn(py, tc.so[j]);
+            const float dz = __fadd_rn(pz, tc.so[q]);
+            for (int i = 0; i < n; ++i) {
+                const float dx = __fadd_rn(px, tc.so[i]);
+                const float t0 = __fadd_rn(__fmul_rn(mm[0], dx), __fmul_rn(mm[1], dy));
+                const float t1 = __fadd_rn(__fmul_rn(mm[3], dx), __fmul_rn(mm[4], dy));
+                const float t2 = __fadd_rn(__fmul_rn(mm[6], dx), __fmul_rn(mm[7], dy));
+                const float q0 = __fadd_rn(t0, __fmul_rn(mm[2], dz));
+                const float q1 = __fadd_rn(t1, __fmul_rn(mm[5], dz));
+                const float q2 = __fadd_rn(t2, __fmul_rn(mm[8], dz));
+                count += __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2)) < 1.0f;
+            }
+        }
+    }
+    return __reduce_add_sync(0xffffffffu, count);
+}
+
+// Solid fraction of cached particle e at a node, (dx,dy,dz) = node - centre (FP32), where
+// it follows from the distance (Eq. naiveSolidFrac) or from the exact early-outs of the
+// subdivision method; *exact is set when the subdivision count itself is needed.
+__device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& tc, int e, float dx, float dy,
+                                            float dz, float R, bool* exact) {
+    const int sh = tc.shape[e];
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    *exact = false;
+    if (sh == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) {
+        // Eq. (naiveSolidFrac): (R + R_c - d) / (2 R_c), clamped
+        float dsc = R + a.Rc - sqrtf(d2);
+        return fminf(fmaxf(dsc * a.inv2Rc, 0.0f), 1.0f);
+    }
+    const int n = a.subdiv_n;
+    const float h = (float)(n - 1) / (float)(2 * n);  // largest sample offset
+    const float hd = 1.7320508f * h;                  // sample-to-node distance bound
+    // exact early-outs (margins far above FP32 rounding): no sample can be inside ...
+    const float far = R + hd + 1e-3f;
+    if (d2 > far * far) return 0.0f;
+    if (sh == LEDDS_SPHERE) {
+        const float nearr = R - hd - 1e-3f;
+        if (nearr > 0.0f && d2 < nearr * nearr) return 1.0f;  // ... or every sample is
+    } else {
+        // normalised radius |M p| of the node (M rows d_j / semi_j, |M| = 1/min semi-axis):
+        // samples within hd of the node lie within hd |M| of it, so beyond the surface by
+        // more than that (plus margins far above FP32 rounding) none is inside, and inside
+        // by more than that every one is
+        const float q0 = tc.m[0][e] * dx + tc.m[1][e] * dy + tc.m[2][e] * dz;
+        const float q1 = tc.m[3][e] * dx + tc.m[4][e] * dy + tc.m[5][e] * dz;
+        const float q2 = tc.m[6][e] * dx + tc.m[7][e] * dy + tc.m[8][e] * dz;
+        const float rn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
+        const float ext = hd * tc.ims[e] * 1.001f + 1e-3f;
+        if (rn - ext > 1.0f) return 0.0f;
+        if (rn + ext < 1.0f) return 1.0f;
+        // every corner of the sample box strictly inside (convexity) => all samples are
+        bool all_in = true;
+#pragma unroll
+        for (int cnr = 0; cnr < 8; ++cnr) {
+            float px = dx + ((cnr & 1) ? h : -h);
+            float py = dy + ((cnr & 2) ? h : -h);
+            float pz = dz + ((cnr & 4) ? h : -h);
+            float q0 = tc.m[0][e] * px + tc.m[1][e] * py + tc.m[2][e] * pz;
+            float q1 = tc.m[3][e] * px + tc.m[4][e] * py + tc.m[5][e] * pz;
+            float q2 = tc.m[6][e] * px + tc.m[7][e] * py + tc.m[8][e] * pz;
+            all_in = all_in && (q0 * q0 + q1 * q1 + q2 * q2 < 0.999f);
+        }
+        if (all_in) return 1.0f;
+    }
+    *exact = true;
+    return 0.0f;
+}
+
+// Row prefilter: which cached particles can touch the x-row (ly, lz) of this tile.
+__device__ __forceinline__ unsigned long long row_mask(const LbmArgs& a, const TileCache& tc,
+                                                       int cnt, int ly, int lz) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long mask = 0ull;
+    for (int base = 0; base < cnt; base += 32) {
+        int e = base + lane;
+        bool hit = false;
+        if (e < cnt) {
+            const float4 ps = tc.pos[e];
+            float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+            float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+            hit = dy * dy + dz * dz < tc.vel[e].w;
+        }
+        unsigned b = __ballot_sync(FULL, hit);
+        mask |= (unsigned long long)b << base;
+    }
+    return mask;
+}
+
+// Up to two solids per node (Sec. 3.2.3): keep the two largest beta, ties to the lower
+// particle id; `total` counts every solid with beta > 0. Everything stays in registers.
+struct Two {
+    int ns, total;
+    int e0, e1;
+    float b0, b1;
+};
+
+__device__ __forceinline__ bool ranks_before(const TileCache& tc, float b, int e, float bw, int ew) {
+    return b > bw || (b == bw && tc_pid(tc, e) < tc_pid(tc, ew));
+}
+
+// Exact subdivision counts for the lanes in `need`, one node after the other, each counted
+// by the whole warp; the node minus the centre is taken in FP64 (minimum image) and rounded
+// to FP32. Out of line, entered by every lane together: it keeps the hot loop small.
+static __device__ __noinline__ float subdiv_lanes(const LbmArgs& a, const TileCache& tc, int e, unsigned need,
+                                           bool exact, int x, int y, int z, float b) {
+    const int lane = threadIdx.x & 31;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    if (exact) {
+        px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
+        py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
+        pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
+    }
+    const int n = a.subdiv_n;
+    while (need) {
+        const int l = __ffs(need) - 1;
+        need &= need - 1;
+        const float qx = __shfl_sync(0xffffffffu, px, l);
+        const float qy = __shfl_sync(0xffffffffu, py, l);
+        const float qz = __shfl_sync(0xffffffffu, pz, l);
+        const int c = subdiv_count_warp(tc, e, qx, qy, qz, n);
+        if (lane == l) b = (float)c / (float)(n * n * n);
+    }
+    return b;
+}
+
+// Called by the whole warp (the row mask is uniform); lanes with valid false take no part
+// beyond the warp-wide subdivision counts.
+__device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
+                                            unsigned long long mask, int lx, int ly, int lz, int x,
+                                            int y, int z, bool valid, Two& t) {
+    t.ns = 0;
+    t.total = 0;
+    t.e0 = t.e1 = 0;
+    t.b0 = t.b1 = 0.f;
+    while (mask) {
+        const int e = __ffsll((long long)mask) - 1;
+        mask &= mask - 1;
+        const float4 ps = tc.pos[e];
+        float dx = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
+        float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+        float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+        bool exact = false;
+        float b = valid ? beta_quick(a, tc, e, dx, dy, dz, ps.w, &exact) : 0.0f;
+        if (a.subdiv_any) {  // uniform: distance-fraction spheres never need counts
+            const unsigned need = __ballot_sync(0xffffffffu, exact);
+            if (need) b = subdiv_lanes(a, tc, e, need, exact, x, y, z, b);  // uniform branch
+        }
+        if (!(b > 0.0f)) continue;
+        t.total++;
+        if (t.ns == 0) {
+            t.e0 = e; t.b0 = b; t.ns = 1;
+        } else if (ranks_before(tc, b, e, t.b0, t.e0)) {
+            t.e1 = t.e0; t.b1 = t.b0; t.e0 = e; t.b0 = b; t.ns = 2;
+        } else if (t.ns == 1 || ranks_before(tc, b, e, t.b1, t.e1)) {
+            t.e1 = e; t.b1 = b; t.ns = 2;
+        }
+    }
+}
+
+// One solid's data at a node: B_k (Eq. bk), surface velocity u_k = v_k + w_k x (x - r_k),
+// the arm x - r_k, and the running sum of Omega^s_{i,k} c_i.
+struct SolidAt {
+    float B, ux, uy, uz, usq, ax, ay, az, sx, sy, sz;
+};
+
+__device__ __forceinline__ void solid_at(const LbmArgs& a, const TileCache& tc, int e, float b, int lx,
+                                         int ly, int lz, float tau, SolidAt& q) {
+    const float4 ps = tc.pos[e], vs = tc.vel[e], ws = tc.spin[e];
+    q.ax = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
+    q.ay = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
+    q.az = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+    q.B = __fdividef(b * (tau - 0.5f), (1.0f - b) + (tau - 0.5f));
+    q.ux = vs.x + (ws.y * q.az - ws.z * q.ay);
+    q.uy = vs.y + (ws.z * q.ax - ws.x * q.az);
+    q.uz = vs.z + (ws.x * q.ay - ws.y * q.ax);
+    q.usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
+    q.sx = q.sy = q.sz = 0.f;
+}
+
+// Force and torque of one node-solid pair, Eqs. (forceSF), (torqueSF):
+// F = -B sum_i Omega^s_i c_i, M = arm x F. The direction sum has the closed form
+// sum_i Omega^s_i c_i = F_fluid - rho (u - u_k) (momentum exchange: sum_i neq_i c_i =
+// -F_fluid/2 and sum_i (geq_i(rho,u) - geq_i(rho,u_k)) c_i = rho (u - u_k)), so
+// F = B (rho (u - u_k) - F_fluid).
+__device__ __forceinline__ void solid_force(const SolidAt& q, float rho, float dux, float duy, float duz,
+                                            const LbmArgs& a, float v[6]) {
+    const float fx = a.has_force ? a.F[0] : 0.f, fy = a.has_force ? a.F[1] : 0.f;
+    const float fz = a.has_force ? a.F[2] : 0.f;
+    v[0] = q.B * (rho * dux - fx);
+    v[1] = q.B * (rho * duy - fy);
+    v[2] = q.B * (rho * duz - fz);
+    v[3] = q.ay * v[2] - q.az * v[1];
+    v[4] = q.az * v[0] - q.ax * v[2];
+    v[5] = q.ax * v[1] - q.ay * v[0];
+}
+
+// Warp-aggregated addition of per-lane (key, 6 values) into the tile accumulators: one
+// butterfly per distinct key present in the warp (lanes with key < 0 take no part).
+__device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
+    const int lane = threadIdx.x & 31;
+    unsigned pending = __ballot_sync(FULL, key >= 0);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int kk = __shfl_sync(FULL, key, leader);
+        const bool mine = key == kk;
+        float v[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] = mine ? val[c] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) v[c] += __shfl_xor_sync(FULL, v[c], off);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) atomicAdd(&tc.acc[c][kk], v[c]);
+        pending &= ~__ballot_sync(FULL, mine);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Asynchronous pull: each thread copies the 19 values it pulls for a plane straight into
+// its own shared-memory slots (cp.async, 4-byte granules; 16-bit formats copy the aligned
+// word holding the value). Only the issuing thread reads them back, so the pipeline
+// needs no CTA barrier, and two planes of loads stay in flight per thread whatever the
+// occupancy.
+// ------------------------------------------------------------------------------------
+constexpr int PSM_THREADS = TILE_X * TILE_Y;
+
+// Per storage format: resident CTAs per SM the PSM kernel is compiled for (its register
+// budget) and depth of the asynchronous pull pipeline (planes in flight + 1). Chosen by
+// timing the variants on GB300: FP32 runs best with more registers and a deeper
+// pipeline, the 16-bit formats with more resident CTAs.
+template <int STORE>
+struct PsmCfg {
+    static constexpr int minb = 3, stages = 3;
+};
+template <>
+struct PsmCfg<LEDDS_STORE_F32> {
+    static constexpr int minb = 2, stages = 4;
+};
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src, bool pred) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    int n = pred ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Per-plane pull plan of one node: the source of direction I is node - off_I, plus a
+// periodic-wrap correction on an axis where the node sits on the first or last layer; a
+// link that leaves the lattice through a wall (bit of bw: x low/high 1/2, y 4/8, z 16/32)
+// pulls the node's own opposite population instead (halfway bounce-back).
+struct Plan {
+    int cell;
+    unsigned bw;                       // wall faces next to this node
+    int wxm, wxp, wym, wyp, wzm, wzp;  // wrap corrections for c = +1 (m) and c = -1 (p)
+};
+
+__device__ __forceinline__ void make_plan(const LbmArgs& a, int x, int y, int z, Plan& p) {
+    const int nxy = a.nx * a.ny;
+    p.cell = x + a.nx * y + nxy * z;
+    unsigned b = 0;
+    p.wxm = p.wxp = p.wym = p.wyp = p.wzm = p.wzp = 0;
+    if (x == 0) { if (a.per[0]) p.wxm = a.nx; else b |= 1u; }
+    if (x == a.nx - 1) { if (a.per[0]) p.wxp = -a.nx; else b |= 2u; }
+    if (y == 0) { if (a.per[1]) p.wym = nxy; else b |= 4u; }
+    if (y == a.ny - 1) { if (a.per[1]) p.wyp = -nxy; else b |= 8u; }
+    if (z == 0) { if (a.per[2]) p.wzm = (int)a.N; else b |= 16u; }
+    if (z == a.nz - 1) { if (a.per[2]) p.wzp = -(int)a.N; else b |= 32u; }
+    p.bw = b;
+}
+
+// Walls crossed by the link of direction I (the axis flags of wall_term).
+template <int I>
+__device__ __forceinline__ void link_walls(const Plan& p, bool& wx, bool& wy, bool& wz) {
+    constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+    wx = (cx == 1 && (p.bw & 1u)) || (cx == -1 && (p.bw & 2u));
+    wy = (cy == 1 && (p.bw & 4u)) || (cy == -1 && (p.bw & 8u));
+    wz = (cz == 1 && (p.bw & 16u)) || (cz == -1 && (p.bw & 32u));
+}
+
+// Element index of the population f_I(x) a step of form MODE reads; WALLS: some link of
+// the warp may cross a wall (uniform choice of the caller).
+//   PSM_AB:      f*_I(x - c_I) in plane I, or at a wall f*_opp(I)(x) (halfway bounce-back);
+//   PSM_AA_EVEN: f_I(x) itself, in plane I at x (no streaming in this step);
+//   PSM_AA_ODD:  f*_I(x - c_I), kept by the previous step in plane opp(I) at x - c_I, or
+//                at a wall f*_opp(I)(x), kept in plane I at x.
+template <int I, bool WALLS, int MODE>
+__device__ __forceinline__ int src_elem(const LbmArgs& a, const Plan& p) {
+    constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+    if constexpr (MODE == PSM_AA_EVEN) return a.pN[I] + p.cell;
+    constexpr int plane_in = MODE == PSM_AA_ODD ? OPP(I) : I;
+    constexpr int plane_wall = MODE == PSM_AA_ODD ? I : OPP(I);
+    if constexpr (WALLS) {
+        bool wx, wy, wz;
+        link_walls<I>(p, wx, wy, wz);
+        if (wx || wy || wz) return a.pN[plane_wall] + p.cell;
+    }
+    int src = p.cell - a.off[I];
+    if (cx == 1) src += p.wxm;
+    if (cx == -1) src += p.wxp;
+    if (cy == 1) src += p.wym;
+    if (cy == -1) src += p.wyp;
+    if (cz == 1) src += p.wzm;
+    if (cz == -1) src += p.wzp;
+    return a.pN[plane_in] + src;
+}
+
+template <class SS, int I, bool WALLS, int MODE>
+struct IssueAll {
+    static __device__ __forceinline__ void run(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
+                                               uint32_t* slot) {
+        uintptr_t q = reinterpret_cast<uintptr_t>(pin + src_elem<I, WALLS, MODE>(a, p));
+        if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
+        cp_async4(slot + I * PSM_THREADS, reinterpret_cast<const void*>(q), true);
+        IssueAll<SS, I + 1, WALLS, MODE>::run(a, pin, p, slot);
+    }
+};
+template <class SS, bool WALLS, int MODE>
+struct IssueAll<SS, 19, WALLS, MODE> {
+    static __device__ __forceinline__ void run(const LbmArgs&, const typename SS::T*, const Plan&, uint32_t*) {}
+};
+
+// Issue the 19 reads of node (x,y,z) into its shared-memory slots (nothing if !pred). Every
+// lane of the warp calls it; warps without a wall link take the plain addressing.
+template <class SS, int MODE>
+__device__ __forceinline__ void issue_node(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
+                                           bool pred, uint32_t* slot) {
+    Plan p;
+    make_plan(a, x, y, z, p);
+    if (MODE != PSM_AA_EVEN && __any_sync(FULL, pred && p.bw != 0u)) {
+        if (pred) IssueAll<SS, 0, true, MODE>::run(a, pin, p, slot);
+    } else if (pred) {
+        IssueAll<SS, 0, false, MODE>::run(a, pin, p, slot);
+    }
+}
+
+template <class SS>
+__device__ __forceinline__ float decode(uint32_t w, int odd, float inv) {
+    if (sizeof(typename SS::T) == 4) return __uint_as_float(w);
+    return SS::from_bits(odd ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), inv);
+}
+
+template <class SS, int I, bool WALLS, int MODE>
+struct ReadAll {
+    static __device__ __forceinline__ void run(const LbmArgs& a, const Plan& p, const uint32_t* slot, float* g) {
+        const uint32_t w = slot[I * PSM_THREADS];
+        bool wx = false, wy = false, wz = false;
+        if constexpr (WALLS) link_walls<I>(p, wx, wy, wz);
+        const bool wl = wx || wy || wz;
+        // 16-bit storage: which half of the copied word holds the value. With nx even every
+        // plane start, offset and wrap correction except c_x is even, so the parity is that
+        // of x - c_x (of x itself for a bounced link or an in-place read).
+        int odd = 0;
+        if (sizeof(typename SS::T) == 2) {
+            const int shift = (wl || MODE == PSM_AA_EVEN) ? 0 : CX(I);
+            odd = a.nx_even ? ((p.cell ^ shift) & 1) : (src_elem<I, WALLS, MODE>(a, p) & 1);
+        }
+        float v = decode<SS>(w, odd, a.inv_scale);
+        if constexpr (WALLS) {
+            if (wl) v += wall_term<I>(a.uw, wx, wy, wz);  // moving-wall bounce-back
+        }
+        g[I] = v;
+        ReadAll<SS, I + 1, WALLS, MODE>::run(a, p, slot, g);
+    }
+};
+template <class SS, bool WALLS, int MODE>
+struct ReadAll<SS, 19, WALLS, MODE> {
+    static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const uint32_t*, float*) {}
+};
+
+// c . v for a lattice vector c with components in {-1, 0, 1} known at compile time (no
+// multiplications by 0 or +/-1 left to run time), and c^T Q c for a symmetric Q.
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cdot(float x, float y, float z) {
+    float r = 0.0f;
+    if constexpr (CXv != 0) r = CXv > 0 ? x : -x;
+    if constexpr (CYv != 0) r = CXv != 0 ? (CYv > 0 ? r + y : r - y) : (CYv > 0 ? y : -y);
+    if constexpr (CZv != 0) r = (CXv != 0 || CYv != 0) ? (CZv > 0 ? r + z : r - z) : (CZv > 0 ? z : -z);
+    return r;
+}
+
+// Solid terms of one node summed over its (at most two) solids k, with d_k = u - u_k:
+//   Bs = sum B_k, D = sum B_k d_k, Q = sum B_k d_k d_k^T, S = sum B_k (u^2 - u_k^2).
+// With e_k = c.d_k, sum_k B_k Omega^s_{i,k} needs only c.D and c^T Q c:
+//   sum_k B_k (geq_i(rho,u) - geq_i(rho,u_k)) = t rho (3 c.D + 9 (c.u)(c.D) - 4.5 c^T Q c - 1.5 S)
+// (from (c.u)^2 - (c.u_k)^2 = 2 (c.u) e_k - e_k^2), the antisymmetric part being 3 t rho c.D.
+struct SolidSums {
+    float Bs, Dx, Dy, Dz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, S;
+};
+
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cqc(const SolidSums& m) {
+    float r = 0.0f;
+    if constexpr (CXv != 0) r += m.Qxx;
+    if constexpr (CYv != 0) r += m.Qyy;
+    if constexpr (CZv != 0) r += m.Qzz;
+    if constexpr (CXv != 0 && CYv != 0) r += (CXv * CYv > 0 ? 2.0f : -2.0f) * m.Qxy;
+    if constexpr (CXv != 0 && CZv != 0) r += (CXv * CZv > 0 ? 2.0f : -2.0f) * m.Qxz;
+    if constexpr (CYv != 0 && CZv != 0) r += (CYv * CZv > 0 ? 2.0f : -2.0f) * m.Qyz;
+    return r;
+}
+
+// Store of the post-collision f*_I(x) by a step of form MODE (WALLS as for src_elem):
+//   PSM_AB:      plane I at x of the other array;
+//   PSM_AA_EVEN: plane opp(I) at x, in place (the next step streams it);
+//   PSM_AA_ODD:  pushed to plane I at x + c_I, where the next step reads it in place, or,
+//                for a link into a wall, returned to x as f_opp(I) in plane opp(I) with
+//                the moving-wall term of that direction (halfway bounce-back).
+// `node` points at the node's element of plane 0.
+template <class SS, int I, int MODE, bool WALLS>
+__device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS::T* node, float v) {
+    if constexpr (MODE == PSM_AB) {
+        SS::store(node + a.pN[I], v, a.scale);
+    } else if constexpr (MODE == PSM_AA_EVEN) {
+        SS::store(node + a.pN[OPP(I)], v, a.scale);
+    } else {
+        constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+        if constexpr (WALLS) {
+            bool wx, wy, wz;
+            link_walls<OPP(I)>(p, wx, wy, wz);
+            if (wx || wy || wz) {
+                SS::store(node + a.pN[OPP(I)], v + wall_term<OPP(I)>(a.uw, wx, wy, wz), a.scale);
+                return;
+            }
+        }
+        int d = a.pN[I] + a.off[I];
+        if (cx == 1) d += p.wxp;
+        if (cx == -1) d += p.wxm;
+        if (cy == 1) d += p.wyp;
+        if (cy == -1) d += p.wym;
+        if (cz == 1) d += p.wzp;
+        if (cz == -1) d += p.wzm;
+        SS::store(node + d, v, a.scale);
+    }
+}
+
+// Collision and store of the direction pair (I, I+1) (c_{I+1} = -c_I). On entry g holds
+// the pulled populations of the pair; the symmetric and antisymmetric parts of the
+// equilibrium and of the solid terms are shared by the two directions:
+//   geq_{I,I+1} = t (base + 4.5 rho cu^2 +/- 3 rho cu)
+//   sum_k B_k Omega^s_I     = Bs (neq_{I+1} - neq_I) - (dsym + dasym)
+//   sum_k B_k Omega^s_{I+1} = Bs (neq_I - neq_{I+1}) - (dsym - dasym)
+// with dsym = t rho (9 cu c.D - 4.5 c^T Q c - 1.5 S), dasym = 3 t rho c.D (SolidSums).
+// SOLID is uniform across the warp: false when no lane of the warp has a solid.
+// The force sum over the directions is not accumulated here: see solid_force.
+template <class SS, int I, bool SOLID, bool TRT, int MODE, bool WALLS>
+struct CollidePairs {
+    static __device__ __forceinline__ void run(float* g, float rho, float ux, float uy, float uz, float base,
+                                               const LbmArgs& a, float Fu, float force_w, float keep,
+                                               float kB, float force_wa, const SolidSums& m,
+                                               typename SS::T* node, const Plan& p, bool valid) {
+        constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
+        constexpr float t = TW(I);
+        const float cu = cdot<cx, cy, cz>(ux, uy, uz);
+        const float cu2 = cu * cu;
+        const float sym = base + 4.5f * rho * cu2;
+        const float asym = 3.0f * rho * cu;
+        const float n0 = g[I] - t * (sym + asym);       // neq_I
+        const float n1 = g[I + 1] - t * (sym - asym);   // neq_{I+1}
+        float o0 = t * (sym + asym) + keep * n0;
+        float o1 = t * (sym - asym) + keep * n1;
+        if constexpr (TRT) {  // the odd part of neq relaxes at the second rate
+            o0 += kB * n1;
+            o1 += kB * n0;
+        }
+        if (a.has_force) {
+            const float cF = cdot<cx, cy, cz>(a.F[0], a.F[1], a.F[2]);
+            // Guo term t [3 (c.F - u.F) + 9 (c.u)(c.F)]: c -> -c flips only 3 c.F
+            const float fs = force_w * t * (-3.0f * Fu + 9.0f * cu * cF);
+            const float fa = (TRT ? force_wa : force_w) * t * 3.0f * cF;
+            o0 += fs + fa;
+            o1 += fs - fa;
+        }
+        if constexpr (SOLID) {
+            const float cD = cdot<cx, cy, cz>(m.Dx, m.Dy, m.Dz);
+            const float trho = t * rho;
+            const float dsym = trho * (9.0f * cu * cD - 4.5f * cqc<cx, cy, cz>(m) - 1.5f * m.S);
+            const float dasym = 3.0f * trho * cD;
+            const float x = m.Bs * (n1 - n0);
+            o0 += x - (dsym + dasym);
+            o1 += -x - (dsym - dasym);
+        }
+        if (valid) {
+            put<SS, I, MODE, WALLS>(a, p, node, o0);
+            put<SS, I + 1, MODE, WALLS>(a, p, node, o1);
+        }
+        CollidePairs<SS, I + 2, SOLID, TRT, MODE, WALLS>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
+                                                              force_wa, m, node, p, valid);
+    }
+};
+template <class SS, bool SOLID, bool TRT, int MODE, bool WALLS>
+struct CollidePairs<SS, 19, SOLID, TRT, MODE, WALLS> {
+    static __device__ __forceinline__ void run(float*, float, float, float, float, float, const LbmArgs&, float,
+                                               float, float, float, float, const SolidSums&, typename SS::T*,
+                                               const Plan&, bool) {}
+};
+
+// ------------------------------------------------------------------------------------
+// The fused PSM step: pull, moments, solid fractions, PSM collision (Eqs. psm1, lbePS,
+// bk, btot), store, and the hydrodynamic force/torque of each solid (Eqs. forceSF,
+// torqueSF) reduced warp -> tile (shared FP32) -> particle (global FP64 atomics).
+// The collision is written around the non-equilibrium parts neq_i = g_i - geq_i:
+//   f*_i = geq_i + (1 - (1-B_tot)/tau) neq_i + sum_k B_k Omega^s_{i,k},
+//   Omega^s_{i,k} = neq_ibar - neq_i - (geq_i(rho,u) - geq_i(rho,u_k)).
+// ------------------------------------------------------------------------------------
+// One 32x8xTILE_Z tile (bx, by, bz) of the lattice described by `a`; psm_smem holds the
+// tile cache followed by the pipeline stages (psm_smem_bytes()).
+template <int STORE, bool TRT, int MODE>
+__device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, int zlo, int zhi,
+                                         unsigned char* psm_smem) {
+    using SS = Store<STORE>;
+    using T = typename SS::T;
+    constexpr int PSM_STAGES = PsmCfg<STORE>::stages;
+    const T* pin = (const T*)a.pop_in;
+    T* pout = (T*)a.pop_out;
+    TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(psm_smem + ((sizeof(TileCache) + 15) & ~(size_t)15));
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int tile = (bz * a.nty + by) * a.ntx + bx;
+    const int x = x0 + lane, y = y0 + warp;
+    const bool valid_xy = x < a.nx && y < a.ny;
+
+    // prologue: the first planes (of this CTA's planes zlo .. zhi-1 of the tile) in flight
+    // while the tile's particles are cached
+#pragma unroll
+    for (int q = 0; q < PSM_STAGES - 1; ++q) {
+        const int z = z0 + zlo + q;
+        issue_node<SS, MODE>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
+                       stage + (q * 19) * PSM_THREADS + tid);
+        cp_async_commit();
+    }
+    const int cnt = min(a.tile_count[tile], a.tile_cap);
+    load_tile(a, tc, tile, cnt, x0, y0, z0);
+    __syncthreads();
+
+    const float tau = a.tau, omega = a.omega;
+    int hkey = -1;                                   // solid held in the running sum
+    float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // its force and torque so far
+    for (int iz = zlo; iz < zhi; ++iz) {
+        const int r = iz - zlo;  // position in the pipeline ring
+        {   // keep PSM_STAGES - 1 planes ahead in flight
+            const int q = r + PSM_STAGES - 1;
+            const int z = z0 + zlo + q;
+            issue_node<SS, MODE>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
+                           stage + ((q % PSM_STAGES) * 19) * PSM_THREADS + tid);
+            cp_async_commit();
+        }
+        cp_async_wait<PSM_STAGES - 1>();
+        const int z = z0 + iz;
+        if (y >= a.ny || z >= a.nz) continue;  // uniform across the warp
+        const bool valid = x < a.nx;
+        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
+
+        float g[19];
+        Plan pl;
+        make_plan(a, valid ? x : 0, y, z, pl);
+        const uint32_t* slot = stage + ((r % PSM_STAGES) * 19) * PSM_THREADS + tid;
+        // some lane of the warp has a wall link (never needed by the in-place step)
+        const bool wwarp = MODE != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
+        if (wwarp) {
+            if (valid) ReadAll<SS, 0, true, MODE>::run(a, pl, slot, g);
+        } else if (valid) {
+            ReadAll<SS, 0, false, MODE>::run(a, pl, slot, g);
+        }
+        if (!valid) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) g[i] = 0.f;
+        }
+        Two t;
+        t.ns = 0;
+        t.total = 0;
+        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+        if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
+
+        // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
+        const float drho = ((g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
+                           (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14]))) +
+                           ((g[15] + g[16]) + (g[17] + g[18]));
+        float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
+        float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
+        float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
+        const float rho = 1.0f + drho;
+        if (a.has_force) {
+            jx += 0.5f * a.F[0];
+            jy += 0.5f * a.F[1];
+            jz += 0.5f * a.F[2];
+        }
+        const float inv_rho = 1.0f / rho;
+        const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+        const float usq = ux * ux + uy * uy + uz * uz;
+        const float base = drho - rho * 1.5f * usq;
+
+        const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
+        // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
+        g[0] -= TW(0) * base;
+        // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
+        // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
+        if (!__any_sync(FULL, t.ns > 0)) {
+            // no lane of the warp meets a solid at this node (uniform): plain BGK/TRT, and
+            // nothing to add to the held force sums
+            const float keep = TRT ? 1.0f - 0.5f * (omega + a.omega_m) : 1.0f - omega;
+            const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
+            SolidSums m;
+            m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
+            if (MODE == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
+                CollidePairs<SS, 1, false, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
+                                                                 kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
+            else
+                CollidePairs<SS, 1, false, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
+                                                                  kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
+            float out0 = TW(0) * base + (1.0f - omega) * g[0];
+            if (a.has_force) out0 += a.guo_pref * TW(0) * (-3.0f * Fu);
+            if (valid) SS::store(pout + pl.cell, out0, a.scale);
+            continue;
+        }
+        // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
+        SolidAt q0, q1;
+        q0.B = q1.B = 0.f;
+        q0.ux = q0.uy = q0.uz = q0.usq = q0.ax = q0.ay = q0.az = 0.f;
+        q1.ux = q1.uy = q1.uz = q1.usq = q1.ax = q1.ay = q1.az = 0.f;
+        q0.sx = q0.sy = q0.sz = q1.sx = q1.sy = q1.sz = 0.f;
+        if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
+        if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
+        const float Btot = fminf(q0.B + q1.B, 1.0f);
+        const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
+        const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
+        const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
+        const float force_w = (1.0f - Btot) * a.guo_pref;
+        const float force_wa = (1.0f - Btot) * a.guo_pref_m;
+        // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
+        const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
+        const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
+        SolidSums m;
+        {
+            const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
+            const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
+            m.Bs = q0.B + q1.B;
+            m.Dx = b0x + b1x;
+            m.Dy = b0y + b1y;
+            m.Dz = b0z + b1z;
+            m.Qxx = b0x * d0x + b1x * d1x;
+            m.Qyy = b0y * d0y + b1y * d1y;
+            m.Qzz = b0z * d0z + b1z * d1z;
+            m.Qxy = b0x * d0y + b1x * d1y;
+            m.Qxz = b0x * d0z + b1x * d1z;
+            m.Qyz = b0y * d0z + b1y * d1z;
+            m.S = q0.B * d0s + q1.B * d1s;
+        }
+        if (MODE == PSM_AA_ODD && wwarp)
+            CollidePairs<SS, 1, true, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
+                                                            force_wa, m, pout + pl.cell, pl, valid);
+        else
+            CollidePairs<SS, 1, true, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
+                                                             force_wa, m, pout + pl.cell, pl, valid);
+        {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
+            float out0 = TW(0) * base + keep0 * g[0];
+            if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
+            out0 += 1.5f * TW(0) * rho * m.S;
+            if (valid) SS::store(pout + pl.cell, out0, a.scale);
+        }
+
+        // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
+        // Down a column a thread rarely meets a second particle within one tile, so it
+        // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
+        // FP32 sums (native shared atomics; the FP64 shared form cost 2-3% of the kernel)
+        // only when some lane meets a different particle (and at the end of the tile); a
+        // second solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
+        {
+            const int key0 = t.ns > 0 ? t.e0 : -1;
+            float v0[6];
+            solid_force(q0, rho, d0x, d0y, d0z, a, v0);
+            // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
+            // held sum (the lane may meet the same particle again further down)
+            const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
+            if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
+            if (change) {
+                hkey = -1;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
+            }
+            if (key0 >= 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) hacc[c] += v0[c];
+                hkey = key0;
+            }
+            if (__any_sync(FULL, t.ns > 1)) {
+                float v1[6];
+                solid_force(q1, rho, d1x, d1y, d1z, a, v1);
+                warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
+            }
+        }
+    }
+    warp_flush(tc, hkey, hacc);
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int idx = tid; idx < 6 * cnt; idx += blockDim.x) {
+        int e = idx / 6, c = idx % 6;
+        double v = (double)tc.acc[c][e];
+        if (v != 0.0) {
+            double* dst = c < 3 ? a.Fh + (long long)c * a.pcap : a.Mh + (long long)(c - 3) * a.pcap;
+            atomicAdd(dst + tc_pid(tc, e), v);
+        }
+    }
+}
+
+template <int STORE, bool TRT, int MODE>
+__global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const LbmArgs a) {
+    extern __shared__ __align__(16) unsigned char psm_smem[];
+    // small lattices: a.zsplit CTAs share a tile, each taking TILE_Z / zsplit of its planes
+    const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
+    psm_tile<STORE, TRT, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per, part * per + per,
+                               psm_smem);
+}
+
+}  // namespace ledds

@@ -23,6 +23,7 @@ VOXEL = {"distance": 0, "subdiv": 1}
 LAW = {"linear": 0, "hertz": 1}
 COLLIDE = {"bgk": 0, "trt": 1}
 ORIENT = {"triad": 0, "quat": 1}
+PATTERN = {"ab": 0, "aa": 1}
 SPHERE, ELLIPSOID = 0, 1
 
 
@@ -41,7 +42,8 @@ class ledds_params(C.Structure):
                 ("young", C.c_double), ("poisson", C.c_double), ("restitution", C.c_double),
                 ("friction", C.c_double), ("skin", C.c_double), ("dem_h", C.c_double),
                 ("ell_max_iter", C.c_int), ("ell_tol", C.c_double),
-                ("force_fp32", C.c_int), ("collision", C.c_int), ("orient", C.c_int)]
+                ("force_fp32", C.c_int), ("collision", C.c_int), ("orient", C.c_int),
+                ("pattern", C.c_int)]
 
 
 class ledds_particle(C.Structure):
@@ -149,6 +151,8 @@ def make_params(**kw) -> ledds_params:
             v = COLLIDE[v] if isinstance(v, str) else v
         elif k == "orient":
             v = ORIENT[v] if isinstance(v, str) else v
+        elif k == "pattern":
+            v = PATTERN[v] if isinstance(v, str) else v
         if k in ("fluid_force", "gravity"):
             getattr(p, k)[:] = [float(x) for x in v]
         else:

@@ -162,7 +162,7 @@ def base_params(**kw) -> dict:
              subdiv_n=10, law="linear", n_sub=1, rho_f=1.0, gravity=(0.0, 0.0, 0.0),
              k_n=1000.0, k_t=1000.0 * 2.0 / 7.0, young=1.0e4, poisson=0.3, restitution=0.7,
              friction=0.4, skin=0.5, dem_h=0.0, ell_max_iter=60, ell_tol=1e-6,
-             force_fp32=1, collision="bgk", orient="triad")
+             force_fp32=1, collision="bgk", orient="triad", pattern="ab")
     p.update(kw)
     return p
 

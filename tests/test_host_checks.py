@@ -23,7 +23,8 @@ BAD_PARAMS = [
     dict(tau=0.5), dict(tau=0.2), dict(tau=float("nan")), dict(storage=3), dict(storage=-1),
     dict(voxel=2), dict(subdiv_n=0), dict(subdiv_n=17), dict(law=2), dict(n_sub=0),
     dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")), dict(collision=2),
-    dict(collision=-1), dict(force_fp32=2), dict(orient=2), dict(orient=-1),
+    dict(collision=-1), dict(force_fp32=2), dict(orient=2), dict(orient=-1), dict(pattern=2),
+    dict(pattern=-1),
 ]
 
 
@@ -62,6 +63,8 @@ def test_workspace_grows_with_the_problem(L):
     assert rc == rc2 == rc3 == 0
     assert b - a >= 2 * 19 * 32 ** 3 * 4      # two FP32 population buffers of the extra cells
     assert a - c >= 2 * 19 * 32 ** 3 * 2      # FP16 storage halves the population bytes
+    rc4, e = _size(L, ledds.make_dims(32, 32, 32, max_particles=10), ledds.make_params(dem_h=2.5, pattern="aa"))
+    assert rc4 == 0 and a - e >= 19 * 32 ** 3 * 4   # the AA pattern keeps one population array
 
 
 def _batch_size(L, dims, params):
@@ -88,6 +91,8 @@ def test_batch_workspace_rules(L):
     trt = ledds.make_params(dem_h=8.0, storage=1, collision="trt")
     assert _batch_size(L, [d1, d2], [p16, trt])[0] == ERR_INVALID            # mixed collision
     assert _batch_size(L, [d1, d2], [trt, trt])[0] == 0
+    aa = ledds.make_params(dem_h=8.0, storage=1, pattern="aa")
+    assert _batch_size(L, [d1, d2], [aa, aa])[0] == ERR_INVALID              # members use two lattices
     no_lattice = ledds.make_dims(0, 0, 0, max_particles=8, box_lo=(0, 0, 0), box_hi=(20, 20, 20))
     assert _batch_size(L, [d1, no_lattice], [p16, p16])[0] == ERR_INVALID    # member without a lattice
     big = ledds.make_dims(32, 32, 32, max_particles=4097)
