@@ -25,8 +25,13 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _lattice(periodic, walls, **kw):
-    nx, ny, nz = 37, 19, 11     # ragged tiles in x, y and z
+# 37 x 19 x 11: ragged tiles in x, y and z, odd nx (16-bit values share words across
+# rows); 104 x 19 x 11: even nx, three full x-tiles and a ragged one.
+SIZES = [(37, 19, 11), (104, 19, 11)]
+
+
+def _lattice(periodic, walls, size=(37, 19, 11), **kw):
+    nx, ny, nz = size
     w = W.Workload(name="lattice", nx=nx, ny=ny, nz=nz, periodic=periodic)
     w.params = W.base_params(tau=0.7, **kw)
     if walls == "z":
@@ -43,15 +48,16 @@ def _np(t):
     return t.cpu().numpy()
 
 
+@pytest.mark.parametrize("size", SIZES)
 @pytest.mark.parametrize("collision", ["bgk", "trt"])
 @pytest.mark.parametrize("periodic,walls", [((1, 1, 1), None), ((0, 0, 0), "resting"), ((1, 1, 0), "z"),
                                             ((0, 0, 0), "all")])
-def test_aa_lattice_matches_ab_and_oracle(oracle, periodic, walls, collision):
+def test_aa_lattice_matches_ab_and_oracle(oracle, periodic, walls, collision, size):
     """Lattice only (forced, off-equilibrium start): bit-exact without moving walls (periodic
     box; resting walls on every face); with moving walls the patterns start one rounding
     apart at the wall links and stay within a few units in the last place."""
     g = W.rng(510)
-    w = _lattice(periodic, walls, collision=collision, fluid_force=(2e-6, -1e-6, 0.0))
+    w = _lattice(periodic, walls, size, collision=collision, fluid_force=(2e-6, -1e-6, 0.0))
     f0 = random_populations(oracle, g, w.nx, w.ny, w.nz)
     o = oracle_from_workload(oracle, w, populations=f0)
     ab = gpu_from_workload(w, populations=f0)
@@ -80,13 +86,14 @@ def test_aa_lattice_matches_ab_and_oracle(oracle, periodic, walls, collision):
     assert normwise(_np(u_aa), u_o) < FP32_TOL
 
 
+@pytest.mark.parametrize("size", SIZES)
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
-def test_aa_16bit_storage(oracle, storage):
+def test_aa_16bit_storage(oracle, storage, size):
     """16-bit storage: bit-exact without walls; with walls the AA pattern rounds f* plus the
     wall term where the pull rounds f* alone, a difference of one rounding of the format."""
     g = W.rng(511)
     for periodic, walls, tol in (((1, 1, 1), None, 0.0), ((0, 0, 0), "all", 2e-3 if storage == "bf16" else 2e-4)):
-        w = _lattice(periodic, walls, storage=storage)
+        w = _lattice(periodic, walls, size, storage=storage)
         f0 = random_populations(oracle, g, w.nx, w.ny, w.nz)
         ab = gpu_from_workload(w, populations=f0)
         aa = gpu_from_workload(w, populations=f0, pattern="aa")
@@ -98,7 +105,7 @@ def test_aa_16bit_storage(oracle, storage):
 
 
 def _coupled(seed=520):
-    w = W.couette_suspension(nx=64, ny=48, nz=40, n_particles=40, radius=4.0, seed_index=seed)
+    w = W.couette_suspension(nx=104, ny=48, nz=40, n_particles=64, radius=4.0, seed_index=seed)
     return w
 
 
