@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--pattern", default="ab", choices=["ab", "aa"],
+                    help="population arrays of the main line: two (ab) or one in place (aa)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true",
@@ -87,16 +89,17 @@ def psm_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_per_cell(storage):
+def traffic_per_cell(storage, pattern="ab"):
     """DRAM bytes per cell update of the PSM kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+    was taken on the current kernel source; else None (AA pattern: key "<storage>_aa",
+    the mean of its two step forms)."""
     path = os.path.join(ROOT, "profiles", "psm_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("source_hash") != psm_source_hash():
         return None
-    v = d.get("bytes_per_cell", {}).get(storage)
+    v = d.get("bytes_per_cell", {}).get(storage if pattern == "ab" else storage + "_aa")
     return float(v) if v is not None else None
 
 
@@ -391,13 +394,16 @@ def main_workload(args):
     """The Couette suspension the main line is measured on (edge E, spheres scaled with E^3)."""
     from paper_2512_04997_gb300 import workloads as W
     E = args.edge
-    return W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
-                                storage=args.storage)
+    w = W.couette_suspension(nx=E, ny=E, nz=E, n_particles=int(round(4000 * (E / 256) ** 3)),
+                             storage=args.storage)
+    w.params["pattern"] = args.pattern
+    return w
 
 
 def main_config(w, storage, world):
     N = w.ncell
     return {"workload": w.name, "cells": N, "particles": w.n, "storage": storage,
+            "pattern": w.params.get("pattern", "ab"),
             "n_sub": w.params["n_sub"], "tau": w.params["tau"], "voxel": w.params["voxel"],
             "l2": f"inputs larger than L2 (populations 2 x 19 x {N / 1e6:.1f}M values)",
             "parallelism": f"replicas x{world}"}
@@ -479,7 +485,7 @@ def main():
     psm_ms = stage_ms[3] / psteps
     bpc = BYTES_PER_CELL[args.storage]
     achieved = N * bpc / (psm_ms * 1e-3) / 1e9
-    tpc = traffic_per_cell(args.storage)
+    tpc = traffic_per_cell(args.storage, args.pattern)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": (tpc * N if tpc is not None else None),
                 "kernel": "k_psm (fused PSM collide-stream, solid fractions, force reduction)",

@@ -560,6 +560,8 @@ static double Bk_of(double beta, double tau) {
     return beta * (tau - 0.5) / ((1.0 - beta) + (tau - 0.5));
 }
 
+double or_bk(double beta, double tau) { return Bk_of(beta, tau); }
+
 /* ------------------------------------------------------------------------------------ */
 /* PSM fluid update: Table 1 "PSM fluid-particle coupling" and "Force reduction" rows.   */
 /* Solid fractions at the current particle positions, collision of every cell, then     */

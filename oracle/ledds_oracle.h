@@ -81,6 +81,8 @@ void or_get_accel(const or_sim* s, double* acc, double* alpha);
 /* Unit quaternion (w, x, y, z) of the body-to-world rotation whose columns are the
  * triad d1, d2, d3 (Shepperd's method); and the triad of a unit quaternion. */
 void or_quat_from_triad(const double triad[9], double q[4]);
+/* Solid weight B_k of a solid fraction beta, Eq. (bk). */
+double or_bk(double beta, double tau);
 void or_triad_from_quat(const double q[4], double triad[9]);
 
 /* One coupled (or DEM-only) time step, flowchart order of Sec. 3.2. */

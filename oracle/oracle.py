@@ -69,6 +69,8 @@ def lib():
         L.or_get_forces.argtypes = [C.c_void_p, dp, dp, dp, dp]
         L.or_get_accel.argtypes = [C.c_void_p, dp, dp]
         L.or_quat_from_triad.argtypes = [dp, dp]
+        L.or_bk.restype = C.c_double
+        L.or_bk.argtypes = [C.c_double, C.c_double]
         L.or_triad_from_quat.argtypes = [dp, dp]
         L.or_step.argtypes = [C.c_void_p, C.c_int]
         L.or_voxelize.argtypes = [C.c_void_p, dp, ip, ip]
@@ -260,6 +262,11 @@ def subdiv_count(rel, shape, radius, semi=(1, 1, 1), triad=None, n=10):
 
 def beta_distance(rel, radius):
     return lib().or_beta_distance(_d(rel, 3), float(radius))
+
+
+def bk(beta, tau):
+    """Solid weight B_k of solid fraction beta, Eq. (bk)."""
+    return lib().or_bk(float(beta), float(tau))
 
 
 def quat_from_triad(triad):

@@ -113,8 +113,9 @@ def test_aa_coupled_matches_ab_and_oracle(oracle):
     """Particles in a sheared box between moving walls: the patterns start one rounding apart
     at the wall links and the force sums use atomics (order-dependent rounding), so they
     agree to rounding: fields 1e-6; the hydrodynamic forces, sums over a particle's surface
-    nodes with strong cancellation, 1e-4 of the largest force (the oracle parity tolerance
-    of the coupled tests), and through them velocities 1e-5 and positions 1e-7 (measured
+    nodes with strong cancellation, within twice the oracle parity tolerance of the coupled
+    tests (each pattern is within 1e-4 of the oracle, so the two within 2e-4; measured
+    1.05e-4 on this machine), and through them velocities 1e-5 and positions 1e-7 (measured
     3e-9 after 11 steps). Both against the oracle at the parity tolerances."""
     w = _coupled()
     o = oracle_from_workload(oracle, w)
@@ -133,7 +134,7 @@ def test_aa_coupled_matches_ab_and_oracle(oracle):
         assert normwise(v_aa, v_ab) < FP32_TOL
         Fh_ab = ab.forces()[0]
         Fh_aa = aa.forces()[0]
-        assert normwise(Fh_aa, Fh_ab) < 1e-4
+        assert normwise(Fh_aa, Fh_ab) < 2e-4
     _, u_o = o.moments()
     assert normwise(_np(u_aa), u_o) < FP32_TOL
     po, vo, _, _ = o.particles()
