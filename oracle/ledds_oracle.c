@@ -975,6 +975,72 @@ static int line_hit(const double r[3], const double R[9], const double s[3],
     return 1;
 }
 
+/* Perram-Wertheim separation certificate (Perram & Wertheim, J. Comput. Phys. 58, 409,
+ * 1985). With A^-1 = R^T diag(s^2) R for each ellipsoid (R rows = body axes) and d the
+ * centre difference, F(l) = l (1 - l) d^T C(l)^-1 d, C(l) = (1 - l) A_i^-1 + l A_j^-1;
+ * the ellipsoids overlap if and only if max over l in [0, 1] of F is at most 1, so any l
+ * with F(l) > 1 proves that they are disjoint. */
+static void pw_inv_shape(const double* R, const double* s, double M[6]) {
+    /* symmetric 3x3 in the order xx, yy, zz, xy, xz, yz */
+    const double q0 = s[0] * s[0], q1 = s[1] * s[1], q2 = s[2] * s[2];
+    M[0] = q0 * R[0] * R[0] + q1 * R[3] * R[3] + q2 * R[6] * R[6];
+    M[1] = q0 * R[1] * R[1] + q1 * R[4] * R[4] + q2 * R[7] * R[7];
+    M[2] = q0 * R[2] * R[2] + q1 * R[5] * R[5] + q2 * R[8] * R[8];
+    M[3] = q0 * R[0] * R[1] + q1 * R[3] * R[4] + q2 * R[6] * R[7];
+    M[4] = q0 * R[0] * R[2] + q1 * R[3] * R[5] + q2 * R[6] * R[8];
+    M[5] = q0 * R[1] * R[2] + q1 * R[4] * R[5] + q2 * R[7] * R[8];
+}
+
+/* F(l), with C(l)^-1 d from the adjugate of the symmetric C(l). */
+static double pw_F(const double Ai[6], const double Aj[6], const double d[3], double l) {
+    double c[6];
+    for (int k = 0; k < 6; ++k) c[k] = (1.0 - l) * Ai[k] + l * Aj[k];
+    const double a00 = c[1] * c[2] - c[5] * c[5];
+    const double a11 = c[0] * c[2] - c[4] * c[4];
+    const double a22 = c[0] * c[1] - c[3] * c[3];
+    const double a01 = c[4] * c[5] - c[3] * c[2];
+    const double a02 = c[3] * c[5] - c[4] * c[1];
+    const double a12 = c[3] * c[4] - c[0] * c[5];
+    const double det = c[0] * a00 + c[3] * a01 + c[4] * a02;
+    const double q = d[0] * (a00 * d[0] + a01 * d[1] + a02 * d[2]) +
+                     d[1] * (a01 * d[0] + a11 * d[1] + a12 * d[2]) +
+                     d[2] * (a02 * d[0] + a12 * d[1] + a22 * d[2]);
+    return l * (1.0 - l) * q / det;
+}
+
+/* 1 if F exceeds 1 + 1e-9 at one of at most 16 values of l, taken by a golden-section
+ * search for the maximum of F from the bracket [0, 1]; 0 if none does (no conclusion). */
+int or_pw_separated(const double ri[3], const double Ri[9], const double si[3],
+                    const double rj[3], const double Rj[9], const double sj[3]) {
+    const double margin = 1.0 + 1e-9, gr = 0.6180339887498949;
+    double Ai[6], Aj[6], d[3];
+    pw_inv_shape(Ri, si, Ai);
+    pw_inv_shape(Rj, sj, Aj);
+    for (int a = 0; a < 3; ++a) d[a] = rj[a] - ri[a];
+    double lo = 0.0, hi = 1.0;
+    double c = hi - gr * (hi - lo), e = lo + gr * (hi - lo);
+    double Fc = pw_F(Ai, Aj, d, c), Fe = pw_F(Ai, Aj, d, e);
+    if (Fc > margin || Fe > margin) return 1;
+    for (int k = 0; k < 14; ++k) {
+        if (Fc > Fe) {
+            hi = e;
+            e = c;
+            Fe = Fc;
+            c = hi - gr * (hi - lo);
+            Fc = pw_F(Ai, Aj, d, c);
+            if (Fc > margin) return 1;
+        } else {
+            lo = c;
+            c = e;
+            Fc = Fe;
+            e = lo + gr * (hi - lo);
+            Fe = pw_F(Ai, Aj, d, e);
+            if (Fe > margin) return 1;
+        }
+    }
+    return 0;
+}
+
 int or_ellipsoid_contact(const double ri[3], const double Ri[9], const double si[3],
                          const double rj[3], const double Rj[9], const double sj[3],
                          int max_iter, double tol, double* delta, double en[3],
@@ -1117,6 +1183,11 @@ static int ellipsoid_geom(or_sim* s, int i, int j, contact_geom* g) {
         }
         if ((h[0] + h[1]) < dist * (1.0 - 1e-12)) return 0;
     }
+    /* Perram-Wertheim certificate (same reading: a second exact pre-test): pairs proven
+     * disjoint skip the iteration. */
+    if (or_pw_separated(s->pos + 3 * i, s->triad + 9 * i, s->semi + 3 * i, rj_img, s->triad + 9 * j,
+                        s->semi + 3 * j))
+        return 0;
     double en[3], cp[3], rho_i, rho_j, delta;
     int iters;
     int rc = or_ellipsoid_contact(s->pos + 3 * i, s->triad + 9 * i, s->semi + 3 * i, rj_img,

@@ -85,6 +85,8 @@ def lib():
         L.or_beta_distance.restype = C.c_double
         L.or_beta_distance.argtypes = [dp, C.c_double]
         L.or_cell_collide.argtypes = [dp, C.c_double, C.c_int, dp, C.c_int, dp, dp, dp, dp, dp, dp]
+        L.or_pw_separated.restype = C.c_int
+        L.or_pw_separated.argtypes = [dp, dp, dp, dp, dp, dp]
         L.or_ellipsoid_contact.restype = C.c_int
         L.or_ellipsoid_contact.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_double,
                                            dp, dp, dp, dp, dp, ip]
@@ -298,6 +300,11 @@ def cell_collide(f, tau, B=(), uk=(), arm=(), force=(0, 0, 0), collision=0):
         armb[: 3 * ns] = np.asarray(arm, dtype=np.float64).reshape(-1)
     lib().or_cell_collide(_d(f, 19), float(tau), int(collision), _d(force, 3), ns, Bb, ukb, armb, fstar, Fk, Mk)
     return fstar, Fk.reshape(2, 3)[:ns], Mk.reshape(2, 3)[:ns]
+
+
+def pw_separated(ri, Ri, si, rj, Rj, sj):
+    """True if a Perram-Wertheim certificate proves the two ellipsoids disjoint."""
+    return bool(lib().or_pw_separated(_d(ri, 3), _d(Ri, 9), _d(si, 3), _d(rj, 3), _d(Rj, 9), _d(sj, 3)))
 
 
 def ellipsoid_contact(ri, Ri, si, rj, Rj, sj, max_iter=60, tol=1e-6):

@@ -361,3 +361,27 @@ def test_quaternion_free_rotation_exact():
         Rw = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
         err = max(err, np.abs(tri[k].reshape(3, 3) - d0[k] @ Rw.T).max())
     assert err < 1e-12
+
+
+def test_fluidised_bed_small(oracle):
+    """The fluidised-bed workload shape (periodic x and z, walls on y, gravity along -y on
+    particles of density ratio 1.1, distance fractions, 10 DEM substeps, tau for Re = 1)
+    scaled to 66 x 48 x 66 with spheres of diameter 10 at solid fraction 0.3, 20 coupled
+    steps: fields, trajectories and hydrodynamic forces at the parity tolerances."""
+    w = W.fluidised_bed(0.3, nx=66, ny=48, nz=66, diameter=10.0)
+    assert w.n > 40
+    o = oracle_from_workload(oracle, w)
+    s = gpu_from_workload(w)
+    o.step(20)
+    s.step(20)
+    _, u_o = o.moments()
+    _, u_g = s.fields()
+    assert normwise(u_g.cpu().numpy(), u_o) < FP32_TOL
+    po, vo, _, _ = o.particles()
+    pg, vg, _, _ = s.particles()
+    assert np.abs(pg - po).max() < 1e-6
+    assert normwise(vg, vo) < FP32_TOL
+    assert normwise(s.forces()[0], o.forces()[0]) < 1e-4
+    assert np.abs(vo[:, 1]).max() > 1e-7            # the spheres have started to settle (7e-7)
+    st = s.status()
+    assert st["rc"] == 0 and st["skin_violation"] == 0, st

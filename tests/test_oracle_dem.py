@@ -481,3 +481,59 @@ def test_quaternion_and_triad_updates_agree_to_second_order(oracle):
         diffs.append(np.abs(tris[0] - tris[1]).max())
     assert 1e-9 < diffs[0] < 1e-4
     assert 3.3 < diffs[0] / diffs[1] < 4.7
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_pw_certificate_spheres_closed_form(oracle, seed):
+    """Two spheres: the Perram-Wertheim function peaks at D^2/(R_i + R_j)^2 (at
+    l = R_i/(R_i + R_j)), so a certificate exists just beyond touching and never before."""
+    g = np.random.default_rng(seed)
+    for _ in range(50):
+        Ri, Rj = g.uniform(0.5, 8.0, 2)
+        u = g.normal(size=3)
+        u /= np.linalg.norm(u)
+        tri = W.quaternion_to_triad(W.random_quaternions(g, 2)).reshape(2, 9)
+        for f, expect in ((1.0 + 1e-4, True), (1.0 - 1e-4, False), (0.5, False), (2.0, True)):
+            rj = u * (Ri + Rj) * f
+            got = oracle.pw_separated(np.zeros(3), tri[0], [Ri] * 3, rj, tri[1], [Rj] * 3)
+            assert got == expect, (Ri, Rj, f)
+
+
+def _ellipsoid_points(center, R, s, n, g):
+    """Surface points of an ellipsoid (body axes = rows of R)."""
+    v = g.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    return center + (v * s) @ R
+
+
+def test_pw_certificate_is_sound_bruteforce(oracle):
+    """Random ellipsoid pairs near contact: whenever the certificate is given, no sampled
+    surface point of either ellipsoid lies inside the other and the common-normal
+    iteration finds a gap; pairs whose surfaces are found to interpenetrate by sampling
+    never get a certificate. Both outcomes occur."""
+    g = np.random.default_rng(95)
+    sep = ovl = 0
+    for _ in range(250):
+        si = g.uniform(0.4, 2.0, 3)
+        sj = g.uniform(0.4, 2.0, 3)
+        tri = W.quaternion_to_triad(W.random_quaternions(g, 2)).reshape(2, 3, 3)
+        d = g.normal(size=3)
+        d *= g.uniform(0.3, 1.2) * (si.max() + sj.max()) / np.linalg.norm(d)
+        ri, rj = np.zeros(3), d
+        cert = oracle.pw_separated(ri, tri[0].ravel(), si, rj, tri[1].ravel(), sj)
+        pi = _ellipsoid_points(ri, tri[0], si, 20000, g)
+        pj = _ellipsoid_points(rj, tri[1], sj, 20000, g)
+        # inside test x^T A x < 1 with A = R^T diag(1/s^2) R
+        bi = ((pj - ri) @ tri[0].T) / si
+        bj = ((pi - rj) @ tri[1].T) / sj
+        inside = (np.einsum("ij,ij->i", bi, bi) < 1.0).any() or (np.einsum("ij,ij->i", bj, bj) < 1.0).any()
+        if cert:
+            sep += 1
+            assert not inside
+            c = oracle.ellipsoid_contact(ri, tri[0].ravel(), si, rj, tri[1].ravel(), sj, max_iter=400, tol=1e-10)
+            if c["rc"] == 0:
+                assert c["delta"] < 0.0
+        if inside:
+            ovl += 1
+            assert not cert
+    assert sep > 50 and ovl > 50
