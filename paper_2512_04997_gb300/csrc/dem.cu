@@ -406,6 +406,66 @@ __device__ __noinline__ bool ell_geo(const DemArgs& A, const double ra[3], const
     return true;
 }
 
+// Perram-Wertheim separation certificate: with M = R^T diag(s^2) R per ellipsoid (R rows
+// = body axes) and d = r_b - r_a, F(l) = l (1 - l) d^T C(l)^-1 d, C(l) = (1 - l) M_a + l M_b;
+// the ellipsoids are disjoint if F(l) > 1 for some l (Perram & Wertheim 1985). F is
+// evaluated at up to 16 points of a golden-section search for its maximum on [0, 1]
+// (C^-1 d by the adjugate); a value above 1 + 1e-9 proves separation. The arithmetic is
+// that of the FP64 reference, in the same order.
+__device__ __forceinline__ void pw_shape(const double R[9], const double s[3], double M[6]) {
+    const double q0 = s[0] * s[0], q1 = s[1] * s[1], q2 = s[2] * s[2];
+    M[0] = q0 * R[0] * R[0] + q1 * R[3] * R[3] + q2 * R[6] * R[6];
+    M[1] = q0 * R[1] * R[1] + q1 * R[4] * R[4] + q2 * R[7] * R[7];
+    M[2] = q0 * R[2] * R[2] + q1 * R[5] * R[5] + q2 * R[8] * R[8];
+    M[3] = q0 * R[0] * R[1] + q1 * R[3] * R[4] + q2 * R[6] * R[7];
+    M[4] = q0 * R[0] * R[2] + q1 * R[3] * R[5] + q2 * R[6] * R[8];
+    M[5] = q0 * R[1] * R[2] + q1 * R[4] * R[5] + q2 * R[7] * R[8];
+}
+__device__ __forceinline__ double pw_value(const double Ma[6], const double Mb[6], const double d[3], double l) {
+    double c[6];
+    for (int k = 0; k < 6; ++k) c[k] = (1.0 - l) * Ma[k] + l * Mb[k];
+    const double a00 = c[1] * c[2] - c[5] * c[5];
+    const double a11 = c[0] * c[2] - c[4] * c[4];
+    const double a22 = c[0] * c[1] - c[3] * c[3];
+    const double a01 = c[4] * c[5] - c[3] * c[2];
+    const double a02 = c[3] * c[5] - c[4] * c[1];
+    const double a12 = c[3] * c[4] - c[0] * c[5];
+    const double det = c[0] * a00 + c[3] * a01 + c[4] * a02;
+    const double q = d[0] * (a00 * d[0] + a01 * d[1] + a02 * d[2]) + d[1] * (a01 * d[0] + a11 * d[1] + a12 * d[2]) +
+                     d[2] * (a02 * d[0] + a12 * d[1] + a22 * d[2]);
+    return l * (1.0 - l) * q / det;
+}
+__device__ __noinline__ bool pw_separated(const double ra[3], const double Ra_[9], const double sa[3],
+                                          const double rb[3], const double Rb_[9], const double sb[3]) {
+    const double margin = 1.0 + 1e-9, gr = 0.6180339887498949;
+    double Ma[6], Mb[6], d[3];
+    pw_shape(Ra_, sa, Ma);
+    pw_shape(Rb_, sb, Mb);
+    for (int a = 0; a < 3; ++a) d[a] = rb[a] - ra[a];
+    double lo = 0.0, hi = 1.0;
+    double c = hi - gr * (hi - lo), e = lo + gr * (hi - lo);
+    double Fc = pw_value(Ma, Mb, d, c), Fe = pw_value(Ma, Mb, d, e);
+    if (Fc > margin || Fe > margin) return true;
+    for (int k = 0; k < 14; ++k) {
+        if (Fc > Fe) {
+            hi = e;
+            e = c;
+            Fe = Fc;
+            c = hi - gr * (hi - lo);
+            Fc = pw_value(Ma, Mb, d, c);
+            if (Fc > margin) return true;
+        } else {
+            lo = c;
+            c = e;
+            Fc = Fe;
+            e = lo + gr * (hi - lo);
+            Fe = pw_value(Ma, Mb, d, e);
+            if (Fe > margin) return true;
+        }
+    }
+    return false;
+}
+
 // Geometry of the canonical pair (a < b) from state buffer st; false if no contact.
 __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& g) {
     double dd[3];
@@ -455,6 +515,7 @@ __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& 
     }
     tri_of(A, st, a, Ra_);
     tri_of(A, st, b, Rb_);
+    if (pw_separated(ra, Ra_, sa, rb, Rb_, sb)) return false;  // proven disjoint: no iteration
     if (!ell_geo(A, ra, Ra_, sa, rb, Rb_, sb, g)) return false;
     return g.delta > 0.0;
 }
