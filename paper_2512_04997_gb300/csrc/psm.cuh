@@ -185,6 +185,19 @@ __device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& t
         const float ext = hd * tc.ims[e] * 1.001f + 1e-3f;
         if (rn - ext > 1.0f) return 0.0f;
         if (rn + ext < 1.0f) return 1.0f;
+        if (rn > 1.0f) {
+            // In normalised coordinates the ellipsoid is the unit ball, which lies behind
+            // its tangent plane at q/|q|; the sample box (half-width h on each world axis)
+            // reaches towards that plane by at most h |M^T q/|q||_1, so if even its nearest
+            // corner is beyond the plane (margins far above FP32 rounding) no sample is
+            // inside. Tighter than the bound above where |M^T q| is small (near the ends
+            // of the long axes).
+            const float ir = 1.0f / rn;
+            const float w0 = (tc.m[0][e] * q0 + tc.m[3][e] * q1 + tc.m[6][e] * q2) * ir;
+            const float w1 = (tc.m[1][e] * q0 + tc.m[4][e] * q1 + tc.m[7][e] * q2) * ir;
+            const float w2 = (tc.m[2][e] * q0 + tc.m[5][e] * q1 + tc.m[8][e] * q2) * ir;
+            if (rn - h * (fabsf(w0) + fabsf(w1) + fabsf(w2)) * 1.001f > 1.0f + 1e-3f) return 0.0f;
+        }
         // every corner of the sample box strictly inside (convexity) => all samples are
         bool all_in = true;
 #pragma unroll
