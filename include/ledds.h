@@ -225,7 +225,10 @@ int ledds_set_profiling(ledds_sim_t s, int on);
 int ledds_read_profile(ledds_sim_t s, double ms[5], long long* steps, long long* launches);
 
 /* Checkpoint: serialise the full state (populations, particles, contact history, step
- * count) to a host buffer. With h_buf NULL, *bytes receives the size needed. */
+ * count) to a host buffer. With h_buf NULL, *bytes receives the size needed. A
+ * checkpoint loads into a simulation of the same dims and storage, or of the same dims
+ * but larger candidate or tile capacities (the lists are re-laid row by row): that is how
+ * a step that overflowed a capacity is replayed with larger capacities. */
 int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes);
 int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes);
 

@@ -1017,21 +1017,88 @@ int ledds_save(ledds_sim_t s, void* h_buf, size_t* bytes) {
     return LEDDS_OK;
 }
 
+// Effective candidate and tile capacities of a dims record (0 selects the defaults).
+static int cand_cap_of(const ledds_dims& d) { return d.cand_cap > 0 ? d.cand_cap : 32; }
+static int tile_cap_of(const ledds_dims& d) { return d.tile_cap > 0 ? d.tile_cap : 64; }
+
+// A checkpoint taken with smaller candidate or tile capacities, copied into this
+// simulation's layout: arrays that do not depend on the capacities whole, the candidate
+// lists and their tangential histories row by row (one row per particle, the new rows
+// longer), and nothing of the lists every step rebuilds (tile lists, pair-once lists).
+static cudaError_t load_resized(ledds_sim_t s, const CkptHeader& hd, const char* img) {
+    ledds_sim_s o;  // the checkpoint's layout, as offsets from a stand-in base
+    char* const base = reinterpret_cast<char*>(4096);
+    layout(&o, &hd.d, &hd.p, base);
+    cudaError_t e = cudaSuccess;
+    auto whole = [&](void* dst, const void* old, size_t bytes) {
+        if (e == cudaSuccess && bytes)
+            e = cudaMemcpyAsync(dst, img + ((const char*)old - base), bytes, cudaMemcpyHostToDevice, s->stream);
+    };
+    auto rows = [&](void* dst, const void* old, size_t row_old, size_t row_new, size_t nrows) {
+        if (e == cudaSuccess && nrows)
+            e = cudaMemcpy2DAsync(dst, row_new, img + ((const char*)old - base), row_old, row_old, nrows,
+                                  cudaMemcpyHostToDevice, s->stream);
+    };
+    const size_t N19 = (size_t)s->N * 19 * storage_bytes(s->p.storage);
+    whole(s->pop[0], o.pop[0], N19);
+    if (s->pop[1] != s->pop[0]) whole(s->pop[1], o.pop[1], N19);
+    const size_t c = (size_t)s->P.cap, d8 = sizeof(double);
+    for (int b = 0; b < 2; ++b) whole(s->P.st[b], o.P.st[b], 18 * c * d8);
+    whole(s->P.acc, o.P.acc, 3 * c * d8);
+    whole(s->P.alpha, o.P.alpha, 3 * c * d8);
+    whole(s->P.Fc, o.P.Fc, 3 * c * d8);
+    whole(s->P.Mc, o.P.Mc, 3 * c * d8);
+    whole(s->P.Fh, o.P.Fh, 6 * c * d8);    // Fh and Mh
+    whole(s->P.Fhp, o.P.Fhp, 6 * c * d8);  // Fhp and Mhp
+    whole(s->P.pos_build, o.P.pos_build, 3 * c * d8);
+    whole(s->P.radius, o.P.radius, c * d8);
+    whole(s->P.semi, o.P.semi, 3 * c * d8);
+    whole(s->P.bound, o.P.bound, c * d8);
+    whole(s->P.mass, o.P.mass, c * d8);
+    whole(s->P.inertia, o.P.inertia, 3 * c * d8);
+    whole(s->P.gfac, o.P.gfac, c * d8);
+    whole(s->P.shape, o.P.shape, c * sizeof(int));
+    whole(s->keys, o.keys, c * sizeof(uint32_t));
+    whole(s->rank, o.rank, c * sizeof(int));
+    whole(s->sorted, o.sorted, c * sizeof(int));
+    whole(s->cell_count, o.cell_count, ((size_t)s->G + 1) * sizeof(uint32_t));
+    whole(s->cell_start, o.cell_start, ((size_t)s->G + 1) * sizeof(uint32_t));
+    const size_t oc = (size_t)o.ccap, nc = (size_t)s->ccap;
+    for (int b = 0; b < 2; ++b) {
+        rows(s->cand[b], o.cand[b], oc * sizeof(int), nc * sizeof(int), c);
+        whole(s->ncand[b], o.ncand[b], c * sizeof(int));
+        rows(s->hist[b], o.hist[b], oc * 3 * d8, nc * 3 * d8, c);
+    }
+    whole(s->whist, o.whist, 18 * c * d8);
+    whole(s->status, o.status, sizeof(DevStatus));
+    return e;
+}
+
 int ledds_load(ledds_sim_t s, const void* h_buf, size_t bytes) {
     if (!s || !h_buf || bytes < sizeof(CkptHeader)) return LEDDS_ERR_INVALID_ARG;
     CkptHeader hd;
     memcpy(&hd, h_buf, sizeof(hd));
     size_t used = layout(nullptr, &s->d, &s->p, nullptr) - 256;
-    if (memcmp(hd.magic, "LEDDSCK2", 8) != 0 || hd.ws_used != used || bytes < sizeof(hd) + used ||
-        memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0 || hd.p.storage != s->p.storage ||
-        hd.p.pattern != s->p.pattern)
+    if (memcmp(hd.magic, "LEDDSCK2", 8) != 0 || hd.p.storage != s->p.storage || hd.p.pattern != s->p.pattern)
         return LEDDS_ERR_INVALID_ARG;
-    if (cudaMemcpyAsync(s->ws, (const char*)h_buf + sizeof(hd), used, cudaMemcpyHostToDevice, s->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(s->stream) != cudaSuccess)
-        return LEDDS_ERR_CUDA;
+    // the same dims, or the same but for larger candidate or tile capacities here
+    ledds_dims same = hd.d;
+    same.cand_cap = s->d.cand_cap;
+    same.tile_cap = s->d.tile_cap;
+    if (memcmp(&same, &s->d, sizeof(ledds_dims)) != 0) return LEDDS_ERR_INVALID_ARG;
+    const bool resized = memcmp(&hd.d, &s->d, sizeof(ledds_dims)) != 0;
+    if (resized && (cand_cap_of(hd.d) > cand_cap_of(s->d) || tile_cap_of(hd.d) > tile_cap_of(s->d)))
+        return LEDDS_ERR_INVALID_ARG;
+    const size_t used_old = resized ? layout(nullptr, &hd.d, &hd.p, nullptr) - 256 : used;
+    if (hd.ws_used != used_old || bytes < sizeof(hd) + used_old) return LEDDS_ERR_INVALID_ARG;
+    const char* img = (const char*)h_buf + sizeof(hd);
+    cudaError_t e = resized ? load_resized(s, hd, img)
+                            : cudaMemcpyAsync(s->ws, img, used, cudaMemcpyHostToDevice, s->stream);
+    if (e != cudaSuccess || cudaStreamSynchronize(s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
     s->p = hd.p;
     s->P.n = hd.n;
+    // (tile lists are rebuilt by every step; the leading rebuild of the next step
+    // rebuilds the candidate lists from the loaded positions and histories)
     s->parity = hd.parity;
     s->steps = hd.steps;
     memcpy(s->uw, hd.uw, sizeof(hd.uw));

@@ -16,6 +16,8 @@ import numpy as np
 from . import build as _build
 
 LEDDS_OK = 0
+LEDDS_ERR_CAPACITY, LEDDS_ERR_STATE = -2, -6
+MAX_CAP = 64        # largest candidate and tile capacity of the library
 ERRORS = {-1: "invalid argument", -2: "capacity exceeded", -3: "non-finite values detected",
           -4: "device wait timed out", -5: "CUDA runtime error", -6: "invalid state"}
 STORE = {"f32": 0, "f16": 1, "bf16": 2}
@@ -276,8 +278,48 @@ class Sim:
         check("ledds_write_kinematics", lib().ledds_write_kinematics(self.h, ptr, int(bool(on_device))))
 
     # stepping -----------------------------------------------------------------------
-    def step(self, n=1):
-        check("ledds_step", lib().ledds_step(self.h, int(n)))
+    def step(self, n=1, regrow=False, chunk=100):
+        """Advance n fluid steps (asynchronous). With regrow, the steps run in chunks of
+        `chunk`, each after a checkpoint; a chunk that overflows the candidate or tile
+        capacity is replayed from that checkpoint in a simulation with doubled capacities
+        (up to the library's maximum, 64), which then replaces this one's handle and
+        workspace. LeddsError(CAPACITY) if the maximum does not suffice."""
+        if not regrow:
+            check("ledds_step", lib().ledds_step(self.h, int(n)))
+            return
+        if getattr(self, "_owner", None) is not None:
+            raise LeddsError("ledds_step", LEDDS_ERR_STATE)   # batch members cannot be replaced
+        left = int(n)
+        while left > 0:
+            k = min(left, int(chunk))
+            snap = self.save()
+            check("ledds_step", lib().ledds_step(self.h, k))
+            st = self.status()
+            while st["tile_overflow"] or st["cand_overflow"]:
+                self._regrow(snap, st["tile_overflow"] > 0, st["cand_overflow"] > 0)
+                check("ledds_step", lib().ledds_step(self.h, k))
+                st = self.status()
+            left -= k
+
+    def _regrow(self, snap, tiles, cands):
+        """Replace this simulation by one with doubled tile and/or candidate capacity,
+        loaded from checkpoint `snap` (taken with the current, smaller capacities)."""
+        d = ledds_dims()
+        C.memmove(C.byref(d), C.byref(self.dims), C.sizeof(d))
+        cur_t = d.tile_cap if d.tile_cap > 0 else 64
+        cur_c = d.cand_cap if d.cand_cap > 0 else 32
+        if (tiles and cur_t >= MAX_CAP) or (cands and cur_c >= MAX_CAP):
+            raise LeddsError("ledds_step", LEDDS_ERR_CAPACITY)
+        if tiles:
+            d.tile_cap = min(MAX_CAP, 2 * cur_t)
+        if cands:
+            d.cand_cap = min(MAX_CAP, 2 * cur_c)
+        new = Sim(d, self.params, self.device, self.stream)
+        new.load(snap)
+        new.n = self.n
+        lib().ledds_destroy(self.h)
+        self.h, self.workspace, self.dims = new.h, new.workspace, new.dims
+        new.h = None
 
     def sync(self):
         check("ledds_sync", lib().ledds_sync(self.h))

@@ -200,3 +200,32 @@ def test_jeffery_orbit_period():
     assert abs(T_meas / T - 1.0) < 0.05, (T_meas, T)
     st = s.status()
     assert st["rc"] == 0 and st["nan_detected"] == 0, st
+
+
+def test_capacity_regrow_and_replay():
+    """Too small candidate and tile capacities: stepping with regrow replays every chunk that
+    overflowed from its checkpoint in a simulation with doubled capacities, and ends where a
+    simulation created with ample capacities ends (to the accumulation-order rounding of
+    the hydrodynamic sums), with no overflow left in its counters."""
+    w = W.couette_suspension(nx=64, ny=64, nz=64, n_particles=62, steps=40)
+    w.params["tile_cap"] = 4        # a 32x8x16 tile meets more spheres than that
+    w.params["cand_cap"] = 2        # and a sphere more candidates
+    ref = gpu_from_workload(w, tile_cap=64, cand_cap=32)
+    s = gpu_from_workload(w)
+    assert (s.dims.tile_cap, s.dims.cand_cap) == (4, 2)
+    ref.step(30)
+    s.step(30, regrow=True, chunk=10)
+    st = s.status()
+    assert st["rc"] == 0 and st["tile_overflow"] == 0 and st["cand_overflow"] == 0, st
+    assert s.dims.tile_cap > 4 and s.dims.cand_cap > 2
+    _, ur = ref.fields()
+    _, us = s.fields()
+    assert normwise(us.cpu().numpy(), ur.cpu().numpy()) < 1e-6
+    pr, vr, _, _ = ref.particles()
+    ps, vs, _, _ = s.particles()
+    assert np.abs(ps - pr).max() < 1e-7
+    assert normwise(vs, vr) < 1e-6
+    # without regrow the same capacities overflow
+    t = gpu_from_workload(w)
+    t.step(10)
+    assert t.status()["tile_overflow"] > 0
