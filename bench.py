@@ -370,9 +370,10 @@ def rheology_measure(device, stream, phis=(0.0, 0.1, 0.2, 0.3), steps=20000, eve
             "seconds": time.perf_counter() - t0, "points": rows}
 
 
-def oracle_sample(steps):
+def oracle_sample(steps, keep=False):
     """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
-    slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps."""
+    slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps
+    after one untimed step; with keep, also the oracle simulation and the workload."""
     from oracle import oracle as O
     from paper_2512_04997_gb300 import workloads as W
     sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -384,10 +385,11 @@ def oracle_sample(steps):
     o.step(steps)
     dt = time.perf_counter() - t0
     mlups = w.ncell * steps / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} coupled steps of a 256x256x32 slab of the workload "
-                      f"(500 spheres, same solid fraction), FP64, single thread",
-            "seconds": dt}
+    res = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+           "sample": f"{steps} coupled steps of a 256x256x32 slab of the workload "
+                     f"(500 spheres, same solid fraction), FP64, single thread",
+           "seconds": dt}
+    return (res, o, w) if keep else res
 
 
 def main_workload(args):
@@ -555,9 +557,24 @@ def main():
         variants["rheology"] = rheology_measure(f"cuda:{local}", stream)
 
     cpu = None
+    oracle_err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(2)
+        cpu, o, ws = oracle_sample(2, keep=True)
         cpu.pop("seconds", None)
+        # the CUDA path on the same slab and steps: its error against the oracle
+        gs = ledds.from_workload(ws, device=f"cuda:{local}")
+        gs.step(3)
+        _, ug = gs.fields()
+        _, uo = o.moments()
+        pg = gs.particles()[0]
+        po = o.particles()[0]
+        import numpy as np
+        ugn = ug.cpu().numpy()
+        oracle_err = {"sample": "the oracle's slab, 3 coupled steps",
+                      "velocity_normwise": float(np.abs(ugn - uo).max() / np.abs(uo).max()),
+                      "positions_max_abs": float(np.abs(pg - po).max()),
+                      "tolerance": {"velocity_normwise": 1e-5, "positions_max_abs": 1e-6}}
+        del gs
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
@@ -565,7 +582,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": main_config(w, args.storage, world),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "error_vs_oracle": oracle_err, "e2e": e2e,
                 "gpu_launches": st["launches_per_step"] * args.steps,
                 "clocks": clk, "stages_ms_per_step": {k: v / psteps for k, v in zip(STAGES, stage_ms)},
                 "status": {k: st[k] for k in ("tile_overflow", "cand_overflow", "skin_violation",

@@ -87,6 +87,7 @@ struct ledds_sim_s {
     long long steps = 0;
     // graphs
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
+    cudaGraphExec_t grb[2] = {nullptr, nullptr};  // the leading list rebuild, per parity
     int launches_per_step = 0;
     // profiling
     bool profiling = false;
@@ -421,7 +422,8 @@ static void drop_graphs(ledds_sim_s* s) {
     for (int q = 0; q < 2; ++q) {
         if (s->g1[q]) cudaGraphExecDestroy(s->g1[q]);
         if (s->g2[q]) cudaGraphExecDestroy(s->g2[q]);
-        s->g1[q] = s->g2[q] = nullptr;
+        if (s->grb[q]) cudaGraphExecDestroy(s->grb[q]);
+        s->g1[q] = s->g2[q] = s->grb[q] = nullptr;
     }
 }
 
@@ -819,11 +821,23 @@ int ledds_step(ledds_sim_t s, int n_steps) {
         return LEDDS_OK;
     }
     if (n_steps > 0 && s->lattice && s->P.n > 0 && !s->lists_ready) {
-        // the first step after new positions: its lists, as a step of the serial order builds them
-        DemArgs A = dem_args(s);
-        int launches = 0;
-        if (launch_rebuild(A, s->parity, s->parity ^ 1, 0, s->scan_partial, s->stream, &launches) != cudaSuccess)
-            return LEDDS_ERR_CUDA;
+        // the first step after new positions: its lists, as a step of the serial order
+        // builds them (one captured graph per parity: host-driven loops that rewrite the
+        // kinematics every step take this path every step)
+        const int p = s->parity;
+        if (!s->grb[p]) {
+            DemArgs A = dem_args(s);
+            int launches = 0;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return LEDDS_ERR_CUDA;
+            cudaError_t e = launch_rebuild(A, p, p ^ 1, 0, s->scan_partial, s->cap_stream, &launches);
+            cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+            if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&s->grb[p], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess || e2 != cudaSuccess) return LEDDS_ERR_CUDA;
+        }
+        if (cudaGraphLaunch(s->grb[p], s->stream) != cudaSuccess) return LEDDS_ERR_CUDA;
     }
     s->lists_ready = true;  // every graph step ends with the rebuild for the next
     int left = n_steps;
