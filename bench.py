@@ -84,7 +84,7 @@ def peaks():
 
 def psm_source_hash():
     h = hashlib.sha256()
-    for f in ("lbm.cu", "psm.cuh", "psm_aa.cu", "internal.cuh"):
+    for f in ("lbm.cu", "psm.cuh", "psm_aa.cu", "psm_wide.cu", "internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2512_04997_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -98,6 +98,9 @@ typedef struct {
                              /* in place by alternating steps (half the population memory;   */
                              /* identical results in FP32; not for batch members). Sec. 6     */
                              /* names single-population schemes as a memory reduction        */
+    int index64;             /* 1: 64-bit population offsets in the PSM kernel; 0: only when  */
+                             /* 19 nx ny nz >= 2^31 (lattices of more than 1.1e8 nodes up to  */
+                             /* 2^31 nodes use them automatically; batch members cannot)      */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */

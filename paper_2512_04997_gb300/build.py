@@ -19,7 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "--expt-relaxed-constexpr"]
-SOURCES = {"lbm.cu": [], "psm_aa.cu": [], "dem.cu": ["-fmad=false"], "api.cu": [], "noalloc.cu": ["-fmad=false"]}
+SOURCES = {"lbm.cu": [], "psm_aa.cu": [], "psm_wide.cu": [], "dem.cu": ["-fmad=false"], "api.cu": [],
+           "noalloc.cu": ["-fmad=false"]}
 
 
 def _nvcc():

@@ -120,8 +120,8 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (d->nx < 0 || d->ny < 0 || d->nz < 0) return LEDDS_ERR_INVALID_ARG;
     bool lat = d->nx > 0 || d->ny > 0 || d->nz > 0;
     if (lat && (d->nx <= 0 || d->ny <= 0 || d->nz <= 0)) return LEDDS_ERR_INVALID_ARG;
-    // populations are addressed with 32-bit element offsets
-    if (lat && 20.0 * (double)d->nx * d->ny * d->nz >= 2147483647.0) return LEDDS_ERR_INVALID_ARG;
+    // node indices are 32-bit (population offsets become 64-bit beyond 19 N = 2^31)
+    if (lat && (double)d->nx * d->ny * d->nz >= 2147483647.0) return LEDDS_ERR_INVALID_ARG;
     if (!lat && d->max_particles <= 0) return LEDDS_ERR_INVALID_ARG;
     if (d->max_particles < 0) return LEDDS_ERR_INVALID_ARG;
     if (!(p->tau > 0.5)) return LEDDS_ERR_INVALID_ARG;
@@ -139,6 +139,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->collision < 0 || p->collision > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->orient < 0 || p->orient > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->pattern < 0 || p->pattern > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->index64 < 0 || p->index64 > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -318,8 +319,10 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
     // the post-collision f*_i in slot opp(i) (the step from it streams); the two pointers
     // are the same array
     a.aa = s->p.pattern != LEDDS_PATTERN_AA ? PSM_AB : (in == 0 ? PSM_AA_EVEN : PSM_AA_ODD);
+    // 64-bit population offsets when 19 N elements pass the 32-bit range (or if requested)
+    a.w64 = s->p.index64 || 19LL * s->N >= 2147483647LL;
     for (int i = 0; i < 19; ++i) {
-        a.pN[i] = (int)(i * s->N);
+        a.pN[i] = a.w64 ? 0 : (int)(i * s->N);
         a.off[i] = CX(i) + s->d.nx * (CY(i) + s->d.ny * CZ(i));
         if (a.off[i] & 1) a.off_odd |= 1u << i;
     }
@@ -557,6 +560,7 @@ int ledds_params_default(ledds_params* p) {
     p->collision = LEDDS_COLLIDE_BGK;
     p->orient = LEDDS_ORIENT_TRIAD;
     p->pattern = LEDDS_PATTERN_AB;
+    p->index64 = 0;
     return LEDDS_OK;
 }
 
@@ -1156,6 +1160,8 @@ static int batch_layout(int nsim, const ledds_dims* dims, const ledds_params* pa
         if (params[i].storage != params[0].storage) return LEDDS_ERR_INVALID_ARG;
         if (params[i].collision != params[0].collision) return LEDDS_ERR_INVALID_ARG;
         if (params[i].pattern != LEDDS_PATTERN_AB) return LEDDS_ERR_INVALID_ARG;  // batches use two lattices
+        if (params[i].index64 || 19.0 * dims[i].nx * dims[i].ny * dims[i].nz >= 2147483647.0)
+            return LEDDS_ERR_INVALID_ARG;  // and 32-bit population offsets
         if (dims[i].max_particles > 4096) return LEDDS_ERR_INVALID_ARG;  // direct candidate search
         if (offs) offs->push_back(off);
         off = align256(off + layout(nullptr, &dims[i], &params[i], nullptr));

@@ -118,8 +118,11 @@ struct DevParticles {
 };
 
 // Population array patterns, which are also the PSM kernel's step forms: the two-lattice
-// pull (AB), and the in-place AA pattern's two alternating steps.
-enum { PSM_AB = 0, PSM_AA_EVEN = 1, PSM_AA_ODD = 2 };
+// pull (AB), and the in-place AA pattern's two alternating steps. A kernel's MODE is the
+// form, plus PSM_W64 when the populations need 64-bit element offsets (19 N >= 2^31).
+enum { PSM_AB = 0, PSM_AA_EVEN = 1, PSM_AA_ODD = 2, PSM_W64 = 4 };
+__host__ __device__ constexpr int psm_form(int mode) { return mode & 3; }
+__host__ __device__ constexpr bool psm_w64(int mode) { return (mode & PSM_W64) != 0; }
 
 // Offsets of the state buffer components.
 constexpr int SP = 0, SV = 3, SW = 6, ST = 9;
@@ -163,6 +166,7 @@ struct LbmArgs {
     int aa;                       // pattern of the array: PSM_AB (two lattices), or one array
                                   // (AA) holding PSM_AA_EVEN: pre-collision f, natural slots,
                                   // or PSM_AA_ODD: post-collision f*_i in slot opp(i)
+    int w64;                      // 64-bit plane offsets (pN unused): 19 N >= 2^31 or requested
 };
 
 // Arguments of one batched PSM launch: up to BATCH_CHUNK members and the prefix sums of

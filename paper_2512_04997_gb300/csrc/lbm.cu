@@ -505,30 +505,10 @@ cudaError_t launch_bin(const LbmArgs& a, int n, int* tile_count, int* tile_ids, 
     return cudaGetLastError();
 }
 
-template <int STORE, bool TRT>
-static cudaError_t launch_psm_t(const LbmArgs& a, cudaStream_t s) {
-    static bool configured = false;
-    const size_t smem = psm_smem_bytes(STORE);
-    if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_psm<STORE, TRT, PSM_AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    k_psm<STORE, TRT, PSM_AB><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_psm(const LbmArgs& a, int store, cudaStream_t s) {
+    if (a.w64) return launch_psm_wide(a, store, s);
     if (a.aa != PSM_AB) return launch_psm_aa(a, store, s);
-    if (a.trt) {
-        if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32, true>(a, s);
-        if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16, true>(a, s);
-        return launch_psm_t<LEDDS_STORE_BF16, true>(a, s);
-    }
-    if (store == LEDDS_STORE_F32) return launch_psm_t<LEDDS_STORE_F32, false>(a, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_t<LEDDS_STORE_F16, false>(a, s);
-    return launch_psm_t<LEDDS_STORE_BF16, false>(a, s);
+    return launch_psm_mode<PSM_AB>(a, store, s);
 }
 
 template <int STORE, bool TRT>

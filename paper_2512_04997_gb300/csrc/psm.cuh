@@ -4,12 +4,15 @@
 // psm_aa.cu (the in-place AA pattern).
 #pragma once
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace ledds {
 
-size_t psm_smem_bytes(int store);                                  // lbm.cu
-cudaError_t launch_psm_aa(const LbmArgs& a, int store, cudaStream_t s);  // psm_aa.cu
+size_t psm_smem_bytes(int store);                                    // lbm.cu
+cudaError_t launch_psm_aa(const LbmArgs& a, int store, cudaStream_t s);    // psm_aa.cu
+cudaError_t launch_psm_wide(const LbmArgs& a, int store, cudaStream_t s);  // psm_wide.cu
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -431,6 +434,16 @@ __device__ __forceinline__ void link_walls(const Plan& p, bool& wx, bool& wy, bo
     wz = (cz == 1 && (p.bw & 16u)) || (cz == -1 && (p.bw & 32u));
 }
 
+// Element offsets into the population array: 32-bit, or 64-bit under PSM_W64; the offset
+// of plane i is then i N computed in 64 bits instead of the 32-bit table entry.
+template <int MODE>
+using PsmIdx = std::conditional_t<psm_w64(MODE), long long, int>;
+template <int MODE>
+__device__ __forceinline__ PsmIdx<MODE> plane_at(const LbmArgs& a, int i) {
+    if constexpr (psm_w64(MODE)) return (long long)i * a.N;
+    else return a.pN[i];
+}
+
 // Element index of the population f_I(x) a step of form MODE reads; WALLS: some link of
 // the warp may cross a wall (uniform choice of the caller).
 //   PSM_AB:      f*_I(x - c_I) in plane I, or at a wall f*_opp(I)(x) (halfway bounce-back);
@@ -438,24 +451,25 @@ __device__ __forceinline__ void link_walls(const Plan& p, bool& wx, bool& wy, bo
 //   PSM_AA_ODD:  f*_I(x - c_I), kept by the previous step in plane opp(I) at x - c_I, or
 //                at a wall f*_opp(I)(x), kept in plane I at x.
 template <int I, bool WALLS, int MODE>
-__device__ __forceinline__ int src_elem(const LbmArgs& a, const Plan& p) {
+__device__ __forceinline__ PsmIdx<MODE> src_elem(const LbmArgs& a, const Plan& p) {
     constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
-    if constexpr (MODE == PSM_AA_EVEN) return a.pN[I] + p.cell;
-    constexpr int plane_in = MODE == PSM_AA_ODD ? OPP(I) : I;
-    constexpr int plane_wall = MODE == PSM_AA_ODD ? I : OPP(I);
+    if constexpr (psm_form(MODE) == PSM_AA_EVEN) return plane_at<MODE>(a, I) + p.cell;
+    constexpr int plane_in = psm_form(MODE) == PSM_AA_ODD ? OPP(I) : I;
+    constexpr int plane_wall = psm_form(MODE) == PSM_AA_ODD ? I : OPP(I);
     if constexpr (WALLS) {
         bool wx, wy, wz;
         link_walls<I>(p, wx, wy, wz);
-        if (wx || wy || wz) return a.pN[plane_wall] + p.cell;
+        if (wx || wy || wz) return plane_at<MODE>(a, plane_wall) + p.cell;
     }
-    int src = p.cell - a.off[I];
+    // (64-bit: with a periodic wrap the index can pass 2^31 before the plane start is added)
+    PsmIdx<MODE> src = (PsmIdx<MODE>)p.cell - a.off[I];
     if (cx == 1) src += p.wxm;
     if (cx == -1) src += p.wxp;
     if (cy == 1) src += p.wym;
     if (cy == -1) src += p.wyp;
     if (cz == 1) src += p.wzm;
     if (cz == -1) src += p.wzp;
-    return a.pN[plane_in] + src;
+    return plane_at<MODE>(a, plane_in) + src;
 }
 
 template <class SS, int I, bool WALLS, int MODE>
@@ -480,7 +494,7 @@ __device__ __forceinline__ void issue_node(const LbmArgs& a, const typename SS::
                                            bool pred, uint32_t* slot) {
     Plan p;
     make_plan(a, x, y, z, p);
-    if (MODE != PSM_AA_EVEN && __any_sync(FULL, pred && p.bw != 0u)) {
+    if (psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, pred && p.bw != 0u)) {
         if (pred) IssueAll<SS, 0, true, MODE>::run(a, pin, p, slot);
     } else if (pred) {
         IssueAll<SS, 0, false, MODE>::run(a, pin, p, slot);
@@ -505,7 +519,7 @@ struct ReadAll {
         // of x - c_x (of x itself for a bounced link or an in-place read).
         int odd = 0;
         if (sizeof(typename SS::T) == 2) {
-            const int shift = (wl || MODE == PSM_AA_EVEN) ? 0 : CX(I);
+            const int shift = (wl || psm_form(MODE) == PSM_AA_EVEN) ? 0 : CX(I);
             odd = a.nx_even ? ((p.cell ^ shift) & 1) : (src_elem<I, WALLS, MODE>(a, p) & 1);
         }
         float v = decode<SS>(w, odd, a.inv_scale);
@@ -562,21 +576,21 @@ __device__ __forceinline__ float cqc(const SolidSums& m) {
 // `node` points at the node's element of plane 0.
 template <class SS, int I, int MODE, bool WALLS>
 __device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS::T* node, float v) {
-    if constexpr (MODE == PSM_AB) {
-        SS::store(node + a.pN[I], v, a.scale);
-    } else if constexpr (MODE == PSM_AA_EVEN) {
-        SS::store(node + a.pN[OPP(I)], v, a.scale);
+    if constexpr (psm_form(MODE) == PSM_AB) {
+        SS::store(node + plane_at<MODE>(a, I), v, a.scale);
+    } else if constexpr (psm_form(MODE) == PSM_AA_EVEN) {
+        SS::store(node + plane_at<MODE>(a, OPP(I)), v, a.scale);
     } else {
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         if constexpr (WALLS) {
             bool wx, wy, wz;
             link_walls<OPP(I)>(p, wx, wy, wz);
             if (wx || wy || wz) {
-                SS::store(node + a.pN[OPP(I)], v + wall_term<OPP(I)>(a.uw, wx, wy, wz), a.scale);
+                SS::store(node + plane_at<MODE>(a, OPP(I)), v + wall_term<OPP(I)>(a.uw, wx, wy, wz), a.scale);
                 return;
             }
         }
-        int d = a.pN[I] + a.off[I];
+        PsmIdx<MODE> d = plane_at<MODE>(a, I) + a.off[I];
         if (cx == 1) d += p.wxp;
         if (cx == -1) d += p.wxm;
         if (cy == 1) d += p.wyp;
@@ -711,7 +725,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
         make_plan(a, valid ? x : 0, y, z, pl);
         const uint32_t* slot = stage + ((r % PSM_STAGES) * 19) * PSM_THREADS + tid;
         // some lane of the warp has a wall link (never needed by the in-place step)
-        const bool wwarp = MODE != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
+        const bool wwarp = psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
         if (wwarp) {
             if (valid) ReadAll<SS, 0, true, MODE>::run(a, pl, slot, g);
         } else if (valid) {
@@ -757,7 +771,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
             const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
             SolidSums m;
             m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
-            if (MODE == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
+            if (psm_form(MODE) == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
                 CollidePairs<SS, 1, false, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
                                                                  kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
             else
@@ -801,7 +815,7 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
             m.Qyz = b0y * d0z + b1y * d1z;
             m.S = q0.B * d0s + q1.B * d1s;
         }
-        if (MODE == PSM_AA_ODD && wwarp)
+        if (psm_form(MODE) == PSM_AA_ODD && wwarp)
             CollidePairs<SS, 1, true, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
                                                             force_wa, m, pout + pl.cell, pl, valid);
         else
@@ -865,6 +879,34 @@ __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const 
     const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
     psm_tile<STORE, TRT, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per, part * per + per,
                                psm_smem);
+}
+
+// Host side: launch k_psm in form MODE (its shared-memory size is set on first use), and
+// the dispatch over storage format and collision operator.
+template <int STORE, bool TRT, int MODE>
+static cudaError_t launch_psm_form(const LbmArgs& a, cudaStream_t s) {
+    static bool configured = false;
+    const size_t smem = psm_smem_bytes(STORE);
+    if (!configured) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_psm<STORE, TRT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_psm<STORE, TRT, MODE><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_psm_mode(const LbmArgs& a, int store, cudaStream_t s) {
+    if (a.trt) {
+        if (store == LEDDS_STORE_F32) return launch_psm_form<LEDDS_STORE_F32, true, MODE>(a, s);
+        if (store == LEDDS_STORE_F16) return launch_psm_form<LEDDS_STORE_F16, true, MODE>(a, s);
+        return launch_psm_form<LEDDS_STORE_BF16, true, MODE>(a, s);
+    }
+    if (store == LEDDS_STORE_F32) return launch_psm_form<LEDDS_STORE_F32, false, MODE>(a, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_form<LEDDS_STORE_F16, false, MODE>(a, s);
+    return launch_psm_form<LEDDS_STORE_BF16, false, MODE>(a, s);
 }
 
 }  // namespace ledds

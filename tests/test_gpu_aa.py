@@ -179,3 +179,65 @@ def test_aa_checkpoint_rebase_and_reinit(oracle):
         aa.step(3)
         ab.step(3)
         assert np.abs(_np(aa.populations()) - _np(ab.populations())).max() < 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_64bit_offsets_identical(oracle, pattern, storage):
+    """The PSM kernel with 64-bit population offsets (used automatically beyond 19 N = 2^31
+    elements, requested here on small lattices) gives the same populations in every step
+    form, with walls and with periodic wraps: bit for bit in FP32; with 16-bit storage the
+    two instantiations may fuse the scaling of decoded values into different FMAs, which
+    shifts a stored value by one rounding of the format now and then (seen: 2e-7 to 2e-6
+    on a few of 1.5e5 values after 3 to 6 steps), so the bound there is 1e-5."""
+    g = W.rng(530)
+    for periodic, walls in (((1, 1, 1), None), ((1, 1, 0), "z"), ((0, 0, 0), "all")):
+        w = _lattice(periodic, walls, (37, 19, 11), storage=storage, fluid_force=(1e-6, 0.0, 0.0))
+        f0 = random_populations(oracle, g, w.nx, w.ny, w.nz)
+        a = gpu_from_workload(w, populations=f0, pattern=pattern)
+        b = gpu_from_workload(w, populations=f0, pattern=pattern, index64=1)
+        for n in (1, 2, 3):
+            a.step(n)
+            b.step(n)
+            d = np.abs(_np(a.populations()) - _np(b.populations())).max()
+            assert d <= (0.0 if storage == "f32" else 1e-5), (walls, n, d)
+
+
+@pytest.mark.parametrize("pattern", ["ab", "aa"])
+def test_lattice_beyond_32bit_offsets(oracle, pattern):
+    """A lattice of 512 x 512 x 432 nodes (1.13e8; 19 N > 2^31 population elements), walls
+    on z moving in x, one step in each form of the pattern: sampled nodes, many in the top
+    planes where the element offsets pass 2^31, against the oracle's collision of the
+    node's pre-collision populations."""
+    import torch
+    from paper_2512_04997_gb300 import ledds
+    nx, ny, nz = 512, 512, 432
+    assert 19 * nx * ny * nz > 2 ** 31
+    w = W.Workload(name="big", nx=nx, ny=ny, nz=nz, periodic=(1, 1, 0))
+    w.params = W.base_params(tau=0.8, pattern=pattern)
+    w.u_wall[2, 0] = [-0.05, 0.0, 0.0]
+    w.u_wall[2, 1] = [0.05, 0.0, 0.0]
+    z = np.arange(nz, dtype=np.float64)
+    u = np.zeros((3, nz, ny, nx), dtype=np.float32)
+    u[0] = (-0.05 + 0.1 * (z + 0.5) / nz)[:, None, None]
+    u[1] = 0.01 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, None, :]
+    s = ledds.from_workload(w)
+    s.init_fluid(None, u.reshape(3, -1))
+    del u
+    g = np.random.default_rng(77)
+    N = nx * ny * nz
+    cells = np.concatenate([g.integers(0, N, 400), g.integers(N - 3 * nx * ny, N, 400)])
+    ci = torch.as_tensor(cells, device="cuda")
+    for step in range(2):   # both step forms of the AA pattern
+        f_pre = s.populations(0)[:, ci].cpu().numpy().astype(np.float64)
+        s.step(1)
+        f_post = s.populations(1)[:, ci].cpu().numpy().astype(np.float64)
+        err = 0.0
+        for j in range(len(cells)):
+            fstar, _, _ = oracle.cell_collide(f_pre[:, j], 0.8)
+            err = max(err, np.abs(fstar - f_post[:, j]).max())
+        assert err < 5e-7, (step, err)
+    st = s.status()
+    assert st["rc"] == 0
+    s.close()
+    torch.cuda.empty_cache()

@@ -24,7 +24,7 @@ BAD_PARAMS = [
     dict(voxel=2), dict(subdiv_n=0), dict(subdiv_n=17), dict(law=2), dict(n_sub=0),
     dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")), dict(collision=2),
     dict(collision=-1), dict(force_fp32=2), dict(orient=2), dict(orient=-1), dict(pattern=2),
-    dict(pattern=-1),
+    dict(pattern=-1), dict(index64=2),
 ]
 
 
@@ -41,7 +41,7 @@ def test_invalid_params_rejected(L, bad):
 BAD_DIMS = [
     dict(nx=-1, ny=8, nz=8), dict(nx=8, ny=0, nz=8), dict(nx=0, ny=0, nz=0, max_particles=0),
     dict(nx=8, ny=8, nz=8, max_particles=-1), dict(nx=8, ny=8, nz=8, cand_cap=65),
-    dict(nx=8, ny=8, nz=8, tile_cap=65), dict(nx=1024, ny=1024, nz=1024),
+    dict(nx=8, ny=8, nz=8, tile_cap=65), dict(nx=2048, ny=1024, nz=1024),
     dict(nx=0, ny=0, nz=0, max_particles=4, box_lo=(0, 0, 0), box_hi=(1, 0, 1)),
 ]
 
@@ -65,6 +65,20 @@ def test_workspace_grows_with_the_problem(L):
     assert a - c >= 2 * 19 * 32 ** 3 * 2      # FP16 storage halves the population bytes
     rc4, e = _size(L, ledds.make_dims(32, 32, 32, max_particles=10), ledds.make_params(dem_h=2.5, pattern="aa"))
     assert rc4 == 0 and a - e >= 19 * 32 ** 3 * 4   # the AA pattern keeps one population array
+
+
+def test_large_lattice_sizes(L):
+    """Node indices are 32-bit: 1024^3 nodes (19 N > 2^31 population elements, 64-bit
+    offsets in the kernel) are accepted and sized, 2^31 nodes are not; one population
+    array (AA) halves the population bytes."""
+    from paper_2512_04997_gb300 import ledds
+    p = ledds.make_params(dem_h=2.5)
+    d = ledds.make_dims(1024, 1024, 1024, max_particles=0)
+    rc, n_ab = _size(L, d, p)
+    assert rc == 0 and n_ab >= 2 * 19 * 1024 ** 3 * 4
+    rc, n_aa = _size(L, d, ledds.make_params(dem_h=2.5, pattern="aa", storage="f16"))
+    assert rc == 0 and n_aa < n_ab / 3.9
+    assert _size(L, ledds.make_dims(2048, 1024, 1024), p)[0] == ERR_INVALID
 
 
 def _batch_size(L, dims, params):
