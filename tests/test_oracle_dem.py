@@ -537,3 +537,30 @@ def test_pw_certificate_is_sound_bruteforce(oracle):
             ovl += 1
             assert not cert
     assert sep > 50 and ovl > 50
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_ellipsoid_wall_contact_closed_form(oracle, seed):
+    """An ellipsoid at rest pressed into the bottom wall by delta, at a random orientation:
+    with the linear law the wall pushes with k_n delta along the wall normal, at the
+    ellipsoid's support point towards the wall, r - E n/sqrt(n.E n) with E = R^T diag(s^2) R
+    (here built as a matrix), moved half the overlap back towards the wall; the torque is
+    that point's arm crossed with the force."""
+    g = np.random.default_rng(seed)
+    semi = g.uniform(0.6, 2.0, 3)
+    R = W.quaternion_to_triad(W.random_quaternions(g, 1)).reshape(3, 3)
+    E = R.T @ np.diag(semi ** 2) @ R
+    n = np.array([0.0, 0.0, 1.0])               # inward normal of the bottom wall z = -5
+    h = np.sqrt(n @ E @ n)
+    delta = 0.05
+    r = np.array([0.3, -0.2, -5.0 + h - delta])
+    kn = 1000.0
+    p = oracle.default_params(rho_f=0.0, dem_h=4.5, k_n=kn, k_t=kn * 2 / 7, friction=0.4)
+    s = dem(oracle, 1, p, periodic=(1, 1, 0))
+    s.set_particles([1], [semi.max()], [semi], [1.0], [r], triad=[R.ravel()])
+    s.contact_forces(0.1)
+    _, _, Fc, Mc = s.forces()
+    F = kn * delta * n
+    assert np.allclose(Fc[0], F, rtol=1e-12, atol=1e-12)
+    pc = r - E @ n / h + 0.5 * delta * n
+    assert np.allclose(Mc[0], np.cross(pc - r, F), rtol=1e-10, atol=1e-12)
