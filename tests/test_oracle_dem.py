@@ -541,11 +541,12 @@ def test_pw_certificate_is_sound_bruteforce(oracle):
 
 @pytest.mark.parametrize("seed", [5, 6, 7])
 def test_ellipsoid_wall_contact_closed_form(oracle, seed):
-    """An ellipsoid at rest pressed into the bottom wall by delta, at a random orientation:
-    with the linear law the wall pushes with k_n delta along the wall normal, at the
-    ellipsoid's support point towards the wall, r - E n/sqrt(n.E n) with E = R^T diag(s^2) R
-    (here built as a matrix), moved half the overlap back towards the wall; the torque is
-    that point's arm crossed with the force."""
+    """An ellipsoid pressed into the bottom wall by delta, at a random orientation: with the
+    linear law the wall pushes with k_n delta along the wall normal, at the ellipsoid's
+    support point towards the wall, r - E n/sqrt(n.E n) with E = R^T diag(s^2) R (here
+    built as a matrix), moved half the overlap back towards the wall; the torque is that
+    point's arm crossed with the force. Sliding along x adds a friction force against the
+    motion, whose torque needs the contact point exactly (also the half-overlap shift)."""
     g = np.random.default_rng(seed)
     semi = g.uniform(0.6, 2.0, 3)
     R = W.quaternion_to_triad(W.random_quaternions(g, 1)).reshape(3, 3)
@@ -564,3 +565,10 @@ def test_ellipsoid_wall_contact_closed_form(oracle, seed):
     assert np.allclose(Fc[0], F, rtol=1e-12, atol=1e-12)
     pc = r - E @ n / h + 0.5 * delta * n
     assert np.allclose(Mc[0], np.cross(pc - r, F), rtol=1e-10, atol=1e-12)
+    s = dem(oracle, 1, p, periodic=(1, 1, 0))
+    s.set_particles([1], [semi.max()], [semi], [1.0], [r], vel=[[0.02, 0.0, 0.0]], triad=[R.ravel()])
+    s.contact_forces(0.1)
+    _, _, Fc, Mc = s.forces()
+    assert Fc[0][2] == pytest.approx(kn * delta, rel=1e-12)
+    assert Fc[0][0] < 0.0 and abs(Fc[0][0]) > 1e-4 * kn * delta      # friction against the motion
+    assert np.allclose(Mc[0], np.cross(pc - r, Fc[0]), rtol=1e-10, atol=1e-12)
