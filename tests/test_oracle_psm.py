@@ -19,18 +19,22 @@ def _random_cell(g, oracle):
     return oracle.equilibrium(rho, u) + 1e-3 * g.uniform(-1, 1, 19)
 
 
-def test_psm_zero_weight_is_bgk(oracle):
-    """B = 0: the PSM operator reverts to the plain collision (Sec. 2.4)."""
+@pytest.mark.parametrize("collision", [0, 1])
+def test_psm_zero_weight_is_bgk(oracle, collision):
+    """B = 0: the PSM operator reverts to the plain collision (Sec. 2.4), BGK or TRT."""
     g = W.rng(200)
     f = _random_cell(g, oracle)
-    plain, _, _ = oracle.cell_collide(f, 0.8)
-    blended, F, M = oracle.cell_collide(f, 0.8, B=[0.0], uk=[[0.01, 0.02, 0.0]], arm=[[1, 0, 0]])
+    plain, _, _ = oracle.cell_collide(f, 0.8, collision=collision)
+    blended, F, M = oracle.cell_collide(f, 0.8, B=[0.0], uk=[[0.01, 0.02, 0.0]], arm=[[1, 0, 0]],
+                                        collision=collision)
     assert np.array_equal(plain, blended)
     assert np.all(F == 0) and np.all(M == 0)
 
 
-def test_psm_full_solid_limit(oracle):
-    """B = 1: f*_i = f_ibar - f^eq_ibar(rho,u) + f^eq_i(rho,u_k), whatever tau is."""
+@pytest.mark.parametrize("collision", [0, 1])
+def test_psm_full_solid_limit(oracle, collision):
+    """B = 1: f*_i = f_ibar - f^eq_ibar(rho,u) + f^eq_i(rho,u_k), whatever tau is and
+    whichever fluid collision (BGK or TRT: its weight 1 - B_tot vanishes)."""
     g = W.rng(201)
     f = _random_cell(g, oracle)
     c, _, opp = oracle.lattice_tables()
@@ -39,13 +43,14 @@ def test_psm_full_solid_limit(oracle):
     uk = np.array([0.02, -0.01, 0.03])
     expect = f[opp] - oracle.equilibrium(rho, u)[opp] + oracle.equilibrium(rho, uk)
     for tau in (0.6, 0.8, 1.5):
-        got, _, _ = oracle.cell_collide(f, tau, B=[1.0], uk=[uk], arm=[[0, 0, 0]])
+        got, _, _ = oracle.cell_collide(f, tau, B=[1.0], uk=[uk], arm=[[0, 0, 0]], collision=collision)
         assert np.allclose(got, expect, rtol=0, atol=1e-15)
 
 
-def test_psm_conserves_mass_and_momentum(oracle):
+@pytest.mark.parametrize("collision", [0, 1])
+def test_psm_conserves_mass_and_momentum(oracle, collision):
     """Sum f* = sum f, and the momentum the fluid gains is exactly minus the force on the
-    solids of Eq. (forceSF) (action-reaction between fluid and particles)."""
+    solids of Eq. (forceSF) (action-reaction between fluid and particles), BGK or TRT."""
     g = W.rng(202)
     c, _, _ = oracle.lattice_tables()
     for _ in range(20):
@@ -53,7 +58,7 @@ def test_psm_conserves_mass_and_momentum(oracle):
         B = g.uniform(0, 1, 2)
         uk = 0.05 * g.uniform(-1, 1, (2, 3))
         arm = g.uniform(-3, 3, (2, 3))
-        fs, F, M = oracle.cell_collide(f, g.uniform(0.55, 1.5), B=B, uk=uk, arm=arm)
+        fs, F, M = oracle.cell_collide(f, g.uniform(0.55, 1.5), B=B, uk=uk, arm=arm, collision=collision)
         assert abs(fs.sum() - f.sum()) < 1e-15
         dp = (fs - f) @ c
         assert np.allclose(dp + F.sum(0), 0.0, atol=1e-16)
