@@ -14,6 +14,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------------------ */
 /* D3Q19 lattice (Sec. 2.3; weights are the textbook ones the paper refers to).          */
@@ -29,6 +32,16 @@ static const int CV[19][3] = {
 
 static double TW(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 static int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+/* Threads the lattice update runs on: 1 in the parity build, the OpenMP team size in the
+ * build used for the timed CPU baseline. */
+int or_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 void or_lattice_tables(int c[57], double w[19], int opp[19]) {
     for (int i = 0; i < 19; ++i) {
@@ -351,7 +364,7 @@ double or_beta_distance(const double rel[3], double radius) {
 int or_subdiv_count(const double rel[3], int shape, double radius, const double semi[3],
                     const double triad[9], int n) {
     float px = (float)rel[0], py = (float)rel[1], pz = (float)rel[2];
-    float m[3][3];
+    float m[3][3] = {{0.0f}};
     float R2 = (float)(radius * radius);
     if (shape == OR_ELLIPSOID)
         for (int j = 0; j < 3; ++j)
@@ -575,6 +588,11 @@ void or_lbm_psm_step(or_sim* s) {
         for (int a = 0; a < 3; ++a) s->Fh[3 * k + a] = s->Mh[3 * k + a] = 0.0;
     long long over = 0;
     int n3[3] = {s->nx, s->ny, s->nz};
+    /* The timed CPU baseline builds this file a second time with OpenMP: planes are
+     * collided and streamed in parallel (every streamed slot has exactly one source), and
+     * the per-particle sums become atomic additions (their order then varies, so that
+     * build is used for timing only; the parity build has no OpenMP and runs in order). */
+#pragma omp parallel for schedule(static) reduction(+ : over)
     for (int z = 0; z < s->nz; ++z)
         for (int y = 0; y < s->ny; ++y)
             for (int x = 0; x < s->nx; ++x) {
@@ -601,7 +619,9 @@ void or_lbm_psm_step(or_sim* s) {
                 for (int m = 0; m < ns; ++m) {
                     int k = cs[c].id[m];
                     for (int a = 0; a < 3; ++a) {
+#pragma omp atomic
                         s->Fh[3 * k + a] += Fk[3 * m + a];
+#pragma omp atomic
                         s->Mh[3 * k + a] += Mk[3 * m + a];
                     }
                 }
@@ -976,7 +996,10 @@ static int line_hit(const double r[3], const double R[9], const double s[3],
 }
 
 /* Perram-Wertheim separation certificate (Perram & Wertheim, J. Comput. Phys. 58, 409,
- * 1985). With A^-1 = R^T diag(s^2) R for each ellipsoid (R rows = body axes) and d the
+ * 1985). Not part of the oracle's step (the method decides ellipsoid contacts by the
+ * common-normal iteration alone); it states the screening test that the CUDA contact
+ * kernel runs before its iteration, so that the tests can list the pairs where the
+ * screened and unscreened decisions differ. With A^-1 = R^T diag(s^2) R for each ellipsoid (R rows = body axes) and d the
  * centre difference, F(l) = l (1 - l) d^T C(l)^-1 d, C(l) = (1 - l) A_i^-1 + l A_j^-1;
  * the ellipsoids overlap if and only if max over l in [0, 1] of F is at most 1, so any l
  * with F(l) > 1 proves that they are disjoint. */
@@ -1152,7 +1175,8 @@ static int sphere_geom(const or_sim* s, int i, int j, contact_geom* g) {
     return 1;
 }
 
-/* Pair involving an ellipsoid: bounding-sphere test, then the common-normal iteration. */
+/* Pair involving an ellipsoid: bounding-sphere test, then the common-normal iteration
+ * (no other screening: the method as Sec. 2.1 states it). */
 static int ellipsoid_geom(or_sim* s, int i, int j, contact_geom* g) {
     double d[3], rj_img[3];
     for (int a = 0; a < 3; ++a) {
@@ -1160,34 +1184,9 @@ static int ellipsoid_geom(or_sim* s, int i, int j, contact_geom* g) {
         rj_img[a] = s->pos[3 * i + a] - d[a];
     }
     double dist = vnorm(d);
+    /* Sec. 2.1: bounding spheres (radius = largest semi-axis) select the pairs that get
+     * the common-normal iteration; the iteration alone decides the contact. */
     if (!((s->bound[i] + s->bound[j]) - dist > 0.0)) return 0;
-    /* Separating plane across the centre line (reading: an exact pre-test, Sec. 2.1 does not
-     * say how pairs are screened): the support of an ellipsoid along a unit vector n is
-     * |diag(s) R n| (R rows = body axes). If the supports of i and j along the centre line
-     * do not reach across the centre distance, the plane between them separates the two and
-     * there is no contact; the iteration runs for the other pairs only. */
-    {
-        double n[3], h[2];
-        for (int a = 0; a < 3; ++a) n[a] = d[a] / dist;
-        for (int k = 0; k < 2; ++k) {
-            const int q = k == 0 ? i : j;
-            const double* R = s->triad + 9 * q;
-            const double* sm = s->semi + 3 * q;
-            double t = 0.0;
-            for (int m = 0; m < 3; ++m) {
-                double b = R[3 * m] * n[0] + R[3 * m + 1] * n[1] + R[3 * m + 2] * n[2];
-                double v = sm[m] * b;
-                t = t + v * v;
-            }
-            h[k] = sqrt(t);
-        }
-        if ((h[0] + h[1]) < dist * (1.0 - 1e-12)) return 0;
-    }
-    /* Perram-Wertheim certificate (same reading: a second exact pre-test): pairs proven
-     * disjoint skip the iteration. */
-    if (or_pw_separated(s->pos + 3 * i, s->triad + 9 * i, s->semi + 3 * i, rj_img, s->triad + 9 * j,
-                        s->semi + 3 * j))
-        return 0;
     double en[3], cp[3], rho_i, rho_j, delta;
     int iters;
     int rc = or_ellipsoid_contact(s->pos + 3 * i, s->triad + 9 * i, s->semi + 3 * i, rj_img,

@@ -372,8 +372,8 @@ def test_eccentric_ellipsoids_energy(oracle):
 
 
 def test_ellipsoid_contact_decision_matches_perram_wertheim(oracle):
-    """The contact decision for ellipsoid pairs (bounding spheres, the separating-plane
-    pre-test, then the common-normal iteration) agrees with the exact Perram-Wertheim
+    """The contact decision for ellipsoid pairs (bounding spheres, then the common-normal
+    iteration) agrees with the exact Perram-Wertheim
     overlap criterion on random pairs at random orientations; pairs within 2 % of
     tangency (contact function within [0.98, 1.02]) are left out."""
     g = np.random.default_rng(91)
