@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="time only the batched 64-simulation ensemble (one JSON line)")
+    ap.add_argument("--long", type=int, default=500,
+                    help="steps of each of the three runs whose median the line also reports")
     ap.add_argument("--edge", type=int, default=256,
                     help="lattice edge of the Couette workload (spheres scaled to keep the "
                          "solid fraction); smaller than 256 only for profiler captures")
@@ -370,24 +372,31 @@ def rheology_measure(device, stream, phis=(0.0, 0.1, 0.2, 0.3), steps=20000, eve
             "seconds": time.perf_counter() - t0, "points": rows}
 
 
-def oracle_sample(steps, keep=False):
-    """The oracle (single-threaded FP64 C) on a bounded sample of the workload: a 256x256x32
+SLAB = dict(nx=256, ny=256, nz=32, n_particles=500)
+
+
+def oracle_sample(steps, keep=False, parallel=True):
+    """The oracle (FP64 C, as it stands) on a bounded sample of the workload: a 256x256x32
     slab of the same Couette suspension (same solid fraction, 500 spheres), `steps` steps
-    after one untimed step; with keep, also the oracle simulation and the workload."""
+    after one untimed step. parallel: its OpenMP build on every host core (the timed CPU
+    baseline), else the serial parity build. keep: also the oracle simulation and the
+    workload (the serial build, for the error check)."""
     from oracle import oracle as O
     from paper_2512_04997_gb300 import workloads as W
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from _helpers import oracle_from_workload
-    w = W.couette_suspension(nx=256, ny=256, nz=32, n_particles=500)
-    o = oracle_from_workload(O, w)
+    w = W.couette_suspension(**SLAB)
+    par = parallel and not keep
+    o = O.from_workload(w, parallel=par)
     o.step(1)   # warm
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
     mlups = w.ncell * steps / dt / 1e6
-    res = {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+    cores = O.threads(par)
+    res = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "host_cores": os.cpu_count(),
            "sample": f"{steps} coupled steps of a 256x256x32 slab of the workload "
-                     f"(500 spheres, same solid fraction), FP64, single thread",
+                     f"({w.ncell} cells, 500 spheres, same solid fraction), FP64, "
+                     + (f"OpenMP build of the oracle source, {cores} threads" if par else "single thread"),
            "seconds": dt}
     return (res, o, w) if keep else res
 
@@ -417,16 +426,22 @@ def run_reference(args):
         return
     steps = max(1, min(args.steps, 8))
     warm = max(0, min(args.warmup, 1))
-    from oracle import oracle as O  # noqa: F401  (built on first use)
     if warm:
         oracle_sample(1)
     res = oracle_sample(steps)
+    config = main_config(main_workload(args), args.storage, args.gpus)
+    # the timed sample is a slab of the workload: its own cell count
+    config["cells"] = SLAB["nx"] * SLAB["ny"] * SLAB["nz"]
+    config["particles"] = SLAB["n_particles"]
+    config.pop("l2", None)
+    config["timed_sample"] = (f"{SLAB['nx']}x{SLAB['ny']}x{SLAB['nz']} slab of the "
+                              f"{config['workload']} workload, same solid fraction")
     line = {"metric": METRIC, "value": res["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * res["seconds"] / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": main_config(main_workload(args), args.storage, args.gpus),
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"],
+            "config": config,
+            "cpu_baseline": {"kind": "oracle", "cores": res["cores"], "sample": res["sample"],
                              "value": res["value"], "unit": "MLUPS"},
             "e2e": {"value": res["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -478,6 +493,22 @@ def main():
     ms = max_over_ranks(e0.elapsed_time(e1), dist)
     value = N * args.steps * world / (ms * 1e-3) / 1e6
     st = sim.status()
+    # the protocol's longer form: three runs of LONG steps each, their median
+    long_runs = []
+    for _ in range(3 if args.long > 0 else 0):
+        barrier()
+        e0.record(stream)
+        sim.step(args.long)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        long_runs.append(max_over_ranks(e0.elapsed_time(e1), dist))
+    median3 = None
+    if long_runs:
+        lm = float(np.median(long_runs))
+        median3 = {"steps_per_run": args.long, "runs_ms": long_runs,
+                   "value": N * args.long * world / (lm * 1e-3) / 1e6, "unit": "MLUPS",
+                   "ms_per_step": lm / args.long}
 
     # profiled pass: CUDA events around every stage of each step (eager launches)
     sim.set_profiling(True)
@@ -559,8 +590,9 @@ def main():
     cpu = None
     oracle_err = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu, o, ws = oracle_sample(2, keep=True)
+        cpu = oracle_sample(4)
         cpu.pop("seconds", None)
+        _, o, ws = oracle_sample(2, keep=True)
         # the CUDA path on the same slab and steps: its error against the oracle
         gs = ledds.from_workload(ws, device=f"cuda:{local}")
         gs.step(3)
@@ -582,6 +614,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": main_config(w, args.storage, world),
+                "median_of_3": median3,
                 "roofline": roofline, "cpu_baseline": cpu, "error_vs_oracle": oracle_err, "e2e": e2e,
                 "gpu_launches": st["launches_per_step"] * args.steps,
                 "clocks": clk, "stages_ms_per_step": {k: v / psteps for k, v in zip(STAGES, stage_ms)},

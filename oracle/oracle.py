@@ -42,13 +42,14 @@ class Params(C.Structure):
     ]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(parallel=False):
+    """The parity build (serial, in order), or with parallel=True the OpenMP build that
+    times the CPU baseline."""
+    if parallel not in _libs:
+        path = _build.build(parallel=parallel)
         L = C.CDLL(path)
         dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
         ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -91,8 +92,15 @@ def lib():
         L.or_ellipsoid_contact.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_double,
                                            dp, dp, dp, dp, dp, ip]
         L.or_status.argtypes = [C.c_void_p, lp]
-        _lib = L
-    return _lib
+        L.or_threads.restype = C.c_int
+        L.or_threads.argtypes = []
+        _libs[parallel] = L
+    return _libs[parallel]
+
+
+def threads(parallel=False):
+    """Threads the oracle's lattice update uses in that build."""
+    return int(lib(parallel).or_threads())
 
 
 def default_params(**kw) -> Params:
@@ -131,8 +139,8 @@ class Sim:
     """One oracle simulation (lattice and/or particles)."""
 
     def __init__(self, nx=0, ny=0, nz=0, periodic=(1, 1, 1), u_wall=None, params=None,
-                 box_lo=(0, 0, 0), box_hi=(1, 1, 1), max_particles=1):
-        L = lib()
+                 box_lo=(0, 0, 0), box_hi=(1, 1, 1), max_particles=1, parallel=False):
+        self._L = L = lib(parallel)
         self.nx, self.ny, self.nz = nx, ny, nz
         self.ncell = nx * ny * nz
         self.params = params if params is not None else default_params()
@@ -144,29 +152,29 @@ class Sim:
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     # fluid -------------------------------------------------------------------------
     def init_equilibrium(self, rho=None, u=None):
         r = None if rho is None else _d(rho, self.ncell)
         v = None if u is None else _d(u, 3 * self.ncell)
-        lib().or_init_equilibrium(self._h, None if r is None else r.ctypes.data,
+        self._L.or_init_equilibrium(self._h, None if r is None else r.ctypes.data,
                                   None if v is None else v.ctypes.data)
         self._keep = (r, v)
 
     def set_populations(self, f):
-        lib().or_set_populations(self._h, _d(f, 19 * self.ncell))
+        self._L.or_set_populations(self._h, _d(f, 19 * self.ncell))
 
     def populations(self):
         out = np.zeros(19 * self.ncell)
-        lib().or_get_populations(self._h, out)
+        self._L.or_get_populations(self._h, out)
         return out.reshape(19, self.ncell)
 
     def moments(self):
         rho = np.zeros(self.ncell)
         u = np.zeros(3 * self.ncell)
-        lib().or_moments(self._h, rho, u)
+        self._L.or_moments(self._h, rho, u)
         return rho, u.reshape(3, self.ncell)
 
     # particles ---------------------------------------------------------------------
@@ -175,7 +183,7 @@ class Sim:
         z3 = np.zeros((n, 3))
         if triad is None:
             triad = np.tile(np.eye(3).reshape(1, 9), (n, 1))
-        rc = lib().or_set_particles(self._h, n, np.ascontiguousarray(shape, dtype=np.int32),
+        rc = self._L.or_set_particles(self._h, n, np.ascontiguousarray(shape, dtype=np.int32),
                                     _d(radius, n), _d(semi, 3 * n), _d(density, n),
                                     _d(pos, 3 * n), _d(z3 if vel is None else vel, 3 * n),
                                     _d(z3 if omg is None else omg, 3 * n), _d(triad, 9 * n))
@@ -186,57 +194,57 @@ class Sim:
     def particles(self):
         n = self.n
         pos, vel, omg, tri = np.zeros(3 * n), np.zeros(3 * n), np.zeros(3 * n), np.zeros(9 * n)
-        lib().or_get_particles(self._h, pos, vel, omg, tri)
+        self._L.or_get_particles(self._h, pos, vel, omg, tri)
         return pos.reshape(n, 3), vel.reshape(n, 3), omg.reshape(n, 3), tri.reshape(n, 9)
 
     def forces(self):
         n = self.n
         a = [np.zeros(3 * n) for _ in range(4)]
-        lib().or_get_forces(self._h, *a)
+        self._L.or_get_forces(self._h, *a)
         return tuple(x.reshape(n, 3) for x in a)  # Fh, Mh, Fc, Mc
 
     def accel(self):
         n = self.n
         a, b = np.zeros(3 * n), np.zeros(3 * n)
-        lib().or_get_accel(self._h, a, b)
+        self._L.or_get_accel(self._h, a, b)
         return a.reshape(n, 3), b.reshape(n, 3)
 
     # stepping ----------------------------------------------------------------------
     def step(self, nsteps=1):
-        lib().or_step(self._h, int(nsteps))
+        self._L.or_step(self._h, int(nsteps))
 
     def lbm_psm_step(self):
-        lib().or_lbm_psm_step(self._h)
+        self._L.or_lbm_psm_step(self._h)
 
     def contact_forces(self, dt):
-        lib().or_contact_forces(self._h, float(dt))
+        self._L.or_contact_forces(self._h, float(dt))
 
     def voxelize(self):
         beta = np.zeros(2 * self.ncell)
         ids = np.zeros(2 * self.ncell, dtype=np.int32)
         ns = np.zeros(self.ncell, dtype=np.int32)
-        lib().or_voxelize(self._h, beta, ids, ns)
+        self._L.or_voxelize(self._h, beta, ids, ns)
         return beta.reshape(self.ncell, 2), ids.reshape(self.ncell, 2), ns
 
     def cell_keys(self):
         keys = np.zeros(max(self.n, 1), dtype=np.uint32)
         ids = np.zeros(max(self.n, 1), dtype=np.int32)
         g = np.zeros(3, dtype=np.int32)
-        lib().or_cell_keys(self._h, keys, ids, g)
+        self._L.or_cell_keys(self._h, keys, ids, g)
         return keys[: self.n], ids[: self.n], tuple(int(x) for x in g)
 
     def contacts(self):
         cap = max(16, 16 * self.n)
         while True:
             out = np.zeros(cap, dtype=np.int64)
-            nc = lib().or_contacts(self._h, out, cap)
+            nc = self._L.or_contacts(self._h, out, cap)
             if nc <= cap:
                 return out[:nc]
             cap = nc
 
     def status(self):
         out = np.zeros(4, dtype=np.int64)
-        lib().or_status(self._h, out)
+        self._L.or_status(self._h, out)
         return {"solids_overflow": int(out[0]), "ell_nonconverged": int(out[1]),
                 "steps": int(out[2]), "ncontacts": int(out[3])}
 
@@ -319,3 +327,32 @@ def ellipsoid_contact(ri, Ri, si, rj, Rj, sj, max_iter=60, tol=1e-6):
                                     rho_i, rho_j, it)
     return {"rc": rc, "delta": float(delta[0]), "en": en, "cp": cp,
             "rho_i": float(rho_i[0]), "rho_j": float(rho_j[0]), "iters": int(it[0])}
+
+
+_VOX = {"distance": 0, "subdiv": 1}
+_LAWS = {"linear": 0, "hertz": 1}
+
+
+def from_workload(w, populations=None, parallel=False):
+    """Oracle simulation of a seeded workload description (``workloads.Workload``: lattice,
+    walls, parameters and particles), the same inputs the CUDA path receives. parallel:
+    the OpenMP timing build."""
+    p = dict(w.params)
+    op = default_params(tau=p["tau"], fluid_force=p["fluid_force"], voxel=_VOX[p["voxel"]],
+                        subdiv_n=p["subdiv_n"], law=_LAWS[p["law"]], n_sub=p["n_sub"],
+                        rho_f=p["rho_f"], gravity=p["gravity"], k_n=p["k_n"], k_t=p["k_t"],
+                        young=p["young"], poisson=p["poisson"], restitution=p["restitution"],
+                        friction=p["friction"], dem_h=p["dem_h"],
+                        ell_max_iter=p["ell_max_iter"], ell_tol=p["ell_tol"],
+                        collision={"bgk": 0, "trt": 1}[p.get("collision", "bgk")],
+                        orient={"triad": 0, "quat": 1}[p.get("orient", "triad")])
+    s = Sim(w.nx, w.ny, w.nz, periodic=w.periodic, u_wall=w.u_wall, params=op,
+            box_lo=w.box_lo, box_hi=w.box_hi, max_particles=max(w.n, 1), parallel=parallel)
+    if w.ncell:
+        if populations is not None:
+            s.set_populations(populations)
+        elif w.init_u is not None:
+            s.init_equilibrium(None, w.init_u)
+    if w.n:
+        s.set_particles(w.shape, w.radius, w.semi, w.density, w.pos, w.vel, w.omg, w.triad)
+    return s

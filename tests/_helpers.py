@@ -4,30 +4,10 @@ import numpy as np
 
 from paper_2512_04997_gb300 import workloads as W
 
-VOX = {"distance": 0, "subdiv": 1}
-LAWS = {"linear": 0, "hertz": 1}
-
 
 def oracle_from_workload(O, w, populations=None):
-    p = dict(w.params)
-    op = O.default_params(tau=p["tau"], fluid_force=p["fluid_force"], voxel=VOX[p["voxel"]],
-                          subdiv_n=p["subdiv_n"], law=LAWS[p["law"]], n_sub=p["n_sub"],
-                          rho_f=p["rho_f"], gravity=p["gravity"], k_n=p["k_n"], k_t=p["k_t"],
-                          young=p["young"], poisson=p["poisson"], restitution=p["restitution"],
-                          friction=p["friction"], dem_h=p["dem_h"],
-                          ell_max_iter=p["ell_max_iter"], ell_tol=p["ell_tol"],
-                          collision={"bgk": 0, "trt": 1}[p.get("collision", "bgk")],
-                          orient={"triad": 0, "quat": 1}[p.get("orient", "triad")])
-    s = O.Sim(w.nx, w.ny, w.nz, periodic=w.periodic, u_wall=w.u_wall, params=op,
-              box_lo=w.box_lo, box_hi=w.box_hi, max_particles=max(w.n, 1))
-    if w.ncell:
-        if populations is not None:
-            s.set_populations(populations)
-        elif w.init_u is not None:
-            s.init_equilibrium(None, w.init_u)
-    if w.n:
-        s.set_particles(w.shape, w.radius, w.semi, w.density, w.pos, w.vel, w.omg, w.triad)
-    return s
+    """The oracle simulation of workload w (O: the oracle module)."""
+    return O.from_workload(w, populations=populations)
 
 
 def gpu_from_workload(w, populations=None, **over):
