@@ -163,23 +163,107 @@ __global__ void k_keys(DemArgs A, int pst) {
 __global__ void k_scatter(DemArgs A) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= A.P.n) return;
-    A.sorted[A.cell_start[A.keys[k]] + A.rank[k]] = k;
+    A.sorted_tmp[A.cell_start[A.keys[k]] + A.rank[k]] = k;
 }
 
-// ids inside each cell in ascending order, so the sorted (key, id) list is unique
-__global__ void k_segsort(DemArgs A) {
+// ------------------------------------------------------------------------------------
+// Ids in ascending order inside each cell, so that the sorted (key, id) list is unique.
+// The scatter above places a cell's ids in atomic-arrival order; each cell's segment is
+// then ordered from that copy (tmp) into `sorted`: a cell of at most SEG_SMALL ids by one
+// thread (insertion sort), a larger one by a CTA that marks its ids in a bitmap over the
+// id range (windows of SEG_WIN ids in shared memory) and writes the set bits in order;
+// O(ids + n / 32) per large cell, so even a grid of one cell (or every particle in
+// cell 0 after a blow-up) is ordered in bounded time.
+// ------------------------------------------------------------------------------------
+constexpr int SEG_SMALL = 32;
+constexpr int SEG_WIN = 1 << 18;
+constexpr int SEG_WORDS = SEG_WIN / 32;
+constexpr int SEG_THREADS = 1024;
+constexpr int SEG_PER_THREAD = SEG_WORDS / SEG_THREADS;
+constexpr int SEG_LARGE_CTAS = 64;
+
+// big[0] counts the cells left to the large-cell kernel, listed in big[1 ..]
+__global__ void k_segsort_small(const uint32_t* start, int G, const int* tmp, int* sorted, int* big) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= A.G) return;
-    int b = (int)A.cell_start[c], e = (int)A.cell_start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = A.sorted[i];
+    if (c >= G) return;
+    int b = (int)start[c], e = (int)start[c + 1];
+    if (e - b > SEG_SMALL) {
+        big[1 + atomicAdd(&big[0], 1)] = c;
+        return;
+    }
+    for (int i = b; i < e; ++i) {
+        int v = tmp[i];
         int j = i - 1;
-        while (j >= b && A.sorted[j] > v) {
-            A.sorted[j + 1] = A.sorted[j];
+        while (j >= b && sorted[j] > v) {
+            sorted[j + 1] = sorted[j];
             --j;
         }
-        A.sorted[j + 1] = v;
+        sorted[j + 1] = v;
     }
+}
+
+__global__ void __launch_bounds__(SEG_THREADS) k_segsort_large(const uint32_t* start, int n, const int* tmp,
+                                                               int* sorted, const int* big) {
+    __shared__ uint32_t bits[SEG_WORDS];
+    __shared__ int warp_sum[SEG_THREADS / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int nbig = big[0];
+    for (int q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const int c = big[1 + q];
+        const int b = (int)start[c], e = (int)start[c + 1];
+        int out = b;
+        for (int w0 = 0; w0 < n; w0 += SEG_WIN) {
+            for (int i = t; i < SEG_WORDS; i += SEG_THREADS) bits[i] = 0u;
+            __syncthreads();
+            for (int i = b + t; i < e; i += SEG_THREADS) {
+                const unsigned r = (unsigned)(tmp[i] - w0);
+                if (r < (unsigned)SEG_WIN) atomicOr(&bits[r >> 5], 1u << (r & 31u));
+            }
+            __syncthreads();
+            // thread t owns words t*SEG_PER_THREAD ..: exclusive scan of their bit counts
+            uint32_t wv[SEG_PER_THREAD];
+            int cnt = 0;
+            for (int k = 0; k < SEG_PER_THREAD; ++k) {
+                wv[k] = bits[t * SEG_PER_THREAD + k];
+                cnt += __popc(wv[k]);
+            }
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (lane == 31) warp_sum[warp] = incl;
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < SEG_THREADS / 32; ++w) {
+                const int v = warp_sum[w];
+                before += w < warp ? v : 0;
+                total += v;
+            }
+            int pos = out + before + incl - cnt;
+            for (int k = 0; k < SEG_PER_THREAD; ++k) {
+                uint32_t m = wv[k];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1u;
+                    sorted[pos++] = w0 + (t * SEG_PER_THREAD + k) * 32 + bit;
+                }
+            }
+            out += total;
+            __syncthreads();  // bits and warp_sum are reused
+        }
+    }
+}
+
+// Orders every cell segment of the counting sort: tmp (scatter order) -> sorted. big
+// holds 2 + n / SEG_SMALL ints; its counter is cleared here.
+cudaError_t launch_segsort(const uint32_t* start, int G, int n, const int* tmp, int* sorted, int* big,
+                           cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(big, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_segsort_small<<<(G + 127) / 128, 128, 0, s>>>(start, G, tmp, sorted, big);
+    k_segsort_large<<<SEG_LARGE_CTAS, SEG_THREADS, 0, s>>>(start, n, tmp, sorted, big);
+    return cudaGetLastError();
 }
 
 // Candidate list of particle i (ascending ids) and its tangential history carried over
@@ -1662,9 +1746,10 @@ cudaError_t launch_rebuild(const DemArgs& A, int ob, int nb, int pst, uint32_t* 
     e = launch_scan(A.cell_count, A.G, A.cell_start, scan_partial, s);
     if (e != cudaSuccess) return e;
     k_scatter<<<nblk(n, 128), 128, 0, s>>>(A);
-    k_segsort<<<nblk(A.G, 128), 128, 0, s>>>(A);
+    e = launch_segsort(A.cell_start, A.G, n, A.sorted_tmp, A.sorted, A.seg_big, s);
+    if (e != cudaSuccess) return e;
     k_candidates<<<nblk(n, CAND_WARPS), 32 * CAND_WARPS, 0, s>>>(A, ob, nb, pst);
-    *launches += 7;
+    *launches += 8;
     if (A.pair_once) {  // canonical pair list of the new candidate lists
         k_cpair_count<<<nblk(n, 128), 128, 0, s>>>(A, nb, A.cp_cnt);
         e = launch_scan(A.cp_cnt, n, A.cp_off, scan_partial, s);

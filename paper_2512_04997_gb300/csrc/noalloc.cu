@@ -2,11 +2,13 @@
 // device allocation, for callers that cannot allocate device memory themselves (see
 // ledds_cell_list_noalloc in include/ledds.h).
 //
-// The scratch the counting sort needs (per-cell counts and starts, scan partials and
-// per-particle ranks) lives in one file-scope __device__ array of fixed size. Every GPU
-// that loads the library holds it until the process exits. Host code cannot use the
-// array's name as a device address: the address is looked up once per device with
+// The scratch the counting sort needs (per-cell counts and starts, scan partials,
+// per-particle ranks, the ids in scatter order and the list of large cells) lives in one
+// file-scope __device__ array of fixed size (about 4.2 MB). Every GPU that loads the
+// library holds it until the process exits. Host code cannot use the array's name as a
+// device address: the address is looked up once per CUDA context with
 // cudaGetSymbolAddress and passed to the kernels.
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include <mutex>
@@ -15,6 +17,8 @@
 
 namespace ledds {
 cudaError_t launch_scan(const uint32_t* in, int n, uint32_t* out, uint32_t* partial, cudaStream_t s);
+cudaError_t launch_segsort(const uint32_t* start, int G, int n, const int* tmp, int* sorted, int* big,
+                           cudaStream_t s);
 }
 using namespace ledds;
 
@@ -23,26 +27,55 @@ namespace {
 constexpr int kMaxCells = 1 << 18;      // grid cells
 constexpr int kMaxParticles = 1 << 18;  // particles
 constexpr int kPartials = 4096;         // scan block partials
-// counts [cells+1] | starts [cells+1] | partials [4096] | ranks [particles]
-constexpr size_t kWords = 2 * ((size_t)kMaxCells + 1) + kPartials + kMaxParticles;
+// counts [cells+1] | starts [cells+1] | partials [4096] | ranks [particles] |
+// ids in scatter order [particles] | large-cell list [particles/32 + 2]
+constexpr size_t kWords = 2 * ((size_t)kMaxCells + 1) + kPartials + 2 * (size_t)kMaxParticles +
+                          kMaxParticles / 32 + 2;
 
 __device__ __align__(256) uint32_t g_scratch[kWords];
 
-constexpr int kMaxDevices = 64;
+// The scratch address per CUDA context: a context (and the library's module in it) can be
+// destroyed and made again on the same device (cudaDeviceReset, or the primary context
+// released and retained), and the array then has a new address.
+constexpr int kSlots = 64;
 std::mutex g_mu;
-uint32_t* g_addr[kMaxDevices] = {nullptr};
+CUcontext g_ctx[kSlots] = {nullptr};
+uint32_t* g_addr[kSlots] = {nullptr};
+PFN_cuCtxGetCurrent_v4000 g_get_ctx = nullptr;
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array in the current context.
 int scratch_address(uint32_t** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LEDDS_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return LEDDS_ERR_CUDA;
-        g_addr[dev] = static_cast<uint32_t*>(p);
+    if (!g_get_ctx) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return LEDDS_ERR_CUDA;
+        g_get_ctx = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(fn);
     }
-    *out = g_addr[dev];
+    CUcontext ctx = nullptr;
+    void* p = nullptr;
+    if (g_get_ctx(&ctx) != CUDA_SUCCESS) return LEDDS_ERR_CUDA;
+    if (!ctx) {
+        // no context is current yet: the symbol lookup makes the device's primary one current
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return LEDDS_ERR_CUDA;
+        if (g_get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return LEDDS_ERR_CUDA;
+    }
+    int slot = -1;
+    for (int i = 0; i < kSlots && slot < 0; ++i)
+        if (g_ctx[i] == ctx) slot = i;
+    if (slot < 0 || !g_addr[slot]) {
+        if (!p && (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p)) return LEDDS_ERR_CUDA;
+        if (slot < 0) {
+            for (int i = 0; i < kSlots && slot < 0; ++i)
+                if (!g_ctx[i]) slot = i;
+            if (slot < 0) slot = (int)(reinterpret_cast<uintptr_t>(ctx) % kSlots);  // table full: reuse
+        }
+        g_ctx[slot] = ctx;
+        g_addr[slot] = static_cast<uint32_t*>(p);
+    }
+    *out = g_addr[slot];
     return LEDDS_OK;
 }
 
@@ -78,22 +111,6 @@ __global__ void k_na_scatter(const uint32_t* keys, const uint32_t* rank, const u
     sorted[start[keys[k]] + rank[k]] = k;
 }
 
-// ids in ascending order inside each cell, so the (key, id) order is unique
-__global__ void k_na_segsort(const uint32_t* start, int G, int* sorted) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= G) return;
-    int b = (int)start[c], e = (int)start[c + 1];
-    for (int i = b + 1; i < e; ++i) {
-        int v = sorted[i];
-        int j = i - 1;
-        while (j >= b && sorted[j] > v) {
-            sorted[j + 1] = sorted[j];
-            --j;
-        }
-        sorted[j + 1] = v;
-    }
-}
-
 }  // namespace
 
 extern "C" int ledds_cell_list_noalloc(const double* d_pos, int n, const double box_lo[3],
@@ -124,12 +141,15 @@ extern "C" int ledds_cell_list_noalloc(const double* d_pos, int n, const double 
     uint32_t* start = count + (kMaxCells + 1);
     uint32_t* partial = start + (kMaxCells + 1);
     uint32_t* rank = partial + kPartials;
+    int* tmp = reinterpret_cast<int*>(rank + kMaxParticles);
+    int* big = tmp + kMaxParticles;
     cudaStream_t s = (cudaStream_t)stream;
-    // the scratch keeps the previous call's contents: the counts must start at zero
+    // the scratch keeps the previous call's contents: the counts (and the large-cell
+    // counter, cleared by launch_segsort) must start at zero
     if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)(G + 1), s) != cudaSuccess) return LEDDS_ERR_CUDA;
     k_na_keys<<<(n + 127) / 128, 128, 0, s>>>(d_pos, n, g, d_keys, count, rank);
     if (launch_scan(count, (int)G, start, partial, s) != cudaSuccess) return LEDDS_ERR_CUDA;
-    k_na_scatter<<<(n + 127) / 128, 128, 0, s>>>(d_keys, rank, start, n, d_sorted_ids);
-    k_na_segsort<<<(int)((G + 127) / 128), 128, 0, s>>>(start, (int)G, d_sorted_ids);
+    k_na_scatter<<<(n + 127) / 128, 128, 0, s>>>(d_keys, rank, start, n, tmp);
+    if (launch_segsort(start, (int)G, n, tmp, d_sorted_ids, big, s) != cudaSuccess) return LEDDS_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? LEDDS_OK : LEDDS_ERR_CUDA;
 }

@@ -73,3 +73,30 @@ def test_cell_list_without_allocation_rejects_oversize(torch_cuda):
     assert rc == -2     # LEDDS_ERR_CAPACITY, before any device work
     rc, _, _, _ = _call(lib, torch, pos, 1, (0, 0, 0), (100, 100, 100), 1.0, stream)
     assert rc == -2     # 10^6 grid cells exceed the 262144 limit
+
+
+@pytest.mark.parametrize("n", [32768, 1 << 18])
+def test_cell_list_without_allocation_one_cell_and_crowded_cells(torch_cuda, n):
+    """Degenerate grids, each cell ordered in bounded time: h larger than the box (one
+    cell holds every particle), and a fine grid where non-finite positions all land in
+    cell 0 beside ordinary cells; (key, id) order against numpy's lexsort."""
+    torch = torch_cuda
+    from paper_2512_04997_gb300 import ledds
+    lib = ledds.lib()
+    stream = torch.cuda.current_stream()
+    g = np.random.default_rng(41)
+    p = g.uniform(0.0, 10.0, (n, 3))
+    pos = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float64, device="cuda")
+    rc, keys, ids, gn = _call(lib, torch, pos, n, (0, 0, 0), (10, 10, 10), 20.0, stream)
+    assert rc == 0 and gn == (1, 1, 1)
+    assert not keys.any() and np.array_equal(ids, np.arange(n))
+    p[g.random(n) < 0.3] = np.nan
+    pos = torch.tensor(np.ascontiguousarray(p.T), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        rc, keys, ids, gn = _call(lib, torch, pos, n, (0, 0, 0), (10, 10, 10), 0.5, stream)
+        assert rc == 0 and gn == (20, 20, 20)
+        c = np.where(np.isfinite(p), np.floor(p / 0.5), 0.0).clip(0, 19).astype(np.int64)
+        c[~np.isfinite(p).all(axis=1)] = 0
+        k = c[:, 0] + 20 * (c[:, 1] + 20 * c[:, 2])
+        assert np.array_equal(keys.astype(np.int64), k)
+        assert np.array_equal(ids, np.lexsort((np.arange(n), k)))
