@@ -101,6 +101,10 @@ typedef struct {
     int index64;             /* 1: 64-bit population offsets in the PSM kernel; 0: only when  */
                              /* 19 nx ny nz >= 2^31 (lattices of more than 1.1e8 nodes up to  */
                              /* 2^31 nodes use them automatically; batch members cannot)      */
+    int psm_route;           /* PSM kernel loads: 0 staged by the tensor copy engine (TMA) where */
+                             /* the lattice suits it (rows a multiple of 16 bytes, nx >= 40   */
+                             /* (FP32) / 48 (16-bit), ny >= 8), else direct; 1 always direct  */
+                             /* per-thread loads. Both give identical results.                 */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */
@@ -124,6 +128,9 @@ typedef struct {
     int nan_detected;        /* non-finite particle state                                    */
     int n_particles;
     int launches_per_step;   /* kernels launched per fluid step                              */
+    int wait_timeout;        /* bounded waits of the staged PSM kernel that gave up (the step's */
+                             /* results are then invalid; ledds_get_status returns TIMEOUT)   */
+    int psm_staged;          /* 1: the PSM kernel stages its loads with tensor copies          */
 } ledds_status;
 
 typedef struct ledds_sim_s* ledds_sim_t;
@@ -285,8 +292,10 @@ int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice);
  * that cannot allocate device memory themselves, such as code running under a memory
  * pool that owns the whole device, or a latency-critical path where an allocation could
  * block or fail. It takes no simulation object and no workspace; its scratch (per-cell
- * counts and starts, scan partials, per-particle ranks) lives in a fixed array inside
- * the library that every GPU loading the library keeps until the process exits.
+ * counts and starts, scan partials, per-particle ranks and scatter order, about 4.2 MB)
+ * lives in a fixed array inside the library that every GPU loading the library keeps
+ * until the process exits. Cells are ordered in bounded time whatever their occupancy
+ * (a grid of one cell included).
  *   d_pos      particle positions on the device, [3][n] doubles (x row, y row, z row)
  *   box_lo/hi  domain; the grid has floor(L/h) cells per axis (at least one), of width
  *              L/cells, exactly as a simulation with dem_h = h builds it
@@ -295,10 +304,10 @@ int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice);
  *   grid_n     may be NULL; receives the cells per axis
  *   stream     cudaStream_t the work is enqueued on (asynchronous)
  * Limits: at most 262144 grid cells and 262144 particles; larger inputs return
- * LEDDS_ERR_CAPACITY before any device work. Every call reuses the same scratch, so
- * calls that may overlap on the GPU (different streams or devices' concurrent use of
- * one stream order aside) race and must be serialised by the caller. The first call on
- * each device looks up the scratch address (cudaGetSymbolAddress); make that first call
+ * LEDDS_ERR_CAPACITY before any device work. Calls on the same device that may overlap
+ * (different streams, or host threads without ordering) share one scratch array and must
+ * be serialised by the caller; each device has its own copy. The first call in each CUDA
+ * context looks up the scratch address (cudaGetSymbolAddress); make that first call
  * before any stream capture. Errors: INVALID_ARG, CAPACITY, CUDA. */
 int ledds_cell_list_noalloc(const double* d_pos, int n, const double box_lo[3],
                             const double box_hi[3], double h, uint32_t* d_keys,

@@ -19,7 +19,7 @@ cudaError_t launch_init(const LbmArgs&, int, const float*, const float*, const f
 cudaError_t launch_read(const LbmArgs&, int, float*, float*, float*, int, cudaStream_t);
 cudaError_t launch_rebase(const LbmArgs&, int, const float (*)[2][3], cudaStream_t);
 cudaError_t launch_bin(const LbmArgs&, int, int*, int*, cudaStream_t);
-cudaError_t launch_psm(const LbmArgs&, int, cudaStream_t);
+cudaError_t launch_psm(const LbmArgs&, const PsmMaps*, int, cudaStream_t);
 cudaError_t launch_voxelize(const LbmArgs&, float*, int*, int*, cudaStream_t);
 cudaError_t launch_rebuild(const DemArgs&, int, int, int, uint32_t*, cudaStream_t, int*);
 cudaError_t launch_predict_first(const DemArgs&, cudaStream_t);
@@ -57,6 +57,8 @@ struct ledds_sim_s {
     long long N = 0;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
     void* pop[2] = {nullptr, nullptr};
+    PsmMaps maps[2];          // tensor maps of pop[0], pop[1] (staged PSM route)
+    bool staged = false;      // the PSM kernel takes the staged route
     int* tile_count = nullptr;
     int* tile_ids = nullptr;
     int tile_cap = 0;
@@ -72,7 +74,7 @@ struct ledds_sim_s {
     uint32_t* cp_list = nullptr;  // canonical pair list (pair-once evaluation)
     double* cp_res = nullptr;     // per-pair force and torques
     long long cp_stride = 0;
-    int *rank = nullptr, *sorted = nullptr;
+    int *rank = nullptr, *sorted = nullptr, *sorted_tmp = nullptr, *seg_big = nullptr;
     int* cand[2] = {nullptr, nullptr};
     int* ncand[2] = {nullptr, nullptr};
     double* hist[2] = {nullptr, nullptr};
@@ -140,6 +142,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->orient < 0 || p->orient > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->pattern < 0 || p->pattern > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->index64 < 0 || p->index64 > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->psm_route < 0 || p->psm_route > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -210,6 +213,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
     uint32_t* keys = c.take<uint32_t>((size_t)capc);
     int* rank = c.take<int>((size_t)capc);
     int* sorted = c.take<int>((size_t)capc);
+    int* sorted_tmp = c.take<int>((size_t)capc);
+    int* seg_big = c.take<int>((size_t)capc / 32 + 2);
     uint32_t* ccount = c.take<uint32_t>((size_t)G + 1);
     uint32_t* cstart = c.take<uint32_t>((size_t)G + 1);
     uint32_t* partial = c.take<uint32_t>(4096);
@@ -236,6 +241,9 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
         s->tile_cap = tcap;
         s->pop[0] = pop0;
         s->pop[1] = pop1;
+        s->staged = N > 0 && p->psm_route == 0 &&
+                    psm_make_maps(pop0, p->storage, d->nx, d->ny, d->nz, &s->maps[0]) &&
+                    psm_make_maps(pop1, p->storage, d->nx, d->ny, d->nz, &s->maps[1]);
         s->tile_count = tcount;
         s->tile_ids = tids;
         s->ccap = ccap;
@@ -263,6 +271,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
         s->keys = keys;
         s->rank = rank;
         s->sorted = sorted;
+        s->sorted_tmp = sorted_tmp;
+        s->seg_big = seg_big;
         s->cell_count = ccount;
         s->cell_start = cstart;
         s->scan_partial = partial;
@@ -408,6 +418,8 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     A.keys = s->keys;
     A.rank = s->rank;
     A.sorted = s->sorted;
+    A.sorted_tmp = s->sorted_tmp;
+    A.seg_big = s->seg_big;
     A.cell_count = s->cell_count;
     A.cell_start = s->cell_start;
     for (int b = 0; b < 2; ++b) {
@@ -482,7 +494,7 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
             *launches += 1;
         }
         if (ev) CK(cudaEventRecord(ev[3], st));
-        CK(launch_psm(la, s->p.storage, st));
+        CK(launch_psm(la, s->staged ? &s->maps[p] : nullptr, s->p.storage, st));
         *launches += 1;
     } else if (ev) {
         CK(cudaEventRecord(ev[3], st));
@@ -561,6 +573,7 @@ int ledds_params_default(ledds_params* p) {
     p->orient = LEDDS_ORIENT_TRIAD;
     p->pattern = LEDDS_PATTERN_AB;
     p->index64 = 0;
+    p->psm_route = 0;
     return LEDDS_OK;
 }
 
@@ -883,7 +896,10 @@ int ledds_get_status(ledds_sim_t s, ledds_status* st) {
     st->nan_detected = h.nan_detected;
     st->n_particles = s->P.n;
     st->launches_per_step = s->launches_per_step;
+    st->wait_timeout = h.wait_timeout;
+    st->psm_staged = s->staged ? 1 : 0;
     if (h.nan_detected) return LEDDS_ERR_NAN;
+    if (h.wait_timeout) return LEDDS_ERR_TIMEOUT;
     if (h.tile_overflow || h.cand_overflow) return LEDDS_ERR_CAPACITY;
     return LEDDS_OK;
 }

@@ -4,6 +4,7 @@
 // structs and the launch helpers used by lbm.cu, dem.cu and api.cu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -49,6 +50,8 @@ template <>
 struct Store<LEDDS_STORE_F32> {
     using T = float;
     static __device__ __forceinline__ float load(const T* p, float) { return *p; }
+    static __device__ __forceinline__ float ldg(const T* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ float dec(T v, float) { return v; }
     static __device__ __forceinline__ float from_bits(unsigned short, float) { return 0.f; }
     static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
 };
@@ -58,6 +61,10 @@ struct Store<LEDDS_STORE_F16> {
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __half2float(*p) * inv;
     }
+    static __device__ __forceinline__ float ldg(const T* p, float inv) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)))) * inv;
+    }
+    static __device__ __forceinline__ float dec(T v, float inv) { return __half2float(v) * inv; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
         return __half2float(__ushort_as_half(h)) * inv;
     }
@@ -72,6 +79,10 @@ struct Store<LEDDS_STORE_BF16> {
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __bfloat162float(*p) * inv;
     }
+    static __device__ __forceinline__ float ldg(const T* p, float inv) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p)))) * inv;
+    }
+    static __device__ __forceinline__ float dec(T v, float inv) { return __bfloat162float(v) * inv; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
         return __bfloat162float(__ushort_as_bfloat16(h)) * inv;
     }
@@ -82,6 +93,7 @@ struct Store<LEDDS_STORE_BF16> {
 };
 
 inline size_t storage_bytes(int store) { return store == LEDDS_STORE_F32 ? 4 : 2; }
+__host__ __device__ constexpr int storage_bytes_c(int store) { return store == LEDDS_STORE_F32 ? 4 : 2; }
 
 // Lattice tile handled by one CTA of the PSM kernel: 32 x 8 nodes per plane (one warp
 // per x-row), TILE_Z planes.
@@ -100,7 +112,8 @@ struct DevStatus {
     int skin_violation;
     int ell_nonconverged;
     int nan_detected;
-    int pad[2];
+    int wait_timeout;             // bounded waits of the staged PSM pipeline that gave up
+    int pad;
 };
 
 // Particle arrays in the workspace. State buffers hold [18][cap] doubles: pos xyz,
@@ -179,6 +192,13 @@ struct BatchChunk {
 };
 static_assert(sizeof(BatchChunk) <= 32764, "a batch chunk must fit the kernel parameter space");
 
+// Tensor maps of one population array for the staged PSM route (4D: x, y, z, plane; boxes
+// of TILE_Y rows by TILE_X or TILE_X + 2H columns, one plane deep), made by psm_make_maps.
+struct PsmMaps {
+    CUtensorMap narrow, wide;
+};
+bool psm_make_maps(const void* pop, int store, int nx, int ny, int nz, PsmMaps* out);  // lbm.cu
+
 struct DemArgs {
     DevParticles P;
     // domain
@@ -211,6 +231,8 @@ struct DemArgs {
     uint32_t* keys;
     int* rank;
     int* sorted;
+    int* sorted_tmp;              // ids in scatter order (before each cell is ordered)
+    int* seg_big;                 // cells of more than SEG_SMALL ids: count, list
     uint32_t* cell_count;
     uint32_t* cell_start;
     int* cand[2];

@@ -10,6 +10,7 @@
 // processes one x-row (32 consecutive nodes: coalesced 128-byte rows for FP32). The PSM
 // kernel itself is in psm.cuh; psm_aa.cu instantiates it for the single-array AA pattern,
 // whose array states the read, initialisation and rebase kernels here also handle.
+#include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
 
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const
         const LbmArgs& a = P.a[sim];
         const int t = item - P.tile_start[sim];
         const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
-        psm_tile<STORE, TRT, PSM_AB>(a, bx, by, bz, 0, TILE_Z, smem);
+        psm_tile_direct<STORE, TRT, PSM_AB>(a, bx, by, bz, 0, TILE_Z, smem);
         __syncthreads();
     }
 }
@@ -430,9 +431,45 @@ __global__ void k_bin_batch(const LbmArgs* args, const int* np) {
 
 int psm_batch_ctas_per_sm() { return PSM_BATCH_MINB; }
 
-size_t psm_smem_bytes(int store) {
-    const int stages = store == LEDDS_STORE_F32 ? PsmCfg<LEDDS_STORE_F32>::stages : PsmCfg<LEDDS_STORE_F16>::stages;
-    return ((sizeof(TileCache) + 15) & ~(size_t)15) + sizeof(uint32_t) * stages * 19 * PSM_THREADS;
+// Tensor maps of a population array for the staged PSM route: 4D (x, y, z, plane), boxes
+// of TILE_Y rows by TILE_X columns (narrow) or TILE_X + 2H columns (wide, H = 16 bytes of
+// elements), one plane deep; elements outside the array read as zero. False when the
+// lattice does not suit the route (rows not a multiple of 16 bytes, fewer rows than a
+// tile, narrower than a wide box) or the driver has no tensor-map encoder; the kernel
+// then takes the direct route.
+bool psm_make_maps(const void* pop, int store, int nx, int ny, int nz, PsmMaps* out) {
+    const int es = (int)storage_bytes(store);
+    const int H = 16 / es;
+    if (((long long)nx * es) % 16 != 0 || (reinterpret_cast<uintptr_t>(pop) & 15u) != 0) return false;
+    if (nx < TILE_X + 2 * H || ny < TILE_Y || nz < 1) return false;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz, 19};
+    const cuuint64_t strides[3] = {(cuuint64_t)nx * es, (cuuint64_t)nx * ny * es, (cuuint64_t)nx * ny * nz * es};
+    const cuuint32_t box_n[4] = {TILE_X, TILE_Y, 1, 1};
+    const cuuint32_t box_w[4] = {(cuuint32_t)(TILE_X + 2 * H), TILE_Y, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    PsmMaps m;
+    memset(&m, 0, sizeof(m));
+    if (encode(&m.narrow, dt, 4, const_cast<void*>(pop), dims, strides, box_n, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (encode(&m.wide, dt, 4, const_cast<void*>(pop), dims, strides, box_w, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *out = m;
+    return true;
 }
 
 // Solid fractions only (the same tile machinery), for inspection.
@@ -505,16 +542,16 @@ cudaError_t launch_bin(const LbmArgs& a, int n, int* tile_count, int* tile_ids, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_psm(const LbmArgs& a, int store, cudaStream_t s) {
-    if (a.w64) return launch_psm_wide(a, store, s);
-    if (a.aa != PSM_AB) return launch_psm_aa(a, store, s);
-    return launch_psm_mode<PSM_AB>(a, store, s);
+cudaError_t launch_psm(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s) {
+    if (a.w64) return launch_psm_wide(a, m, store, s);
+    if (a.aa != PSM_AB) return launch_psm_aa(a, m, store, s);
+    return launch_psm_mode<PSM_AB>(a, m, store, s);
 }
 
 template <int STORE, bool TRT>
 static cudaError_t launch_psm_batch_t(const BatchChunk& P, int* counter, int nblocks, cudaStream_t s) {
     static bool configured = false;
-    const size_t smem = psm_smem_bytes(STORE);
+    const size_t smem = PsmSmem<STORE, false, true>::bytes;
     if (!configured) {
         cudaError_t e =
             cudaFuncSetAttribute(k_psm_batch<STORE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

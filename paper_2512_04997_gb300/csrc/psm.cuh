@@ -1,18 +1,18 @@
 // psm.cuh -- the fused PSM kernel of one lattice tile (Secs. 2.3-2.4, Table 1
 // "Compute solid fractions", "LBM-PSM collision and streaming", "Force reduction"),
-// shared by the translation units that instantiate it: lbm.cu (two-lattice pull) and
-// psm_aa.cu (the in-place AA pattern).
+// shared by the translation units that instantiate it: lbm.cu (two-lattice pull),
+// psm_aa.cu (the in-place AA pattern) and psm_wide.cu (64-bit population offsets).
 #pragma once
 
 #include <type_traits>
+#include <utility>
 
 #include "internal.cuh"
 
 namespace ledds {
 
-size_t psm_smem_bytes(int store);                                    // lbm.cu
-cudaError_t launch_psm_aa(const LbmArgs& a, int store, cudaStream_t s);    // psm_aa.cu
-cudaError_t launch_psm_wide(const LbmArgs& a, int store, cudaStream_t s);  // psm_wide.cu
+cudaError_t launch_psm_aa(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s);    // psm_aa.cu
+cudaError_t launch_psm_wide(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s);  // psm_wide.cu
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -370,36 +370,30 @@ __device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float v
     }
 }
 
+
 // ------------------------------------------------------------------------------------
-// Asynchronous pull: each thread copies the 19 values it pulls for a plane straight into
-// its own shared-memory slots (cp.async, 4-byte granules; 16-bit formats copy the aligned
-// word holding the value). Only the issuing thread reads them back, so the pipeline
-// needs no CTA barrier, and two planes of loads stay in flight per thread whatever the
-// occupancy.
+// Pulling the populations of a node. Two routes with one result:
+//  - staged: per z-plane of a tile, the tensor engine (TMA) copies one box per direction
+//    (the tile's 8 rows shifted by -c_i) from the population array into a ring of
+//    shared-memory stages, each guarded by a pair of mbarriers (data landed / stage read
+//    by every warp); each warp reads its own row back at fixed offsets;
+//  - direct: per-thread loads from global memory, for lattices whose rows are not a
+//    multiple of 16 bytes, batch members, the rows on a lattice face and the lanes at
+//    the x ends of the lattice (periodic wraps and halfway bounce-back).
 // ------------------------------------------------------------------------------------
 constexpr int PSM_THREADS = TILE_X * TILE_Y;
 
-// Per storage format: resident CTAs per SM the PSM kernel is compiled for (its register
-// budget) and depth of the asynchronous pull pipeline (planes in flight + 1). Chosen by
-// timing the variants on GB300: FP32 runs best with more registers and a deeper
-// pipeline, the 16-bit formats with more resident CTAs.
-template <int STORE>
-struct PsmCfg {
-    static constexpr int minb = 3, stages = 3;
-};
-template <>
-struct PsmCfg<LEDDS_STORE_F32> {
-    static constexpr int minb = 2, stages = 4;
-};
-
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src, bool pred) {
-    unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-    int n = pred ? 4 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(n) : "memory");
+// Calls f(std::integral_constant<int, I>) for I = 0 .. N-1 (a compile-time loop over the
+// directions, so every table entry folds into an immediate).
+template <class F, int... Is>
+__device__ __forceinline__ void static_for_seq(F&& f, std::integer_sequence<int, Is...>) {
+    (f(std::integral_constant<int, Is>{}), ...);
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_seq(f, std::make_integer_sequence<int, N>{});
+}
+
 
 // Per-plane pull plan of one node: the source of direction I is node - off_I, plus a
 // periodic-wrap correction on an axis where the node sits on the first or last layer; a
@@ -472,68 +466,154 @@ __device__ __forceinline__ PsmIdx<MODE> src_elem(const LbmArgs& a, const Plan& p
     return plane_at<MODE>(a, plane_in) + src;
 }
 
-template <class SS, int I, bool WALLS, int MODE>
-struct IssueAll {
-    static __device__ __forceinline__ void run(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
-                                               uint32_t* slot) {
-        uintptr_t q = reinterpret_cast<uintptr_t>(pin + src_elem<I, WALLS, MODE>(a, p));
-        if (sizeof(typename SS::T) == 2) q &= ~(uintptr_t)3;
-        cp_async4(slot + I * PSM_THREADS, reinterpret_cast<const void*>(q), true);
-        IssueAll<SS, I + 1, WALLS, MODE>::run(a, pin, p, slot);
-    }
-};
-template <class SS, bool WALLS, int MODE>
-struct IssueAll<SS, 19, WALLS, MODE> {
-    static __device__ __forceinline__ void run(const LbmArgs&, const typename SS::T*, const Plan&, uint32_t*) {}
-};
 
-// Issue the 19 reads of node (x,y,z) into its shared-memory slots (nothing if !pred). Every
-// lane of the warp calls it; warps without a wall link take the plain addressing.
+// The two-lattice pull reads an array the kernel does not write (read-only data path);
+// the AA pattern reads and writes one array.
 template <class SS, int MODE>
-__device__ __forceinline__ void issue_node(const LbmArgs& a, const typename SS::T* pin, int x, int y, int z,
-                                           bool pred, uint32_t* slot) {
-    Plan p;
-    make_plan(a, x, y, z, p);
-    if (psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, pred && p.bw != 0u)) {
-        if (pred) IssueAll<SS, 0, true, MODE>::run(a, pin, p, slot);
-    } else if (pred) {
-        IssueAll<SS, 0, false, MODE>::run(a, pin, p, slot);
+__device__ __forceinline__ float ld_pop(const typename SS::T* p, float inv) {
+    if constexpr (psm_form(MODE) == PSM_AB) return SS::ldg(p, inv);
+    else return SS::load(p, inv);
+}
+
+// Direct pull of direction I of a node. GEN: periodic wraps and halfway bounce-back with
+// the moving-wall term, from the node's plan; without GEN the caller knows that neither
+// occurs for any lane (a node off every lattice face), and the source is node - off_I.
+template <class SS, int I, bool GEN, int MODE>
+__device__ __forceinline__ float pull_one(const LbmArgs& a, const typename SS::T* pin, const Plan& p) {
+    if constexpr (!GEN) {
+        constexpr int plane_in = psm_form(MODE) == PSM_AA_ODD ? OPP(I) : I;
+        PsmIdx<MODE> src = (PsmIdx<MODE>)p.cell;
+        if constexpr (psm_form(MODE) != PSM_AA_EVEN) src -= a.off[I];
+        return ld_pop<SS, MODE>(pin + (plane_at<MODE>(a, plane_in) + src), a.inv_scale);
+    } else {
+        float v = ld_pop<SS, MODE>(pin + src_elem<I, true, MODE>(a, p), a.inv_scale);
+        if constexpr (psm_form(MODE) != PSM_AA_EVEN) {
+            bool wx, wy, wz;
+            link_walls<I>(p, wx, wy, wz);
+            if (wx || wy || wz) v += wall_term<I>(a.uw, wx, wy, wz);  // moving-wall bounce-back
+        }
+        return v;
     }
 }
 
-template <class SS>
-__device__ __forceinline__ float decode(uint32_t w, int odd, float inv) {
-    if (sizeof(typename SS::T) == 4) return __uint_as_float(w);
-    return SS::from_bits(odd ? (unsigned short)(w >> 16) : (unsigned short)(w & 0xffffu), inv);
+template <class SS, bool GEN, int MODE>
+__device__ __forceinline__ void pull_all(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
+                                         float (&g)[19]) {
+    static_for<19>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        g[I] = pull_one<SS, I, GEN, MODE>(a, pin, p);
+    });
 }
 
-template <class SS, int I, bool WALLS, int MODE>
-struct ReadAll {
-    static __device__ __forceinline__ void run(const LbmArgs& a, const Plan& p, const uint32_t* slot, float* g) {
-        const uint32_t w = slot[I * PSM_THREADS];
-        bool wx = false, wy = false, wz = false;
-        if constexpr (WALLS) link_walls<I>(p, wx, wy, wz);
-        const bool wl = wx || wy || wz;
-        // 16-bit storage: which half of the copied word holds the value. With nx even every
-        // plane start, offset and wrap correction except c_x is even, so the parity is that
-        // of x - c_x (of x itself for a bounced link or an in-place read).
-        int odd = 0;
-        if (sizeof(typename SS::T) == 2) {
-            const int shift = (wl || psm_form(MODE) == PSM_AA_EVEN) ? 0 : CX(I);
-            odd = a.nx_even ? ((p.cell ^ shift) & 1) : (src_elem<I, WALLS, MODE>(a, p) & 1);
+// Shared-memory stage of one z-plane: per direction i a box of TILE_Y rows. A streaming
+// step (SHIFT) reads direction i at x - c_i: the boxes of directions with c_x != 0 are
+// TILE_X + 2H columns wide from x0 - H (H elements = 16 bytes, so that every box starts
+// on a 16-byte boundary, as tensor copies require) and are read at column lane + H - c_x;
+// the other boxes, and every box of the in-place AA step, are TILE_X columns from x0.
+// Every box is a multiple of 128 bytes, so each one starts 128-byte aligned.
+template <int ES, bool SHIFT>
+struct Stage {
+    static constexpr int H = 16 / ES;
+    static constexpr int WB = TILE_X + 2 * H;
+    static constexpr bool wide(int i) { return SHIFT && CX(i) != 0; }
+    static constexpr int width(int i) { return wide(i) ? WB : TILE_X; }
+    static constexpr int slot(int i) { return i == 0 ? 0 : slot(i - 1) + TILE_Y * width(i - 1); }  // elements
+    static constexpr int elems = slot(19);
+    static constexpr int bytes = elems * ES;
+    static_assert((TILE_Y * TILE_X * ES) % 128 == 0 && (TILE_Y * WB * ES) % 128 == 0, "box alignment");
+};
+
+// mbarrier and tensor-copy primitives (PTX ISA: mbarrier, cp.async.bulk.tensor).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Every wait is bounded: after about a quarter of a second at the GB300 clock it counts a
+// timeout in the status block (ledds_get_status returns LEDDS_ERR_TIMEOUT) and gives up.
+constexpr long long PSM_WAIT_CYCLES = 1ll << 29;
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, unsigned parity, DevStatus* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > PSM_WAIT_CYCLES) {
+            atomicAdd(&status->wait_timeout, 1);
+            return false;
         }
-        float v = decode<SS>(w, odd, a.inv_scale);
-        if constexpr (WALLS) {
-            if (wl) v += wall_term<I>(a.uw, wx, wy, wz);  // moving-wall bounce-back
-        }
-        g[I] = v;
-        ReadAll<SS, I + 1, WALLS, MODE>::run(a, p, slot, g);
     }
-};
-template <class SS, bool WALLS, int MODE>
-struct ReadAll<SS, 19, WALLS, MODE> {
-    static __device__ __forceinline__ void run(const LbmArgs&, const Plan&, const uint32_t*, float*) {}
-};
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Issue the boxes of z-plane z of the tile at (x0, y0) into a stage; one thread. The box
+// of direction I comes from plane I (plane opp(I) in the AA pattern's streaming step,
+// which keeps f*_I there), shifted by -c_I in a streaming step. Boxes that reach beyond
+// the lattice are filled with zeros by the copy engine; the rows and lanes that would
+// read them take the direct route.
+template <int ES, int MODE>
+__device__ __forceinline__ void issue_plane(const PsmMaps& m, uint32_t stage, uint32_t full, int x0, int y0, int z) {
+    constexpr bool SHIFT = psm_form(MODE) != PSM_AA_EVEN;
+    using G = Stage<ES, SHIFT>;
+    mbar_expect_tx(full, (unsigned)G::bytes);
+    static_for<19>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        constexpr int plane = psm_form(MODE) == PSM_AA_ODD ? OPP(I) : I;
+        const CUtensorMap* map = G::wide(I) ? &m.wide : &m.narrow;
+        tma_load_4d(stage + (uint32_t)(G::slot(I) * ES), map, x0 - (G::wide(I) ? G::H : 0),
+                    y0 - (SHIFT ? CY(I) : 0), z - (SHIFT ? CZ(I) : 0), plane, full);
+    });
+}
+
+// A warp's row of the stage: g_I of the lane's node.
+template <class SS, int MODE>
+__device__ __forceinline__ void read_stage(const LbmArgs& a, const unsigned char* stage, int lane, int warp,
+                                           float (&g)[19]) {
+    using T = typename SS::T;
+    constexpr bool SHIFT = psm_form(MODE) != PSM_AA_EVEN;
+    using G = Stage<(int)sizeof(T), SHIFT>;
+    const T* sb = reinterpret_cast<const T*>(stage);
+    const int on = warp * TILE_X + lane;            // narrow boxes
+    const int ow = warp * G::WB + lane + G::H;      // wide boxes
+    static_for<19>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        const T v = G::wide(I) ? sb[G::slot(I) + ow - CX(I)] : sb[G::slot(I) + on];
+        g[I] = SS::dec(v, a.inv_scale);
+    });
+}
+
+// Lanes at the x ends of the lattice in a row off the y and z faces: the directions with
+// c_x != 0 wrap or bounce back; re-pulled directly.
+template <class SS, int MODE>
+__device__ __forceinline__ void fix_x_ends(const LbmArgs& a, const typename SS::T* pin, const Plan& p,
+                                           float (&g)[19]) {
+    static_for<19>([&](auto ic) {
+        constexpr int I = decltype(ic)::value;
+        if constexpr (CX(I) != 0) g[I] = pull_one<SS, I, true, MODE>(a, pin, p);
+    });
+}
 
 // c . v for a lattice vector c with components in {-1, 0, 1} known at compile time (no
 // multiplications by 0 or +/-1 left to run time), and c^T Q c for a symmetric Q.
@@ -662,6 +742,7 @@ struct CollidePairs<SS, 19, SOLID, TRT, MODE, WALLS> {
                                                const Plan&, bool) {}
 };
 
+
 // ------------------------------------------------------------------------------------
 // The fused PSM step: pull, moments, solid fractions, PSM collision (Eqs. psm1, lbePS,
 // bk, btot), store, and the hydrodynamic force/torque of each solid (Eqs. forceSF,
@@ -670,199 +751,177 @@ struct CollidePairs<SS, 19, SOLID, TRT, MODE, WALLS> {
 //   f*_i = geq_i + (1 - (1-B_tot)/tau) neq_i + sum_k B_k Omega^s_{i,k},
 //   Omega^s_{i,k} = neq_ibar - neq_i - (geq_i(rho,u) - geq_i(rho,u_k)).
 // ------------------------------------------------------------------------------------
-// One 32x8xTILE_Z tile (bx, by, bz) of the lattice described by `a`; psm_smem holds the
-// tile cache followed by the pipeline stages (psm_smem_bytes()).
-template <int STORE, bool TRT, int MODE>
-__device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int bz, int zlo, int zhi,
-                                         unsigned char* psm_smem) {
-    using SS = Store<STORE>;
-    using T = typename SS::T;
-    constexpr int PSM_STAGES = PsmCfg<STORE>::stages;
-    const T* pin = (const T*)a.pop_in;
-    T* pout = (T*)a.pop_out;
-    TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
-    uint32_t* stage = reinterpret_cast<uint32_t*>(psm_smem + ((sizeof(TileCache) + 15) & ~(size_t)15));
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
-    const int tile = (bz * a.nty + by) * a.ntx + bx;
-    const int x = x0 + lane, y = y0 + warp;
-    const bool valid_xy = x < a.nx && y < a.ny;
-
-    // prologue: the first planes (of this CTA's planes zlo .. zhi-1 of the tile) in flight
-    // while the tile's particles are cached
-#pragma unroll
-    for (int q = 0; q < PSM_STAGES - 1; ++q) {
-        const int z = z0 + zlo + q;
-        issue_node<SS, MODE>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
-                       stage + (q * 19) * PSM_THREADS + tid);
-        cp_async_commit();
-    }
-    const int cnt = min(a.tile_count[tile], a.tile_cap);
-    load_tile(a, tc, tile, cnt, x0, y0, z0);
-    __syncthreads();
-
+// One node (x, y, z) = tile offset (lane, warp, iz) after its pull: g holds the pulled
+// populations. Entered by every lane of the warp together (the solid search and the
+// force sums are warp-cooperative); `valid` is false for lanes beyond the lattice, and
+// wwarp is true when some lane of the warp has a wall link. hkey/hacc: the running force
+// sum of the solid this lane last met down its column.
+template <class SS, bool TRT, int MODE>
+__device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float (&g)[19], const Plan& pl,
+                                         bool valid, bool wwarp, unsigned long long mask, int lane, int warp,
+                                         int iz, int x, int y, int z, typename SS::T* pout, int& hkey,
+                                         float (&hacc)[6]) {
     const float tau = a.tau, omega = a.omega;
-    int hkey = -1;                                   // solid held in the running sum
-    float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // its force and torque so far
-    for (int iz = zlo; iz < zhi; ++iz) {
-        const int r = iz - zlo;  // position in the pipeline ring
-        {   // keep PSM_STAGES - 1 planes ahead in flight
-            const int q = r + PSM_STAGES - 1;
-            const int z = z0 + zlo + q;
-            issue_node<SS, MODE>(a, pin, x, y, z, zlo + q < zhi && valid_xy && z < a.nz,
-                           stage + ((q % PSM_STAGES) * 19) * PSM_THREADS + tid);
-            cp_async_commit();
-        }
-        cp_async_wait<PSM_STAGES - 1>();
-        const int z = z0 + iz;
-        if (y >= a.ny || z >= a.nz) continue;  // uniform across the warp
-        const bool valid = x < a.nx;
-        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
-
-        float g[19];
-        Plan pl;
-        make_plan(a, valid ? x : 0, y, z, pl);
-        const uint32_t* slot = stage + ((r % PSM_STAGES) * 19) * PSM_THREADS + tid;
-        // some lane of the warp has a wall link (never needed by the in-place step)
-        const bool wwarp = psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
-        if (wwarp) {
-            if (valid) ReadAll<SS, 0, true, MODE>::run(a, pl, slot, g);
-        } else if (valid) {
-            ReadAll<SS, 0, false, MODE>::run(a, pl, slot, g);
-        }
-        if (!valid) {
+    if (!valid) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) g[i] = 0.f;
-        }
-        Two t;
-        t.ns = 0;
-        t.total = 0;
-        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
-        if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
+        for (int i = 0; i < 19; ++i) g[i] = 0.f;
+    }
+    Two t;
+    t.ns = 0;
+    t.total = 0;
+    if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+    if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
 
-        // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
-        const float drho = ((g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
-                           (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14]))) +
-                           ((g[15] + g[16]) + (g[17] + g[18]));
-        float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
-        float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
-        float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
-        const float rho = 1.0f + drho;
-        if (a.has_force) {
-            jx += 0.5f * a.F[0];
-            jy += 0.5f * a.F[1];
-            jz += 0.5f * a.F[2];
-        }
-        const float inv_rho = 1.0f / rho;
-        const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-        const float usq = ux * ux + uy * uy + uz * uz;
-        const float base = drho - rho * 1.5f * usq;
+    // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
+    const float drho = ((g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
+                       (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14]))) +
+                       ((g[15] + g[16]) + (g[17] + g[18]));
+    float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
+    float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
+    float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
+    const float rho = 1.0f + drho;
+    if (a.has_force) {
+        jx += 0.5f * a.F[0];
+        jy += 0.5f * a.F[1];
+        jz += 0.5f * a.F[2];
+    }
+    const float inv_rho = 1.0f / rho;
+    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float base = drho - rho * 1.5f * usq;
 
-        const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
-        // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
-        g[0] -= TW(0) * base;
-        // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
-        // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
-        if (!__any_sync(FULL, t.ns > 0)) {
-            // no lane of the warp meets a solid at this node (uniform): plain BGK/TRT, and
-            // nothing to add to the held force sums
-            const float keep = TRT ? 1.0f - 0.5f * (omega + a.omega_m) : 1.0f - omega;
-            const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
-            SolidSums m;
-            m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
-            if (psm_form(MODE) == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
-                CollidePairs<SS, 1, false, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
-                                                                 kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
-            else
-                CollidePairs<SS, 1, false, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
-                                                                  kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
-            float out0 = TW(0) * base + (1.0f - omega) * g[0];
-            if (a.has_force) out0 += a.guo_pref * TW(0) * (-3.0f * Fu);
-            if (valid) SS::store(pout + pl.cell, out0, a.scale);
-            continue;
-        }
-        // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
-        SolidAt q0, q1;
-        q0.B = q1.B = 0.f;
-        q0.ux = q0.uy = q0.uz = q0.usq = q0.ax = q0.ay = q0.az = 0.f;
-        q1.ux = q1.uy = q1.uz = q1.usq = q1.ax = q1.ay = q1.az = 0.f;
-        q0.sx = q0.sy = q0.sz = q1.sx = q1.sy = q1.sz = 0.f;
-        if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
-        if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
-        const float Btot = fminf(q0.B + q1.B, 1.0f);
-        const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
-        const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
-        const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
-        const float force_w = (1.0f - Btot) * a.guo_pref;
-        const float force_wa = (1.0f - Btot) * a.guo_pref_m;
-        // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
-        const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
-        const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
+    const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
+    // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
+    g[0] -= TW(0) * base;
+    // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
+    // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
+    if (!__any_sync(FULL, t.ns > 0)) {
+        // no lane of the warp meets a solid at this node (uniform): plain BGK/TRT, and
+        // nothing to add to the held force sums
+        const float keep = TRT ? 1.0f - 0.5f * (omega + a.omega_m) : 1.0f - omega;
+        const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
         SolidSums m;
-        {
-            const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
-            const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
-            m.Bs = q0.B + q1.B;
-            m.Dx = b0x + b1x;
-            m.Dy = b0y + b1y;
-            m.Dz = b0z + b1z;
-            m.Qxx = b0x * d0x + b1x * d1x;
-            m.Qyy = b0y * d0y + b1y * d1y;
-            m.Qzz = b0z * d0z + b1z * d1z;
-            m.Qxy = b0x * d0y + b1x * d1y;
-            m.Qxz = b0x * d0z + b1x * d1z;
-            m.Qyz = b0y * d0z + b1y * d1z;
-            m.S = q0.B * d0s + q1.B * d1s;
-        }
-        if (psm_form(MODE) == PSM_AA_ODD && wwarp)
-            CollidePairs<SS, 1, true, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
-                                                            force_wa, m, pout + pl.cell, pl, valid);
+        m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
+        if (psm_form(MODE) == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
+            CollidePairs<SS, 1, false, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
+                                                             kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
         else
-            CollidePairs<SS, 1, true, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
-                                                             force_wa, m, pout + pl.cell, pl, valid);
-        {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
-            float out0 = TW(0) * base + keep0 * g[0];
-            if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
-            out0 += 1.5f * TW(0) * rho * m.S;
-            if (valid) SS::store(pout + pl.cell, out0, a.scale);
-        }
+            CollidePairs<SS, 1, false, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
+                                                              kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
+        float out0 = TW(0) * base + (1.0f - omega) * g[0];
+        if (a.has_force) out0 += a.guo_pref * TW(0) * (-3.0f * Fu);
+        if (valid) SS::store(pout + pl.cell, out0, a.scale);
+        return;
+    }
+    // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
+    SolidAt q0, q1;
+    q0.B = q1.B = 0.f;
+    q0.ux = q0.uy = q0.uz = q0.usq = q0.ax = q0.ay = q0.az = 0.f;
+    q1.ux = q1.uy = q1.uz = q1.usq = q1.ax = q1.ay = q1.az = 0.f;
+    q0.sx = q0.sy = q0.sz = q1.sx = q1.sy = q1.sz = 0.f;
+    if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
+    if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
+    const float Btot = fminf(q0.B + q1.B, 1.0f);
+    const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
+    const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
+    const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
+    const float force_w = (1.0f - Btot) * a.guo_pref;
+    const float force_wa = (1.0f - Btot) * a.guo_pref_m;
+    // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
+    const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
+    const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
+    SolidSums m;
+    {
+        const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
+        const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
+        m.Bs = q0.B + q1.B;
+        m.Dx = b0x + b1x;
+        m.Dy = b0y + b1y;
+        m.Dz = b0z + b1z;
+        m.Qxx = b0x * d0x + b1x * d1x;
+        m.Qyy = b0y * d0y + b1y * d1y;
+        m.Qzz = b0z * d0z + b1z * d1z;
+        m.Qxy = b0x * d0y + b1x * d1y;
+        m.Qxz = b0x * d0z + b1x * d1z;
+        m.Qyz = b0y * d0z + b1y * d1z;
+        m.S = q0.B * d0s + q1.B * d1s;
+    }
+    if (psm_form(MODE) == PSM_AA_ODD && wwarp)
+        CollidePairs<SS, 1, true, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
+                                                        force_wa, m, pout + pl.cell, pl, valid);
+    else
+        CollidePairs<SS, 1, true, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
+                                                         force_wa, m, pout + pl.cell, pl, valid);
+    {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
+        float out0 = TW(0) * base + keep0 * g[0];
+        if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
+        out0 += 1.5f * TW(0) * rho * m.S;
+        if (valid) SS::store(pout + pl.cell, out0, a.scale);
+    }
 
-        // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
-        // Down a column a thread rarely meets a second particle within one tile, so it
-        // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
-        // FP32 sums (native shared atomics; the FP64 shared form cost 2-3% of the kernel)
-        // only when some lane meets a different particle (and at the end of the tile); a
-        // second solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
-        {
-            const int key0 = t.ns > 0 ? t.e0 : -1;
-            float v0[6];
-            solid_force(q0, rho, d0x, d0y, d0z, a, v0);
-            // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
-            // held sum (the lane may meet the same particle again further down)
-            const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
-            if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
-            if (change) {
-                hkey = -1;
+    // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
+    // Down a column a thread rarely meets a second particle within one tile, so it
+    // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
+    // FP32 sums (native shared atomics; the FP64 shared form cost 2-3% of the kernel)
+    // only when some lane meets a different particle (and at the end of the tile); a
+    // second solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
+    {
+        const int key0 = t.ns > 0 ? t.e0 : -1;
+        float v0[6];
+        solid_force(q0, rho, d0x, d0y, d0z, a, v0);
+        // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
+        // held sum (the lane may meet the same particle again further down)
+        const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
+        if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
+        if (change) {
+            hkey = -1;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
-            }
-            if (key0 >= 0) {
+            for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
+        }
+        if (key0 >= 0) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) hacc[c] += v0[c];
-                hkey = key0;
-            }
-            if (__any_sync(FULL, t.ns > 1)) {
-                float v1[6];
-                solid_force(q1, rho, d1x, d1y, d1z, a, v1);
-                warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
-            }
+            for (int c = 0; c < 6; ++c) hacc[c] += v0[c];
+            hkey = key0;
+        }
+        if (__any_sync(FULL, t.ns > 1)) {
+            float v1[6];
+            solid_force(q1, rho, d1x, d1y, d1z, a, v1);
+            warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
         }
     }
-    warp_flush(tc, hkey, hacc);
-    cp_async_wait<0>();
-    __syncthreads();
-    for (int idx = tid; idx < 6 * cnt; idx += blockDim.x) {
+}
+
+// Per storage format and route: resident CTAs per SM the PSM kernel is compiled for (its
+// register budget) and, for the staged route, the stages in the ring (planes in flight +
+// the one being read). Chosen by timing the variants on GB300.
+template <int STORE, bool STAGED>
+struct PsmCfg {
+    static constexpr int minb = 3, stages = 4;
+};
+template <>
+struct PsmCfg<LEDDS_STORE_F32, true> {
+    static constexpr int minb = 2, stages = 4;
+};
+
+// Shared memory of the PSM kernel: the tile cache, then (staged route) the full and
+// empty barriers of each stage and the stages, 128-byte aligned in the shared window.
+template <int STORE, bool STAGED, bool SHIFT>
+struct PsmSmem {
+    static constexpr int S = PsmCfg<STORE, STAGED>::stages;
+    static constexpr size_t bars = (sizeof(TileCache) + 15) & ~(size_t)15;
+    static constexpr size_t stages = bars + 2 * S * sizeof(unsigned long long);
+    static constexpr size_t bytes =
+        STAGED ? stages + 128 + (size_t)S * Stage<(int)storage_bytes_c(STORE), SHIFT>::bytes : sizeof(TileCache);
+};
+
+// Node (x, y, z) needs no wrap and no bounce-back on any axis.
+__device__ __forceinline__ bool off_faces(const LbmArgs& a, int x, int y, int z) {
+    return x > 0 && x < a.nx - 1 && y > 0 && y < a.ny - 1 && z > 0 && z < a.nz - 1;
+}
+
+// Force and torque sums of the tile's particles to their FP64 totals (after a CTA barrier).
+__device__ __forceinline__ void tile_sums_out(const LbmArgs& a, const TileCache& tc, int cnt) {
+    for (int idx = threadIdx.x; idx < 6 * cnt; idx += blockDim.x) {
         int e = idx / 6, c = idx % 6;
         double v = (double)tc.acc[c][e];
         if (v != 0.0) {
@@ -872,41 +931,196 @@ __device__ __forceinline__ void psm_tile(const LbmArgs& a, int bx, int by, int b
     }
 }
 
+// One 32x8xTILE_Z tile (bx, by, bz), planes zlo .. zhi-1 of it, direct route: each
+// thread loads its node's 19 pulled values from global memory (independent loads, all
+// in flight at once).
 template <int STORE, bool TRT, int MODE>
-__global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE>::minb) k_psm(const LbmArgs a) {
-    extern __shared__ __align__(16) unsigned char psm_smem[];
+__device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by, int bz, int zlo, int zhi,
+                                                unsigned char* psm_smem) {
+    using SS = Store<STORE>;
+    using T = typename SS::T;
+    const T* pin = (const T*)a.pop_in;
+    T* pout = (T*)a.pop_out;
+    TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int tile = (bz * a.nty + by) * a.ntx + bx;
+    const int x = x0 + lane, y = y0 + warp;
+    const int cnt = min(a.tile_count[tile], a.tile_cap);
+    load_tile(a, tc, tile, cnt, x0, y0, z0);
+    __syncthreads();
+
+    int hkey = -1;
+    float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int iz = zlo; iz < zhi; ++iz) {
+        const int z = z0 + iz;
+        if (y >= a.ny || z >= a.nz) continue;  // uniform across the warp
+        const bool valid = x < a.nx;
+        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
+        Plan pl;
+        make_plan(a, valid ? x : 0, y, z, pl);
+        const bool gen = __any_sync(FULL, valid && !off_faces(a, x, y, z));
+        const bool wwarp = psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
+        float g[19];
+        if (valid) {
+            if (gen && psm_form(MODE) != PSM_AA_EVEN) pull_all<SS, true, MODE>(a, pin, pl, g);
+            else pull_all<SS, false, MODE>(a, pin, pl, g);
+        }
+        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, mask, lane, warp, iz, x, y, z, pout, hkey, hacc);
+    }
+    warp_flush(tc, hkey, hacc);
+    __syncthreads();
+    tile_sums_out(a, tc, cnt);
+}
+
+// The same tile, staged route. Thread 0 keeps S-1 planes of boxes in flight: before it
+// refills a stage it waits until every warp has read the plane held there (the stage's
+// empty barrier, one arrival per warp); each warp waits for the plane's boxes (the full
+// barrier, completed by the copy engine's byte count), reads its row into registers and
+// releases the stage before it collides. Rows on a y or z face of the lattice take the
+// direct route; in a tile at an x end, the end lanes re-pull their x-shifted directions.
+template <int STORE, bool TRT, int MODE>
+__device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps& m, int bx, int by, int bz,
+                                                int zlo, int zhi, unsigned char* psm_smem) {
+    using SS = Store<STORE>;
+    using T = typename SS::T;
+    constexpr int ES = (int)sizeof(T);
+    constexpr bool SHIFT = psm_form(MODE) != PSM_AA_EVEN;
+    using G = Stage<ES, SHIFT>;
+    using SM = PsmSmem<STORE, true, SHIFT>;
+    constexpr int S = SM::S;
+    const T* pin = (const T*)a.pop_in;
+    T* pout = (T*)a.pop_out;
+    TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
+    const uint32_t bar0 = smem_addr(psm_smem + SM::bars);  // full[s] at bar0 + 8 s, empty[s] at + 8 (S + s)
+    uint32_t st0 = smem_addr(psm_smem + SM::stages);
+    const uint32_t pad = (128u - (st0 & 127u)) & 127u;
+    st0 += pad;
+    const unsigned char* stg = psm_smem + SM::stages + pad;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int tile = (bz * a.nty + by) * a.ntx + bx;
+    const int x = x0 + lane, y = y0 + warp;
+    const int nplanes = min(zhi, a.nz - z0) - zlo;  // CTA-uniform
+    if (nplanes <= 0) return;
+    const bool xend = SHIFT && (x0 == 0 || x0 + TILE_X >= a.nx);  // CTA-uniform
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(bar0 + 8u * s, 1u);
+            mbar_init(bar0 + 8u * (S + s), (unsigned)TILE_Y);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int q = 0; q < S - 1 && q < nplanes; ++q)
+            issue_plane<ES, MODE>(m, st0 + (uint32_t)(q * G::bytes), bar0 + 8u * q, x0, y0, z0 + zlo + q);
+    const int cnt = min(a.tile_count[tile], a.tile_cap);
+    load_tile(a, tc, tile, cnt, x0, y0, z0);
+    __syncthreads();
+
+    int issued = min(S - 1, nplanes);  // thread 0 only
+    bool ok = true;
+    int hkey = -1;
+    float hacc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int r = 0;
+    for (; r < nplanes; ++r) {
+        const int s = r % S;
+        if (tid == 0 && ok && issued < nplanes) {
+            const int q = issued;  // = r + S - 1
+            const int sq = q % S;
+            if (q >= S) ok = mbar_wait(bar0 + 8u * (S + sq), (unsigned)((q / S - 1) & 1), a.status);
+            if (ok) {
+                issue_plane<ES, MODE>(m, st0 + (uint32_t)(sq * G::bytes), bar0 + 8u * sq, x0, y0, z0 + zlo + q);
+                ++issued;
+            }
+        }
+        const bool landed = __all_sync(FULL, mbar_wait(bar0 + 8u * s, (unsigned)((r / S) & 1), a.status));
+        if (!landed) break;  // uniform across the warp
+        const int iz = zlo + r, z = z0 + iz;
+        const bool valid = x < a.nx;
+        const bool row = y < a.ny;  // uniform
+        const bool face = SHIFT && (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1);  // uniform
+        float g[19];
+        if (row && !face) read_stage<SS, MODE>(a, stg + (size_t)s * G::bytes, lane, warp, g);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar0 + 8u * (S + s));
+        if (!row) continue;
+        Plan pl;
+        make_plan(a, valid ? x : 0, y, z, pl);
+        if (face) {
+            if (valid) pull_all<SS, true, MODE>(a, pin, pl, g);
+        } else if (xend) {
+            if (valid && (x == 0 || x == a.nx - 1)) fix_x_ends<SS, MODE>(a, pin, pl, g);
+        }
+        const bool wwarp = SHIFT && __any_sync(FULL, valid && pl.bw != 0u);
+        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
+        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, mask, lane, warp, iz, x, y, z, pout, hkey, hacc);
+    }
+    warp_flush(tc, hkey, hacc);
+    if (tid == 0) {
+        // after a timeout: wait (bounded) for the copies still in flight into this CTA's
+        // shared memory before the CTA ends
+        for (int q = r; q < issued; ++q) {
+            if (!mbar_wait(bar0 + 8u * (q % S), (unsigned)((q / S) & 1), a.status)) break;
+        }
+    }
+    __syncthreads();
+    tile_sums_out(a, tc, cnt);
+}
+
+template <int STORE, bool TRT, int MODE, bool STAGED>
+__global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE, STAGED>::minb)
+    k_psm(const __grid_constant__ LbmArgs a, const __grid_constant__ PsmMaps m) {
+    extern __shared__ __align__(128) unsigned char psm_smem[];
     // small lattices: a.zsplit CTAs share a tile, each taking TILE_Z / zsplit of its planes
     const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
-    psm_tile<STORE, TRT, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per, part * per + per,
-                               psm_smem);
+    if constexpr (STAGED)
+        psm_tile_staged<STORE, TRT, MODE>(a, m, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
+                                          part * per + per, psm_smem);
+    else
+        psm_tile_direct<STORE, TRT, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
+                                          part * per + per, psm_smem);
 }
 
 // Host side: launch k_psm in form MODE (its shared-memory size is set on first use), and
-// the dispatch over storage format and collision operator.
-template <int STORE, bool TRT, int MODE>
-static cudaError_t launch_psm_form(const LbmArgs& a, cudaStream_t s) {
+// the dispatch over storage format, collision operator and route (staged when maps are
+// given).
+template <int STORE, bool TRT, int MODE, bool STAGED>
+static cudaError_t launch_psm_form(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
     static bool configured = false;
-    const size_t smem = psm_smem_bytes(STORE);
+    constexpr size_t smem = PsmSmem<STORE, STAGED, psm_form(MODE) != PSM_AA_EVEN>::bytes;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_psm<STORE, TRT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_psm<STORE, TRT, MODE, STAGED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm<STORE, TRT, MODE><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a);
+    static const PsmMaps none{};
+    k_psm<STORE, TRT, MODE, STAGED><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a, m ? *m : none);
     return cudaGetLastError();
 }
 
+template <int STORE, bool TRT, int MODE>
+static cudaError_t launch_psm_route(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
+    if (m) return launch_psm_form<STORE, TRT, MODE, true>(a, m, s);
+    return launch_psm_form<STORE, TRT, MODE, false>(a, m, s);
+}
+
 template <int MODE>
-static cudaError_t launch_psm_mode(const LbmArgs& a, int store, cudaStream_t s) {
+static cudaError_t launch_psm_mode(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s) {
     if (a.trt) {
-        if (store == LEDDS_STORE_F32) return launch_psm_form<LEDDS_STORE_F32, true, MODE>(a, s);
-        if (store == LEDDS_STORE_F16) return launch_psm_form<LEDDS_STORE_F16, true, MODE>(a, s);
-        return launch_psm_form<LEDDS_STORE_BF16, true, MODE>(a, s);
+        if (store == LEDDS_STORE_F32) return launch_psm_route<LEDDS_STORE_F32, true, MODE>(a, m, s);
+        if (store == LEDDS_STORE_F16) return launch_psm_route<LEDDS_STORE_F16, true, MODE>(a, m, s);
+        return launch_psm_route<LEDDS_STORE_BF16, true, MODE>(a, m, s);
     }
-    if (store == LEDDS_STORE_F32) return launch_psm_form<LEDDS_STORE_F32, false, MODE>(a, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_form<LEDDS_STORE_F16, false, MODE>(a, s);
-    return launch_psm_form<LEDDS_STORE_BF16, false, MODE>(a, s);
+    if (store == LEDDS_STORE_F32) return launch_psm_route<LEDDS_STORE_F32, false, MODE>(a, m, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_route<LEDDS_STORE_F16, false, MODE>(a, m, s);
+    return launch_psm_route<LEDDS_STORE_BF16, false, MODE>(a, m, s);
 }
 
 }  // namespace ledds

@@ -9,10 +9,10 @@
 
 namespace ledds {
 
-cudaError_t launch_psm_aa(const LbmArgs& a, int store, cudaStream_t s) {
+cudaError_t launch_psm_aa(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s) {
     if (a.pop_in != a.pop_out) return cudaErrorInvalidValue;
-    if (a.aa == PSM_AA_EVEN) return launch_psm_mode<PSM_AA_EVEN>(a, store, s);
-    if (a.aa == PSM_AA_ODD) return launch_psm_mode<PSM_AA_ODD>(a, store, s);
+    if (a.aa == PSM_AA_EVEN) return launch_psm_mode<PSM_AA_EVEN>(a, m, store, s);
+    if (a.aa == PSM_AA_ODD) return launch_psm_mode<PSM_AA_ODD>(a, m, store, s);
     return cudaErrorInvalidValue;
 }
 

@@ -7,11 +7,11 @@
 
 namespace ledds {
 
-cudaError_t launch_psm_wide(const LbmArgs& a, int store, cudaStream_t s) {
-    if (a.aa == PSM_AB) return launch_psm_mode<PSM_AB | PSM_W64>(a, store, s);
+cudaError_t launch_psm_wide(const LbmArgs& a, const PsmMaps* m, int store, cudaStream_t s) {
+    if (a.aa == PSM_AB) return launch_psm_mode<PSM_AB | PSM_W64>(a, m, store, s);
     if (a.pop_in != a.pop_out) return cudaErrorInvalidValue;
-    if (a.aa == PSM_AA_EVEN) return launch_psm_mode<PSM_AA_EVEN | PSM_W64>(a, store, s);
-    if (a.aa == PSM_AA_ODD) return launch_psm_mode<PSM_AA_ODD | PSM_W64>(a, store, s);
+    if (a.aa == PSM_AA_EVEN) return launch_psm_mode<PSM_AA_EVEN | PSM_W64>(a, m, store, s);
+    if (a.aa == PSM_AA_ODD) return launch_psm_mode<PSM_AA_ODD | PSM_W64>(a, m, store, s);
     return cudaErrorInvalidValue;
 }
 

@@ -45,7 +45,7 @@ class ledds_params(C.Structure):
                 ("friction", C.c_double), ("skin", C.c_double), ("dem_h", C.c_double),
                 ("ell_max_iter", C.c_int), ("ell_tol", C.c_double),
                 ("force_fp32", C.c_int), ("collision", C.c_int), ("orient", C.c_int),
-                ("pattern", C.c_int), ("index64", C.c_int)]
+                ("pattern", C.c_int), ("index64", C.c_int), ("psm_route", C.c_int)]
 
 
 class ledds_particle(C.Structure):
@@ -58,7 +58,8 @@ class ledds_status(C.Structure):
     _fields_ = [("steps", C.c_longlong), ("tile_overflow", C.c_int), ("cand_overflow", C.c_int),
                 ("solids_overflow", C.c_int), ("skin_violation", C.c_int),
                 ("ell_nonconverged", C.c_int), ("nan_detected", C.c_int),
-                ("n_particles", C.c_int), ("launches_per_step", C.c_int)]
+                ("n_particles", C.c_int), ("launches_per_step", C.c_int), ("wait_timeout", C.c_int),
+                ("psm_staged", C.c_int)]
 
 
 VP = C.c_void_p
