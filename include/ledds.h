@@ -105,6 +105,12 @@ typedef struct {
                              /* the lattice suits it (rows a multiple of 16 bytes, nx >= 40   */
                              /* (FP32) / 48 (16-bit), ny >= 8), else direct; 1 always direct  */
                              /* per-thread loads. Both give identical results.                 */
+    int ell_screen;          /* 1 (default): before the common-normal iteration, two exact    */
+                             /* tests of disjointness (separating plane across the centre line, */
+                             /* Perram-Wertheim certificate) skip pairs that cannot touch; 0:   */
+                             /* the iteration alone decides, as Sec. 2.1 states the method. The */
+                             /* two differ only where the iteration does not converge on a pair */
+                             /* the tests prove disjoint (counted in ell_nonconverged).         */
 } ledds_params;
 
 /* One particle as given to ledds_set_particles (host memory). */
@@ -137,7 +143,7 @@ typedef struct ledds_sim_s* ledds_sim_t;
 
 /* Fill *p with defaults: tau 0.8, FP32 storage, distance voxels (subdiv_n 10), linear law,
  * n_sub 1, rho_f 1, no gravity/force, k_n 1000, k_t 2/7 k_n, restitution 0.7, friction
- * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision, triad orientation update, two population arrays. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
+ * 0.4, skin 0.5, ell_max_iter 60, ell_tol 1e-6, force_fp32 1, BGK collision, triad orientation update, two population arrays, staged PSM route where the lattice suits it, ellipsoid screens on. Returns LEDDS_ERR_INVALID_ARG if p is NULL. */
 int ledds_params_default(ledds_params* p);
 
 /* Bytes of device workspace a simulation of these dimensions and parameters needs

@@ -143,6 +143,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->pattern < 0 || p->pattern > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->index64 < 0 || p->index64 > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->psm_route < 0 || p->psm_route > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->ell_screen < 0 || p->ell_screen > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
             if (!(d->box_hi[a] > d->box_lo[a])) return LEDDS_ERR_INVALID_ARG;
@@ -406,6 +407,7 @@ static DemArgs dem_args(const ledds_sim_s* s) {
     A.skin = s->p.skin;
     A.ell_max_iter = s->p.ell_max_iter;
     A.ell_tol = s->p.ell_tol;
+    A.ell_screen = s->p.ell_screen;
     A.force_f32 = s->p.force_fp32;
     A.quat = s->p.orient == LEDDS_ORIENT_QUAT;
     A.pair_once = s->any_ellipsoid;
@@ -574,6 +576,7 @@ int ledds_params_default(ledds_params* p) {
     p->pattern = LEDDS_PATTERN_AB;
     p->index64 = 0;
     p->psm_route = 0;
+    p->ell_screen = 1;
     return LEDDS_OK;
 }
 

@@ -573,8 +573,12 @@ __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& 
     }
     double dist = norm3(dd);
     if (!((A.P.bound[a] + A.P.bound[b]) - dist > 0.0)) return false;
-    {   // separating plane across the centre line: supports |diag(s) R n| that do not reach
-        // across the centre distance mean no contact (same arithmetic as the reference)
+    // Screens (ell_screen, on by default): two exact tests of disjointness before the
+    // common-normal iteration; a pair either rejects is disjoint, so the iteration does not
+    // run for it (the iteration can fail to converge on such near-tangent pairs and then
+    // report a spurious overlap). Off: the iteration alone decides, as Sec. 2.1 states.
+    if (A.ell_screen) {   // separating plane across the centre line: supports |diag(s) R n|
+        // that do not reach across the centre distance mean no contact
         double n[3], h[2];
         for (int c = 0; c < 3; ++c) n[c] = dd[c] / dist;
         for (int k = 0; k < 2; ++k) {
@@ -599,7 +603,7 @@ __device__ bool pair_geo(const DemArgs& A, const double* st, int a, int b, Geo& 
     }
     tri_of(A, st, a, Ra_);
     tri_of(A, st, b, Rb_);
-    if (pw_separated(ra, Ra_, sa, rb, Rb_, sb)) return false;  // proven disjoint: no iteration
+    if (A.ell_screen && pw_separated(ra, Ra_, sa, rb, Rb_, sb)) return false;  // proven disjoint
     if (!ell_geo(A, ra, Ra_, sa, rb, Rb_, sb, g)) return false;
     return g.delta > 0.0;
 }

@@ -50,8 +50,11 @@ template <>
 struct Store<LEDDS_STORE_F32> {
     using T = float;
     static __device__ __forceinline__ float load(const T* p, float) { return *p; }
-    static __device__ __forceinline__ float ldg(const T* p, float) { return __ldg(p); }
-    static __device__ __forceinline__ float dec(T v, float) { return v; }
+    // stored units (the PSM kernel works on stored values and scales its moments)
+    static __device__ __forceinline__ float raw(T v) { return v; }
+    static __device__ __forceinline__ float ldg_raw(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ void store_raw(T* p, float v) { __stcs(p, v); }
+    static __device__ __forceinline__ float up(float v, float) { return v; }
     static __device__ __forceinline__ float from_bits(unsigned short, float) { return 0.f; }
     static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
 };
@@ -61,10 +64,14 @@ struct Store<LEDDS_STORE_F16> {
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __half2float(*p) * inv;
     }
-    static __device__ __forceinline__ float ldg(const T* p, float inv) {
-        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p)))) * inv;
+    static __device__ __forceinline__ float raw(T v) { return __half2float(v); }
+    static __device__ __forceinline__ float ldg_raw(const T* p) {
+        return __half2float(__ushort_as_half(__ldg(reinterpret_cast<const unsigned short*>(p))));
     }
-    static __device__ __forceinline__ float dec(T v, float inv) { return __half2float(v) * inv; }
+    static __device__ __forceinline__ void store_raw(T* p, float v) {
+        __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
+    }
+    static __device__ __forceinline__ float up(float v, float scale) { return v * scale; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
         return __half2float(__ushort_as_half(h)) * inv;
     }
@@ -79,10 +86,14 @@ struct Store<LEDDS_STORE_BF16> {
     static __device__ __forceinline__ float load(const T* p, float inv) {
         return __bfloat162float(*p) * inv;
     }
-    static __device__ __forceinline__ float ldg(const T* p, float inv) {
-        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p)))) * inv;
+    static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float ldg_raw(const T* p) {
+        return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
     }
-    static __device__ __forceinline__ float dec(T v, float inv) { return __bfloat162float(v) * inv; }
+    static __device__ __forceinline__ void store_raw(T* p, float v) {
+        __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    }
+    static __device__ __forceinline__ float up(float v, float scale) { return v * scale; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
         return __bfloat162float(__ushort_as_bfloat16(h)) * inv;
     }
@@ -218,6 +229,7 @@ struct DemArgs {
     double skin;
     int ell_max_iter;
     double ell_tol;
+    int ell_screen;   // exact disjointness screens before the ellipsoid iteration
     int force_f32;  // FP32 contact arithmetic, FP64 sums
     int quat;       // quaternion orientation update in the predictor
     // pair-once evaluation (simulations with ellipsoids): canonical pair counts, offsets

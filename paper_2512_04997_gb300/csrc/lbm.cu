@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const
         const LbmArgs& a = P.a[sim];
         const int t = item - P.tile_start[sim];
         const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
-        psm_tile_direct<STORE, TRT, PSM_AB>(a, bx, by, bz, 0, TILE_Z, smem);
+        psm_tile_direct<STORE, TRT, PSM_AB, false>(a, bx, by, bz, 0, TILE_Z, smem);
         __syncthreads();
     }
 }
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(256) k_voxelize(const LbmArgs a, float* beta, 
         Two t;
         t.ns = 0;
         t.total = 0;
-        if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+        if (mask) node_solids<false>(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
         if (!valid) continue;
         long long cell = x + (long long)a.nx * (y + (long long)a.ny * z);
         beta[2 * cell] = t.ns > 0 ? t.b0 : 0.f;

@@ -16,6 +16,14 @@ cudaError_t launch_psm_wide(const LbmArgs& a, const PsmMaps* m, int store, cudaS
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Explicitly rounded FP32 operations: the collision is written with these so that every
+// instantiation of the kernel (pull route, step form, offset width) rounds identically
+// (no contraction or reassociation left to the compiler).
+__device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mu(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ad(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
+
 // Moving-wall correction 6 t_i (c_i . u_w) (rho_w = 1) for a link that crossed walls;
 // with walls on two axes the wall of the higher axis (z, then y, then x) is used. The
 // side of each axis is fixed by the sign of c_i, so every parameter index is constant.
@@ -160,12 +168,12 @@ __device__ __forceinline__ int subdiv_count_warp(const TileCache& tc, int e, flo
 __device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& tc, int e, float dx, float dy,
                                             float dz, float R, bool* exact) {
     const int sh = tc.shape[e];
-    const float d2 = dx * dx + dy * dy + dz * dz;
+    const float d2 = fm(dz, dz, fm(dy, dy, mu(dx, dx)));
     *exact = false;
     if (sh == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) {
         // Eq. (naiveSolidFrac): (R + R_c - d) / (2 R_c), clamped
-        float dsc = R + a.Rc - sqrtf(d2);
-        return fminf(fmaxf(dsc * a.inv2Rc, 0.0f), 1.0f);
+        const float dsc = sb(ad(R, a.Rc), __fsqrt_rn(d2));
+        return fminf(fmaxf(mu(dsc, a.inv2Rc), 0.0f), 1.0f);
     }
     const int n = a.subdiv_n;
     const float h = (float)(n - 1) / (float)(2 * n);  // largest sample offset
@@ -278,6 +286,9 @@ static __device__ __noinline__ float subdiv_lanes(const LbmArgs& a, const TileCa
 
 // Called by the whole warp (the row mask is uniform); lanes with valid false take no part
 // beyond the warp-wide subdivision counts.
+// SPHD: every particle is a sphere with distance-based solid fractions (known at compile
+// time: the subdivision and ellipsoid code is left out).
+template <bool SPHD>
 __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
                                             unsigned long long mask, int lx, int ly, int lz, int x,
                                             int y, int z, bool valid, Two& t) {
@@ -292,11 +303,19 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& t
         float dx = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
         float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
         float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
-        bool exact = false;
-        float b = valid ? beta_quick(a, tc, e, dx, dy, dz, ps.w, &exact) : 0.0f;
-        if (a.subdiv_any) {  // uniform: distance-fraction spheres never need counts
-            const unsigned need = __ballot_sync(0xffffffffu, exact);
-            if (need) b = subdiv_lanes(a, tc, e, need, exact, x, y, z, b);  // uniform branch
+        float b;
+        if constexpr (SPHD) {
+            // Eq. (naiveSolidFrac), as in beta_quick
+            const float d2 = fm(dz, dz, fm(dy, dy, mu(dx, dx)));
+            const float dsc = sb(ad(ps.w, a.Rc), __fsqrt_rn(d2));
+            b = valid ? fminf(fmaxf(mu(dsc, a.inv2Rc), 0.0f), 1.0f) : 0.0f;
+        } else {
+            bool exact = false;
+            b = valid ? beta_quick(a, tc, e, dx, dy, dz, ps.w, &exact) : 0.0f;
+            if (a.subdiv_any) {  // uniform: distance-fraction spheres never need counts
+                const unsigned need = __ballot_sync(0xffffffffu, exact);
+                if (need) b = subdiv_lanes(a, tc, e, need, exact, x, y, z, b);  // uniform branch
+            }
         }
         if (!(b > 0.0f)) continue;
         t.total++;
@@ -310,24 +329,23 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& t
     }
 }
 
-// One solid's data at a node: B_k (Eq. bk), surface velocity u_k = v_k + w_k x (x - r_k),
-// the arm x - r_k, and the running sum of Omega^s_{i,k} c_i.
+// One solid's data at a node: B_k (Eq. bk), surface velocity u_k = v_k + w_k x (x - r_k)
+// and the arm x - r_k.
 struct SolidAt {
-    float B, ux, uy, uz, usq, ax, ay, az, sx, sy, sz;
+    float B, ux, uy, uz, ax, ay, az;
 };
 
 __device__ __forceinline__ void solid_at(const LbmArgs& a, const TileCache& tc, int e, float b, int lx,
-                                         int ly, int lz, float tau, SolidAt& q) {
+                                         int ly, int lz, SolidAt& q) {
     const float4 ps = tc.pos[e], vs = tc.vel[e], ws = tc.spin[e];
-    q.ax = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
-    q.ay = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
-    q.az = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
-    q.B = __fdividef(b * (tau - 0.5f), (1.0f - b) + (tau - 0.5f));
-    q.ux = vs.x + (ws.y * q.az - ws.z * q.ay);
-    q.uy = vs.y + (ws.z * q.ax - ws.x * q.az);
-    q.uz = vs.z + (ws.x * q.ay - ws.y * q.ax);
-    q.usq = q.ux * q.ux + q.uy * q.uy + q.uz * q.uz;
-    q.sx = q.sy = q.sz = 0.f;
+    q.ax = min_image_f(sb((float)lx, ps.x), a.mi[0], (float)a.nx);
+    q.ay = min_image_f(sb((float)ly, ps.y), a.mi[1], (float)a.ny);
+    q.az = min_image_f(sb((float)lz, ps.z), a.mi[2], (float)a.nz);
+    const float th = sb(a.tau, 0.5f);
+    q.B = __fdividef(mu(b, th), ad(sb(1.0f, b), th));
+    q.ux = ad(vs.x, sb(mu(ws.y, q.az), mu(ws.z, q.ay)));
+    q.uy = ad(vs.y, sb(mu(ws.z, q.ax), mu(ws.x, q.az)));
+    q.uz = ad(vs.z, sb(mu(ws.x, q.ay), mu(ws.y, q.ax)));
 }
 
 // Force and torque of one node-solid pair, Eqs. (forceSF), (torqueSF):
@@ -339,17 +357,17 @@ __device__ __forceinline__ void solid_force(const SolidAt& q, float rho, float d
                                             const LbmArgs& a, float v[6]) {
     const float fx = a.has_force ? a.F[0] : 0.f, fy = a.has_force ? a.F[1] : 0.f;
     const float fz = a.has_force ? a.F[2] : 0.f;
-    v[0] = q.B * (rho * dux - fx);
-    v[1] = q.B * (rho * duy - fy);
-    v[2] = q.B * (rho * duz - fz);
-    v[3] = q.ay * v[2] - q.az * v[1];
-    v[4] = q.az * v[0] - q.ax * v[2];
-    v[5] = q.ax * v[1] - q.ay * v[0];
+    v[0] = mu(q.B, sb(mu(rho, dux), fx));
+    v[1] = mu(q.B, sb(mu(rho, duy), fy));
+    v[2] = mu(q.B, sb(mu(rho, duz), fz));
+    v[3] = sb(mu(q.ay, v[2]), mu(q.az, v[1]));
+    v[4] = sb(mu(q.az, v[0]), mu(q.ax, v[2]));
+    v[5] = sb(mu(q.ax, v[1]), mu(q.ay, v[0]));
 }
 
 // Warp-aggregated addition of per-lane (key, 6 values) into the tile accumulators: one
 // butterfly per distinct key present in the warp (lanes with key < 0 take no part).
-__device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
+static __device__ __noinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
     const int lane = threadIdx.x & 31;
     unsigned pending = __ballot_sync(FULL, key >= 0);
     while (pending) {
@@ -470,27 +488,28 @@ __device__ __forceinline__ PsmIdx<MODE> src_elem(const LbmArgs& a, const Plan& p
 // The two-lattice pull reads an array the kernel does not write (read-only data path);
 // the AA pattern reads and writes one array.
 template <class SS, int MODE>
-__device__ __forceinline__ float ld_pop(const typename SS::T* p, float inv) {
-    if constexpr (psm_form(MODE) == PSM_AB) return SS::ldg(p, inv);
-    else return SS::load(p, inv);
+__device__ __forceinline__ float ld_pop(const typename SS::T* p) {
+    if constexpr (psm_form(MODE) == PSM_AB) return SS::ldg_raw(p);
+    else return SS::raw(*p);
 }
 
-// Direct pull of direction I of a node. GEN: periodic wraps and halfway bounce-back with
-// the moving-wall term, from the node's plan; without GEN the caller knows that neither
-// occurs for any lane (a node off every lattice face), and the source is node - off_I.
+// Direct pull of direction I of a node, in stored units. GEN: periodic wraps and halfway
+// bounce-back with the moving-wall term, from the node's plan; without GEN the caller
+// knows that neither occurs for any lane (a node off every lattice face), and the source
+// is node - off_I.
 template <class SS, int I, bool GEN, int MODE>
 __device__ __forceinline__ float pull_one(const LbmArgs& a, const typename SS::T* pin, const Plan& p) {
     if constexpr (!GEN) {
         constexpr int plane_in = psm_form(MODE) == PSM_AA_ODD ? OPP(I) : I;
         PsmIdx<MODE> src = (PsmIdx<MODE>)p.cell;
         if constexpr (psm_form(MODE) != PSM_AA_EVEN) src -= a.off[I];
-        return ld_pop<SS, MODE>(pin + (plane_at<MODE>(a, plane_in) + src), a.inv_scale);
+        return ld_pop<SS, MODE>(pin + (plane_at<MODE>(a, plane_in) + src));
     } else {
-        float v = ld_pop<SS, MODE>(pin + src_elem<I, true, MODE>(a, p), a.inv_scale);
+        float v = ld_pop<SS, MODE>(pin + src_elem<I, true, MODE>(a, p));
         if constexpr (psm_form(MODE) != PSM_AA_EVEN) {
             bool wx, wy, wz;
             link_walls<I>(p, wx, wy, wz);
-            if (wx || wy || wz) v += wall_term<I>(a.uw, wx, wy, wz);  // moving-wall bounce-back
+            if (wx || wy || wz) v += SS::up(wall_term<I>(a.uw, wx, wy, wz), a.scale);  // moving wall
         }
         return v;
     }
@@ -587,7 +606,7 @@ __device__ __forceinline__ void issue_plane(const PsmMaps& m, uint32_t stage, ui
     });
 }
 
-// A warp's row of the stage: g_I of the lane's node.
+// A warp's row of the stage: g_I of the lane's node, in stored units.
 template <class SS, int MODE>
 __device__ __forceinline__ void read_stage(const LbmArgs& a, const unsigned char* stage, int lane, int warp,
                                            float (&g)[19]) {
@@ -600,7 +619,7 @@ __device__ __forceinline__ void read_stage(const LbmArgs& a, const unsigned char
     static_for<19>([&](auto ic) {
         constexpr int I = decltype(ic)::value;
         const T v = G::wide(I) ? sb[G::slot(I) + ow - CX(I)] : sb[G::slot(I) + on];
-        g[I] = SS::dec(v, a.inv_scale);
+        g[I] = SS::raw(v);
     });
 }
 
@@ -626,28 +645,8 @@ __device__ __forceinline__ float cdot(float x, float y, float z) {
     return r;
 }
 
-// Solid terms of one node summed over its (at most two) solids k, with d_k = u - u_k:
-//   Bs = sum B_k, D = sum B_k d_k, Q = sum B_k d_k d_k^T, S = sum B_k (u^2 - u_k^2).
-// With e_k = c.d_k, sum_k B_k Omega^s_{i,k} needs only c.D and c^T Q c:
-//   sum_k B_k (geq_i(rho,u) - geq_i(rho,u_k)) = t rho (3 c.D + 9 (c.u)(c.D) - 4.5 c^T Q c - 1.5 S)
-// (from (c.u)^2 - (c.u_k)^2 = 2 (c.u) e_k - e_k^2), the antisymmetric part being 3 t rho c.D.
-struct SolidSums {
-    float Bs, Dx, Dy, Dz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, S;
-};
-
-template <int CXv, int CYv, int CZv>
-__device__ __forceinline__ float cqc(const SolidSums& m) {
-    float r = 0.0f;
-    if constexpr (CXv != 0) r += m.Qxx;
-    if constexpr (CYv != 0) r += m.Qyy;
-    if constexpr (CZv != 0) r += m.Qzz;
-    if constexpr (CXv != 0 && CYv != 0) r += (CXv * CYv > 0 ? 2.0f : -2.0f) * m.Qxy;
-    if constexpr (CXv != 0 && CZv != 0) r += (CXv * CZv > 0 ? 2.0f : -2.0f) * m.Qxz;
-    if constexpr (CYv != 0 && CZv != 0) r += (CYv * CZv > 0 ? 2.0f : -2.0f) * m.Qyz;
-    return r;
-}
-
-// Store of the post-collision f*_I(x) by a step of form MODE (WALLS as for src_elem):
+// Store of the post-collision f*_I(x) by a step of form MODE (WALLS as for src_elem); v
+// is in stored units (g times the storage scale):
 //   PSM_AB:      plane I at x of the other array;
 //   PSM_AA_EVEN: plane opp(I) at x, in place (the next step streams it);
 //   PSM_AA_ODD:  pushed to plane I at x + c_I, where the next step reads it in place, or,
@@ -657,16 +656,17 @@ __device__ __forceinline__ float cqc(const SolidSums& m) {
 template <class SS, int I, int MODE, bool WALLS>
 __device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS::T* node, float v) {
     if constexpr (psm_form(MODE) == PSM_AB) {
-        SS::store(node + plane_at<MODE>(a, I), v, a.scale);
+        SS::store_raw(node + plane_at<MODE>(a, I), v);
     } else if constexpr (psm_form(MODE) == PSM_AA_EVEN) {
-        SS::store(node + plane_at<MODE>(a, OPP(I)), v, a.scale);
+        SS::store_raw(node + plane_at<MODE>(a, OPP(I)), v);
     } else {
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         if constexpr (WALLS) {
             bool wx, wy, wz;
             link_walls<OPP(I)>(p, wx, wy, wz);
             if (wx || wy || wz) {
-                SS::store(node + plane_at<MODE>(a, OPP(I)), v + wall_term<OPP(I)>(a.uw, wx, wy, wz), a.scale);
+                SS::store_raw(node + plane_at<MODE>(a, OPP(I)),
+                              v + SS::up(wall_term<OPP(I)>(a.uw, wx, wy, wz), a.scale));
                 return;
             }
         }
@@ -677,200 +677,246 @@ __device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS
         if (cy == -1) d += p.wym;
         if (cz == 1) d += p.wzp;
         if (cz == -1) d += p.wzm;
-        SS::store(node + d, v, a.scale);
+        SS::store_raw(node + d, v);
     }
 }
 
-// Collision and store of the direction pair (I, I+1) (c_{I+1} = -c_I). On entry g holds
-// the pulled populations of the pair; the symmetric and antisymmetric parts of the
-// equilibrium and of the solid terms are shared by the two directions:
-//   geq_{I,I+1} = t (base + 4.5 rho cu^2 +/- 3 rho cu)
-//   sum_k B_k Omega^s_I     = Bs (neq_{I+1} - neq_I) - (dsym + dasym)
-//   sum_k B_k Omega^s_{I+1} = Bs (neq_I - neq_{I+1}) - (dsym - dasym)
-// with dsym = t rho (9 cu c.D - 4.5 c^T Q c - 1.5 S), dasym = 3 t rho c.D (SolidSums).
-// SOLID is uniform across the warp: false when no lane of the warp has a solid.
-// The force sum over the directions is not accumulated here: see solid_force.
-template <class SS, int I, bool SOLID, bool TRT, int MODE, bool WALLS>
-struct CollidePairs {
-    static __device__ __forceinline__ void run(float* g, float rho, float ux, float uy, float uz, float base,
-                                               const LbmArgs& a, float Fu, float force_w, float keep,
-                                               float kB, float force_wa, const SolidSums& m,
-                                               typename SS::T* node, const Plan& p, bool valid) {
+// ------------------------------------------------------------------------------------
+// The PSM collision in coefficient form. With g_i = f_i - t_i, the BGK or TRT collision
+// of the fluid part weighted by 1 - B_tot (Eqs. lbePS, TRT), the solid terms
+// sum_k B_k Omega^s_{i,k} (Eqs. psm1, bk, btot) and the Guo force term expand, direction
+// by direction, into
+//   g*_i = al g_i + ga g_ibar + t_i (q0 + c_i . q + c_i^T Q c_i)
+// with, for We = (1 - B_tot) w+, Wo = (1 - B_tot) w- (Wo = We for BGK), Bs = sum_k B_k,
+// V = sum_k B_k u_k, Y = sum_k B_k u_k u_k^T, Z = sum_k B_k u_k^2, E = We - Bs:
+//   al = 1 - (We + Wo)/2 - Bs,   ga = Bs - (We - Wo)/2,
+//   q0 = We drho - 1.5 rho (E u^2 + Z),   q = 3 rho ((Wo + Bs) u + V),
+//   Q  = 4.5 rho (E u u^T + Y),
+// and the force terms -3 fw u.F in q0, 3 fwa F in q, 4.5 fw (u F^T + F u^T) in Q
+// (fw = (1 - B_tot)(1 - w+/2), fwa the same with w-). The rest direction reduces to
+// (1 - We) g_0 + t_0 q0. (Obtained by writing neq_i = g_i - geq_i, splitting the fluid
+// relaxation into the parts even and odd in c, and expanding geq_i(rho, u) -
+// geq_i(rho, u_k) in c . u and c . u_k.) A node off every solid has Bs = V = Y = Z = 0.
+// Every quantity is kept in stored units (g times the storage scale), so 16-bit values
+// are used as loaded and stored as computed.
+// ------------------------------------------------------------------------------------
+struct Coef {
+    float al, ga, q0, qx, qy, qz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz;
+};
+
+// Solid sums of a node: Bs, B_tot and V, Y, Z of the coefficient form.
+struct SolidTerms {
+    float Bs, Btot, Vx, Vy, Vz, Yxx, Yyy, Yzz, Yxy, Yxz, Yyz, Z;
+};
+
+template <bool TRT, bool SOLID>
+__device__ __forceinline__ void node_coef(const LbmArgs& a, float sc, float drho, float rho, float ux, float uy,
+                                          float uz, float usq, const SolidTerms& m, Coef& k) {
+    const float Btot = SOLID ? m.Btot : 0.0f, Bs = SOLID ? m.Bs : 0.0f;
+    const float fl = sb(1.0f, Btot);  // weight of the fluid part
+    const float We = mu(fl, a.omega);
+    const float Wo = TRT ? mu(fl, a.omega_m) : We;
+    if constexpr (TRT) {
+        const float hs = mu(0.5f, ad(We, Wo)), hd = mu(0.5f, sb(We, Wo));
+        k.al = sb(sb(1.0f, hs), Bs);
+        k.ga = sb(Bs, hd);
+    } else {
+        k.al = sb(sb(1.0f, We), Bs);
+        k.ga = Bs;
+    }
+    const float E = sb(We, Bs);
+    const float rs = mu(rho, sc);
+    const float r15 = mu(1.5f, rs), r3 = mu(3.0f, rs), r45 = mu(4.5f, rs);
+    const float w3 = mu(r3, ad(Wo, Bs)), e45 = mu(r45, E);
+    const float Eu = SOLID ? fm(E, usq, m.Z) : mu(E, usq);
+    k.q0 = sb(mu(mu(sc, We), drho), mu(r15, Eu));
+    const float ex = mu(e45, ux), ey = mu(e45, uy), ez = mu(e45, uz);
+    if constexpr (SOLID) {
+        k.qx = fm(w3, ux, mu(r3, m.Vx));
+        k.qy = fm(w3, uy, mu(r3, m.Vy));
+        k.qz = fm(w3, uz, mu(r3, m.Vz));
+        k.Qxx = fm(ex, ux, mu(r45, m.Yxx));
+        k.Qyy = fm(ey, uy, mu(r45, m.Yyy));
+        k.Qzz = fm(ez, uz, mu(r45, m.Yzz));
+        k.Qxy = fm(ex, uy, mu(r45, m.Yxy));
+        k.Qxz = fm(ex, uz, mu(r45, m.Yxz));
+        k.Qyz = fm(ey, uz, mu(r45, m.Yyz));
+    } else {
+        k.qx = mu(w3, ux);
+        k.qy = mu(w3, uy);
+        k.qz = mu(w3, uz);
+        k.Qxx = mu(ex, ux);
+        k.Qyy = mu(ey, uy);
+        k.Qzz = mu(ez, uz);
+        k.Qxy = mu(ex, uy);
+        k.Qxz = mu(ex, uz);
+        k.Qyz = mu(ey, uz);
+    }
+    if (a.has_force) {  // uniform: Guo forcing, weighted by 1 - B_tot like the fluid part
+        const float fw = mu(mu(fl, a.guo_pref), sc);
+        const float fwa = TRT ? mu(mu(fl, a.guo_pref_m), sc) : fw;
+        const float Fx = a.F[0], Fy = a.F[1], Fz = a.F[2];
+        const float fw3 = mu(3.0f, fw), fa3 = mu(3.0f, fwa), f45 = mu(4.5f, fw), f9 = mu(9.0f, fw);
+        k.q0 = sb(k.q0, mu(fw3, fm(Fz, uz, fm(Fy, uy, mu(Fx, ux)))));
+        k.qx = fm(fa3, Fx, k.qx);
+        k.qy = fm(fa3, Fy, k.qy);
+        k.qz = fm(fa3, Fz, k.qz);
+        k.Qxx = fm(f9, mu(ux, Fx), k.Qxx);
+        k.Qyy = fm(f9, mu(uy, Fy), k.Qyy);
+        k.Qzz = fm(f9, mu(uz, Fz), k.Qzz);
+        k.Qxy = fm(f45, fm(ux, Fy, mu(Fx, uy)), k.Qxy);
+        k.Qxz = fm(f45, fm(ux, Fz, mu(Fx, uz)), k.Qxz);
+        k.Qyz = fm(f45, fm(uy, Fz, mu(Fy, uz)), k.Qyz);
+    }
+}
+
+// c . q and c^T Q c for a lattice vector c with components in {-1, 0, 1} known at compile
+// time, in a fixed order of explicitly rounded additions.
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cq(const Coef& k) {
+    float r = 0.0f;
+    bool first = true;
+    if constexpr (CXv != 0) { r = CXv > 0 ? k.qx : -k.qx; first = false; }
+    if constexpr (CYv != 0) { r = first ? (CYv > 0 ? k.qy : -k.qy) : (CYv > 0 ? ad(r, k.qy) : sb(r, k.qy)); first = false; }
+    if constexpr (CZv != 0) { r = first ? (CZv > 0 ? k.qz : -k.qz) : (CZv > 0 ? ad(r, k.qz) : sb(r, k.qz)); }
+    return r;
+}
+template <int CXv, int CYv, int CZv>
+__device__ __forceinline__ float cqqc(const Coef& k) {
+    // q0 + c^T Q c: diagonal terms, then the cross term of the two nonzero components
+    float r = k.q0;
+    if constexpr (CXv != 0) r = ad(r, k.Qxx);
+    if constexpr (CYv != 0) r = ad(r, k.Qyy);
+    if constexpr (CZv != 0) r = ad(r, k.Qzz);
+    if constexpr (CXv != 0 && CYv != 0) r = CXv * CYv > 0 ? fm(2.0f, k.Qxy, r) : fm(-2.0f, k.Qxy, r);
+    if constexpr (CXv != 0 && CZv != 0) r = CXv * CZv > 0 ? fm(2.0f, k.Qxz, r) : fm(-2.0f, k.Qxz, r);
+    if constexpr (CYv != 0 && CZv != 0) r = CYv * CZv > 0 ? fm(2.0f, k.Qyz, r) : fm(-2.0f, k.Qyz, r);
+    return r;
+}
+
+// Collision of every direction of one node and its stores: the rest direction, then the
+// nine pairs (I, I+1) with c_{I+1} = -c_I, which share t (q0 + c^T Q c) and flip c . q.
+template <class SS, int MODE, bool WALLS>
+__device__ __forceinline__ void collide_store(const LbmArgs& a, const float (&G)[19], const Coef& k,
+                                              const Plan& p, typename SS::T* node, bool valid) {
+    const float o0 = fm(ad(k.al, k.ga), G[0], mu(TW(0), k.q0));  // al + ga = 1 - We
+    if (valid) put<SS, 0, MODE, WALLS>(a, p, node, o0);
+    static_for<9>([&](auto ic) {
+        constexpr int I = 1 + 2 * decltype(ic)::value;
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         constexpr float t = TW(I);
-        const float cu = cdot<cx, cy, cz>(ux, uy, uz);
-        const float cu2 = cu * cu;
-        const float sym = base + 4.5f * rho * cu2;
-        const float asym = 3.0f * rho * cu;
-        const float n0 = g[I] - t * (sym + asym);       // neq_I
-        const float n1 = g[I + 1] - t * (sym - asym);   // neq_{I+1}
-        float o0 = t * (sym + asym) + keep * n0;
-        float o1 = t * (sym - asym) + keep * n1;
-        if constexpr (TRT) {  // the odd part of neq relaxes at the second rate
-            o0 += kB * n1;
-            o1 += kB * n0;
-        }
-        if (a.has_force) {
-            const float cF = cdot<cx, cy, cz>(a.F[0], a.F[1], a.F[2]);
-            // Guo term t [3 (c.F - u.F) + 9 (c.u)(c.F)]: c -> -c flips only 3 c.F
-            const float fs = force_w * t * (-3.0f * Fu + 9.0f * cu * cF);
-            const float fa = (TRT ? force_wa : force_w) * t * 3.0f * cF;
-            o0 += fs + fa;
-            o1 += fs - fa;
-        }
-        if constexpr (SOLID) {
-            const float cD = cdot<cx, cy, cz>(m.Dx, m.Dy, m.Dz);
-            const float trho = t * rho;
-            const float dsym = trho * (9.0f * cu * cD - 4.5f * cqc<cx, cy, cz>(m) - 1.5f * m.S);
-            const float dasym = 3.0f * trho * cD;
-            const float x = m.Bs * (n1 - n0);
-            o0 += x - (dsym + dasym);
-            o1 += -x - (dsym - dasym);
-        }
+        const float P = mu(t, cqqc<cx, cy, cz>(k));
+        const float A = mu(t, cq<cx, cy, cz>(k));
+        const float oi = fm(k.al, G[I], fm(k.ga, G[I + 1], ad(P, A)));
+        const float oj = fm(k.al, G[I + 1], fm(k.ga, G[I], sb(P, A)));
         if (valid) {
-            put<SS, I, MODE, WALLS>(a, p, node, o0);
-            put<SS, I + 1, MODE, WALLS>(a, p, node, o1);
+            put<SS, I, MODE, WALLS>(a, p, node, oi);
+            put<SS, I + 1, MODE, WALLS>(a, p, node, oj);
         }
-        CollidePairs<SS, I + 2, SOLID, TRT, MODE, WALLS>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
-                                                              force_wa, m, node, p, valid);
-    }
-};
-template <class SS, bool SOLID, bool TRT, int MODE, bool WALLS>
-struct CollidePairs<SS, 19, SOLID, TRT, MODE, WALLS> {
-    static __device__ __forceinline__ void run(float*, float, float, float, float, float, const LbmArgs&, float,
-                                               float, float, float, float, const SolidSums&, typename SS::T*,
-                                               const Plan&, bool) {}
-};
-
+    });
+}
 
 // ------------------------------------------------------------------------------------
-// The fused PSM step: pull, moments, solid fractions, PSM collision (Eqs. psm1, lbePS,
-// bk, btot), store, and the hydrodynamic force/torque of each solid (Eqs. forceSF,
-// torqueSF) reduced warp -> tile (shared FP32) -> particle (global FP64 atomics).
-// The collision is written around the non-equilibrium parts neq_i = g_i - geq_i:
-//   f*_i = geq_i + (1 - (1-B_tot)/tau) neq_i + sum_k B_k Omega^s_{i,k},
-//   Omega^s_{i,k} = neq_ibar - neq_i - (geq_i(rho,u) - geq_i(rho,u_k)).
+// The fused PSM step of one node: moments, solid fractions, PSM collision, store, and
+// the hydrodynamic force and torque of each solid (Eqs. forceSF, torqueSF) reduced warp
+// -> tile (shared FP32) -> particle (global FP64 atomics).
 // ------------------------------------------------------------------------------------
-// One node (x, y, z) = tile offset (lane, warp, iz) after its pull: g holds the pulled
-// populations. Entered by every lane of the warp together (the solid search and the
-// force sums are warp-cooperative); `valid` is false for lanes beyond the lattice, and
-// wwarp is true when some lane of the warp has a wall link. hkey/hacc: the running force
-// sum of the solid this lane last met down its column.
+// Node (x, y, z) = tile offset (lane, warp, iz) after its pull: G holds the pulled
+// populations in stored units and t its solids (node_solids). Entered by every lane of
+// the warp together (the force sums are warp-cooperative); `valid` is false for lanes
+// beyond the lattice, wwarp true when some lane of the warp has a wall link. hkey/hacc:
+// the running force sum of the solid this lane last met down its column.
 template <class SS, bool TRT, int MODE>
-__device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float (&g)[19], const Plan& pl,
-                                         bool valid, bool wwarp, unsigned long long mask, int lane, int warp,
-                                         int iz, int x, int y, int z, typename SS::T* pout, int& hkey,
-                                         float (&hacc)[6]) {
-    const float tau = a.tau, omega = a.omega;
+__device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float (&G)[19], const Plan& pl,
+                                         bool valid, bool wwarp, const Two& t, int lane, int warp, int iz,
+                                         typename SS::T* pout, int& hkey, float (&hacc)[6]) {
+    constexpr bool SCALED = sizeof(typename SS::T) == 2;
+    const float sc = SCALED ? a.scale : 1.0f;
     if (!valid) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) g[i] = 0.f;
+        for (int i = 0; i < 19; ++i) G[i] = 0.f;
     }
-    Two t;
-    t.ns = 0;
-    t.total = 0;
-    if (mask) node_solids(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
-    if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
-
     // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
-    const float drho = ((g[0] + (g[1] + g[2])) + ((g[3] + g[4]) + (g[5] + g[6]))) +
-                       (((g[7] + g[8]) + (g[9] + g[10])) + ((g[11] + g[12]) + (g[13] + g[14]))) +
-                       ((g[15] + g[16]) + (g[17] + g[18]));
-    float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
-    float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
-    float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
-    const float rho = 1.0f + drho;
+    float drho = ad(ad(ad(G[0], ad(G[1], G[2])), ad(ad(G[3], G[4]), ad(G[5], G[6]))),
+                    ad(ad(ad(ad(G[7], G[8]), ad(G[9], G[10])), ad(ad(G[11], G[12]), ad(G[13], G[14]))),
+                       ad(ad(G[15], G[16]), ad(G[17], G[18]))));
+    float jx = ad(ad(ad(sb(G[1], G[2]), sb(G[7], G[8])), ad(sb(G[9], G[10]), sb(G[11], G[12]))), sb(G[13], G[14]));
+    float jy = ad(ad(ad(sb(G[3], G[4]), sb(G[7], G[8])), ad(sb(G[10], G[9]), sb(G[15], G[16]))), sb(G[17], G[18]));
+    float jz = ad(ad(ad(sb(G[5], G[6]), sb(G[11], G[12])), ad(sb(G[14], G[13]), sb(G[15], G[16]))), sb(G[18], G[17]));
+    if constexpr (SCALED) {
+        drho = mu(drho, a.inv_scale);
+        jx = mu(jx, a.inv_scale);
+        jy = mu(jy, a.inv_scale);
+        jz = mu(jz, a.inv_scale);
+    }
+    const float rho = ad(1.0f, drho);
     if (a.has_force) {
-        jx += 0.5f * a.F[0];
-        jy += 0.5f * a.F[1];
-        jz += 0.5f * a.F[2];
+        jx = fm(0.5f, a.F[0], jx);
+        jy = fm(0.5f, a.F[1], jy);
+        jz = fm(0.5f, a.F[2], jz);
     }
-    const float inv_rho = 1.0f / rho;
-    const float ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    const float base = drho - rho * 1.5f * usq;
-
-    const float Fu = a.has_force ? a.F[0] * ux + a.F[1] * uy + a.F[2] * uz : 0.f;
-    // non-equilibrium part of the rest direction in place: g_0 <- g_0 - geq_0(rho, u)
-    g[0] -= TW(0) * base;
-    // fluid part weighted by 1 - B_tot (Eq. lbePS); TRT (Eq. TRT): the even part of neq
-    // relaxes at omega, the odd part at omega_m, i.e. neq_i -> keep neq_i + kB neq_ibar
-    if (!__any_sync(FULL, t.ns > 0)) {
-        // no lane of the warp meets a solid at this node (uniform): plain BGK/TRT, and
+    const float inv_rho = __frcp_rn(rho);
+    const float ux = mu(jx, inv_rho), uy = mu(jy, inv_rho), uz = mu(jz, inv_rho);
+    const float usq = fm(uz, uz, fm(uy, uy, mu(ux, ux)));
+    typename SS::T* node = pout + pl.cell;
+    Coef k;
+    const bool solid = __any_sync(FULL, t.ns > 0);  // uniform
+    if (!solid) {
+        // no lane of the warp meets a solid at this node: the plain fluid collision, and
         // nothing to add to the held force sums
-        const float keep = TRT ? 1.0f - 0.5f * (omega + a.omega_m) : 1.0f - omega;
-        const float kB = TRT ? -0.5f * (omega - a.omega_m) : 0.0f;
-        SolidSums m;
-        m.Bs = m.Dx = m.Dy = m.Dz = m.Qxx = m.Qyy = m.Qzz = m.Qxy = m.Qxz = m.Qyz = m.S = 0.f;
-        if (psm_form(MODE) == PSM_AA_ODD && wwarp)  // pushes that may return from a wall
-            CollidePairs<SS, 1, false, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
-                                                             kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
-        else
-            CollidePairs<SS, 1, false, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, a.guo_pref, keep,
-                                                              kB, a.guo_pref_m, m, pout + pl.cell, pl, valid);
-        float out0 = TW(0) * base + (1.0f - omega) * g[0];
-        if (a.has_force) out0 += a.guo_pref * TW(0) * (-3.0f * Fu);
-        if (valid) SS::store(pout + pl.cell, out0, a.scale);
-        return;
-    }
-    // B_k, B_tot (Eqs. bk, btot), u_k = v_k + w_k x (x - r_k)
-    SolidAt q0, q1;
-    q0.B = q1.B = 0.f;
-    q0.ux = q0.uy = q0.uz = q0.usq = q0.ax = q0.ay = q0.az = 0.f;
-    q1.ux = q1.uy = q1.uz = q1.usq = q1.ax = q1.ay = q1.az = 0.f;
-    q0.sx = q0.sy = q0.sz = q1.sx = q1.sy = q1.sz = 0.f;
-    if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, tau, q0);
-    if (t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, tau, q1);
-    const float Btot = fminf(q0.B + q1.B, 1.0f);
-    const float keep = TRT ? 1.0f - 0.5f * (1.0f - Btot) * (omega + a.omega_m) : 1.0f - (1.0f - Btot) * omega;
-    const float kB = TRT ? -0.5f * (1.0f - Btot) * (omega - a.omega_m) : 0.0f;
-    const float keep0 = 1.0f - (1.0f - Btot) * omega;  // rest direction: no odd part
-    const float force_w = (1.0f - Btot) * a.guo_pref;
-    const float force_wa = (1.0f - Btot) * a.guo_pref_m;
-    // solid k: d_k = u - u_k, u^2 - u_k^2 (B_k = 0 for a missing solid)
-    const float d0x = ux - q0.ux, d0y = uy - q0.uy, d0z = uz - q0.uz, d0s = usq - q0.usq;
-    const float d1x = ux - q1.ux, d1y = uy - q1.uy, d1z = uz - q1.uz, d1s = usq - q1.usq;
-    SolidSums m;
-    {
-        const float b0x = q0.B * d0x, b0y = q0.B * d0y, b0z = q0.B * d0z;
-        const float b1x = q1.B * d1x, b1y = q1.B * d1y, b1z = q1.B * d1z;
-        m.Bs = q0.B + q1.B;
-        m.Dx = b0x + b1x;
-        m.Dy = b0y + b1y;
-        m.Dz = b0z + b1z;
-        m.Qxx = b0x * d0x + b1x * d1x;
-        m.Qyy = b0y * d0y + b1y * d1y;
-        m.Qzz = b0z * d0z + b1z * d1z;
-        m.Qxy = b0x * d0y + b1x * d1y;
-        m.Qxz = b0x * d0z + b1x * d1z;
-        m.Qyz = b0y * d0z + b1y * d1z;
-        m.S = q0.B * d0s + q1.B * d1s;
-    }
-    if (psm_form(MODE) == PSM_AA_ODD && wwarp)
-        CollidePairs<SS, 1, true, TRT, MODE, true>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
-                                                        force_wa, m, pout + pl.cell, pl, valid);
-    else
-        CollidePairs<SS, 1, true, TRT, MODE, false>::run(g, rho, ux, uy, uz, base, a, Fu, force_w, keep, kB,
-                                                         force_wa, m, pout + pl.cell, pl, valid);
-    {   // rest direction: sum_k B_k Omega^s_0 = -sum_k B_k (geq_0(rho,u) - geq_0(rho,u_k)) = 1.5 t_0 rho S
-        float out0 = TW(0) * base + keep0 * g[0];
-        if (a.has_force) out0 += force_w * TW(0) * (-3.0f * Fu);
-        out0 += 1.5f * TW(0) * rho * m.S;
-        if (valid) SS::store(pout + pl.cell, out0, a.scale);
-    }
+        SolidTerms m;
+        node_coef<TRT, false>(a, sc, drho, rho, ux, uy, uz, usq, m, k);
+    } else {
+        // B_k (Eq. bk), surface velocities u_k = v_k + w_k x (x - r_k), sums over the solids
+        const bool two = __any_sync(FULL, t.ns > 1);  // uniform
+        SolidAt s0, s1;
+        s0.B = s1.B = 0.f;
+        s0.ux = s0.uy = s0.uz = s0.ax = s0.ay = s0.az = 0.f;
+        s1.ux = s1.uy = s1.uz = s1.ax = s1.ay = s1.az = 0.f;
+        if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, s0);
+        if (two && t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, s1);
+        SolidTerms m;
+        const float v0x = mu(s0.B, s0.ux), v0y = mu(s0.B, s0.uy), v0z = mu(s0.B, s0.uz);
+        m.Bs = s0.B;
+        m.Vx = v0x;
+        m.Vy = v0y;
+        m.Vz = v0z;
+        m.Yxx = mu(v0x, s0.ux);
+        m.Yyy = mu(v0y, s0.uy);
+        m.Yzz = mu(v0z, s0.uz);
+        m.Yxy = mu(v0x, s0.uy);
+        m.Yxz = mu(v0x, s0.uz);
+        m.Yyz = mu(v0y, s0.uz);
+        m.Z = fm(v0z, s0.uz, fm(v0y, s0.uy, mu(v0x, s0.ux)));
+        if (two) {
+            const float v1x = mu(s1.B, s1.ux), v1y = mu(s1.B, s1.uy), v1z = mu(s1.B, s1.uz);
+            m.Bs = ad(m.Bs, s1.B);
+            m.Vx = ad(m.Vx, v1x);
+            m.Vy = ad(m.Vy, v1y);
+            m.Vz = ad(m.Vz, v1z);
+            m.Yxx = fm(v1x, s1.ux, m.Yxx);
+            m.Yyy = fm(v1y, s1.uy, m.Yyy);
+            m.Yzz = fm(v1z, s1.uz, m.Yzz);
+            m.Yxy = fm(v1x, s1.uy, m.Yxy);
+            m.Yxz = fm(v1x, s1.uz, m.Yxz);
+            m.Yyz = fm(v1y, s1.uz, m.Yyz);
+            m.Z = fm(v1z, s1.uz, fm(v1y, s1.uy, fm(v1x, s1.ux, m.Z)));
+        }
+        m.Btot = fminf(m.Bs, 1.0f);
+        node_coef<TRT, true>(a, sc, drho, rho, ux, uy, uz, usq, m, k);
 
-    // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids.
-    // Down a column a thread rarely meets a second particle within one tile, so it
-    // keeps a running FP32 sum for the first solid and the warp flushes to the tile's
-    // FP32 sums (native shared atomics; the FP64 shared form cost 2-3% of the kernel)
-    // only when some lane meets a different particle (and at the end of the tile); a
-    // second solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
-    {
+        // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids,
+        // before the collision (they need only rho, u and the solids). Down a column a
+        // thread rarely meets a second particle within one tile, so it keeps a running
+        // FP32 sum for the first solid and the warp flushes to the tile's FP32 sums (native
+        // shared atomics) only when some lane meets a different particle (and at the end
+        // of the tile); a second solid in a node (rare) is flushed at once. Tiles add to
+        // FP64 totals.
         const int key0 = t.ns > 0 ? t.e0 : -1;
         float v0[6];
-        solid_force(q0, rho, d0x, d0y, d0z, a, v0);
-        // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
-        // held sum (the lane may meet the same particle again further down)
+        solid_force(s0, rho, sb(ux, s0.ux), sb(uy, s0.uy), sb(uz, s0.uz), a, v0);
+        // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the held
+        // sum (the lane may meet the same particle again further down)
         const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
         if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
         if (change) {
@@ -880,15 +926,17 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
         }
         if (key0 >= 0) {
 #pragma unroll
-            for (int c = 0; c < 6; ++c) hacc[c] += v0[c];
+            for (int c = 0; c < 6; ++c) hacc[c] = ad(hacc[c], v0[c]);
             hkey = key0;
         }
-        if (__any_sync(FULL, t.ns > 1)) {
+        if (two) {
             float v1[6];
-            solid_force(q1, rho, d1x, d1y, d1z, a, v1);
+            solid_force(s1, rho, sb(ux, s1.ux), sb(uy, s1.uy), sb(uz, s1.uz), a, v1);
             warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
         }
     }
+    if (psm_form(MODE) == PSM_AA_ODD && wwarp) collide_store<SS, MODE, true>(a, G, k, pl, node, valid);
+    else collide_store<SS, MODE, false>(a, G, k, pl, node, valid);
 }
 
 // Per storage format and route: resident CTAs per SM the PSM kernel is compiled for (its
@@ -896,11 +944,9 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
 // the one being read). Chosen by timing the variants on GB300.
 template <int STORE, bool STAGED>
 struct PsmCfg {
-    static constexpr int minb = 3, stages = 4;
-};
-template <>
-struct PsmCfg<LEDDS_STORE_F32, true> {
-    static constexpr int minb = 2, stages = 4;
+    static constexpr bool F32 = STORE == LEDDS_STORE_F32;
+    static constexpr int minb = STAGED ? (F32 ? 2 : 3) : 3;
+    static constexpr int stages = F32 ? 4 : 4;
 };
 
 // Shared memory of the PSM kernel: the tile cache, then (staged route) the full and
@@ -934,7 +980,7 @@ __device__ __forceinline__ void tile_sums_out(const LbmArgs& a, const TileCache&
 // One 32x8xTILE_Z tile (bx, by, bz), planes zlo .. zhi-1 of it, direct route: each
 // thread loads its node's 19 pulled values from global memory (independent loads, all
 // in flight at once).
-template <int STORE, bool TRT, int MODE>
+template <int STORE, bool TRT, int MODE, bool SPHD>
 __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by, int bz, int zlo, int zhi,
                                                 unsigned char* psm_smem) {
     using SS = Store<STORE>;
@@ -967,7 +1013,13 @@ __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by
             if (gen && psm_form(MODE) != PSM_AA_EVEN) pull_all<SS, true, MODE>(a, pin, pl, g);
             else pull_all<SS, false, MODE>(a, pin, pl, g);
         }
-        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, mask, lane, warp, iz, x, y, z, pout, hkey, hacc);
+        // the node's solids while its loads are in flight
+        Two t;
+        t.ns = 0;
+        t.total = 0;
+        if (mask) node_solids<SPHD>(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+        if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
+        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
     warp_flush(tc, hkey, hacc);
     __syncthreads();
@@ -980,7 +1032,7 @@ __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by
 // barrier, completed by the copy engine's byte count), reads its row into registers and
 // releases the stage before it collides. Rows on a y or z face of the lattice take the
 // direct route; in a tile at an x end, the end lanes re-pull their x-shifted directions.
-template <int STORE, bool TRT, int MODE>
+template <int STORE, bool TRT, int MODE, bool SPHD>
 __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps& m, int bx, int by, int bz,
                                                 int zlo, int zhi, unsigned char* psm_smem) {
     using SS = Store<STORE>;
@@ -1039,11 +1091,20 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
                 ++issued;
             }
         }
-        const bool landed = __all_sync(FULL, mbar_wait(bar0 + 8u * s, (unsigned)((r / S) & 1), a.status));
-        if (!landed) break;  // uniform across the warp
         const int iz = zlo + r, z = z0 + iz;
         const bool valid = x < a.nx;
         const bool row = y < a.ny;  // uniform
+        // the node's solids (from the tile cache) while the plane's boxes are in flight
+        Two t;
+        t.ns = 0;
+        t.total = 0;
+        if (row && cnt) {
+            const unsigned long long mask = row_mask(a, tc, cnt, warp, iz);
+            if (mask) node_solids<SPHD>(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
+            if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
+        }
+        const bool landed = __all_sync(FULL, mbar_wait(bar0 + 8u * s, (unsigned)((r / S) & 1), a.status));
+        if (!landed) break;  // uniform across the warp
         const bool face = SHIFT && (y == 0 || y == a.ny - 1 || z == 0 || z == a.nz - 1);  // uniform
         float g[19];
         if (row && !face) read_stage<SS, MODE>(a, stg + (size_t)s * G::bytes, lane, warp, g);
@@ -1058,8 +1119,7 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
             if (valid && (x == 0 || x == a.nx - 1)) fix_x_ends<SS, MODE>(a, pin, pl, g);
         }
         const bool wwarp = SHIFT && __any_sync(FULL, valid && pl.bw != 0u);
-        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
-        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, mask, lane, warp, iz, x, y, z, pout, hkey, hacc);
+        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
     warp_flush(tc, hkey, hacc);
     if (tid == 0) {
@@ -1073,42 +1133,52 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
     tile_sums_out(a, tc, cnt);
 }
 
-template <int STORE, bool TRT, int MODE, bool STAGED>
+template <int STORE, bool TRT, int MODE, bool STAGED, bool SPHD>
 __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE, STAGED>::minb)
     k_psm(const __grid_constant__ LbmArgs a, const __grid_constant__ PsmMaps m) {
     extern __shared__ __align__(128) unsigned char psm_smem[];
     // small lattices: a.zsplit CTAs share a tile, each taking TILE_Z / zsplit of its planes
     const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
     if constexpr (STAGED)
-        psm_tile_staged<STORE, TRT, MODE>(a, m, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
-                                          part * per + per, psm_smem);
+        psm_tile_staged<STORE, TRT, MODE, SPHD>(a, m, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
+                                                part * per + per, psm_smem);
     else
-        psm_tile_direct<STORE, TRT, MODE>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
-                                          part * per + per, psm_smem);
+        psm_tile_direct<STORE, TRT, MODE, SPHD>(a, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
+                                                part * per + per, psm_smem);
 }
 
 // Host side: launch k_psm in form MODE (its shared-memory size is set on first use), and
-// the dispatch over storage format, collision operator and route (staged when maps are
-// given).
-template <int STORE, bool TRT, int MODE, bool STAGED>
+// the dispatch over storage format, collision operator, route (staged when maps are
+// given) and particle geometry (spheres with distance fractions only, or any; lattices
+// with 64-bit offsets take the general form).
+template <int STORE, bool TRT, int MODE, bool STAGED, bool SPHD>
 static cudaError_t launch_psm_form(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
     static bool configured = false;
     constexpr size_t smem = PsmSmem<STORE, STAGED, psm_form(MODE) != PSM_AA_EVEN>::bytes;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_psm<STORE, TRT, MODE, STAGED>,
+        cudaError_t e = cudaFuncSetAttribute(k_psm<STORE, TRT, MODE, STAGED, SPHD>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     static const PsmMaps none{};
-    k_psm<STORE, TRT, MODE, STAGED><<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a, m ? *m : none);
+    k_psm<STORE, TRT, MODE, STAGED, SPHD>
+        <<<dim3(a.ntx, a.nty, a.ntz * a.zsplit), PSM_THREADS, smem, s>>>(a, m ? *m : none);
     return cudaGetLastError();
+}
+
+template <int STORE, bool TRT, int MODE, bool STAGED>
+static cudaError_t launch_psm_geom(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
+    if constexpr (!psm_w64(MODE)) {
+        if (!a.subdiv_any) return launch_psm_form<STORE, TRT, MODE, STAGED, true>(a, m, s);
+    }
+    return launch_psm_form<STORE, TRT, MODE, STAGED, false>(a, m, s);
 }
 
 template <int STORE, bool TRT, int MODE>
 static cudaError_t launch_psm_route(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
-    if (m) return launch_psm_form<STORE, TRT, MODE, true>(a, m, s);
-    return launch_psm_form<STORE, TRT, MODE, false>(a, m, s);
+    if (m) return launch_psm_geom<STORE, TRT, MODE, true>(a, m, s);
+    return launch_psm_geom<STORE, TRT, MODE, false>(a, m, s);
 }
 
 template <int MODE>

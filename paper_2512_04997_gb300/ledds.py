@@ -45,7 +45,8 @@ class ledds_params(C.Structure):
                 ("friction", C.c_double), ("skin", C.c_double), ("dem_h", C.c_double),
                 ("ell_max_iter", C.c_int), ("ell_tol", C.c_double),
                 ("force_fp32", C.c_int), ("collision", C.c_int), ("orient", C.c_int),
-                ("pattern", C.c_int), ("index64", C.c_int), ("psm_route", C.c_int)]
+                ("pattern", C.c_int), ("index64", C.c_int), ("psm_route", C.c_int),
+                ("ell_screen", C.c_int)]
 
 
 class ledds_particle(C.Structure):

@@ -285,17 +285,14 @@ def test_dem_forces_and_trajectories(oracle, fp32):
     assert np.abs(vo).max() > 1e-3             # the pile is moving
 
 
-@pytest.mark.parametrize("fp32,orient", [(0, "triad"), (1, "triad"), (0, "quat"), (1, "quat")])
-def test_dem_ellipsoids_hertz(oracle, fp32, orient):
-    """Ellipsoid contacts (common-normal iteration, FP64 in both modes) with the Hertz law
-    and walls; orientations integrated by the triad update or by the quaternion option."""
+def _ellipsoid_pile(fp32, orient, screen):
     g = W.rng(604)
     n = 500
     box = (30.0, 30.0, 30.0)
     w = W.Workload(name="ell", box_lo=(0, 0, 0), box_hi=box, periodic=(1, 0, 0))
     w.params = W.base_params(law="hertz", young=5.0, poisson=0.3, restitution=0.8, friction=0.3,
                              rho_f=0.0, gravity=(0, 0, -1e-3), dem_h=2 * 1.5 + 0.3, skin=0.3,
-                             force_fp32=fp32, orient=orient)
+                             force_fp32=fp32, orient=orient, ell_screen=screen)
     semi = np.array([1.5, 0.8, 0.6])
     w.shape = np.ones(n, dtype=np.int32)
     w.semi = np.tile(semi, (n, 1))
@@ -305,6 +302,62 @@ def test_dem_ellipsoids_hertz(oracle, fp32, orient):
     w.vel = g.normal(0, 0.02, (n, 3))
     w.omg = g.normal(0, 0.01, (n, 3))
     w.triad = W.quaternion_to_triad(W.random_quaternions(g, n))
+    return w
+
+
+def _pairs_of(keys):
+    return {(int(k) >> 32, int(k) & 0xffffffff) for k in keys}
+
+
+def test_dem_ellipsoid_screens_from_identical_state(oracle):
+    """The kernel's default decision (exact disjointness screens, then the iteration)
+    against the oracle's (the iteration alone, Sec. 2.1) at identical states: snapshots of
+    a GPU run of a dense ellipsoid pile, uploaded into the oracle. Every pair the oracle
+    finds and the kernel does not is one where the oracle's iteration did not converge and
+    the pair is proven disjoint; the kernel finds no pair the oracle does not."""
+    w = _ellipsoid_pile(0, "triad", 1)
+    s = gpu_from_workload(w)
+    semi = w.semi[0]
+    listed = []
+    common = 0
+    for snap in range(4):
+        s.step(20)
+        pg = _pairs_of(s.pairs())
+        pos, vel, omg, tri = s.particles()
+        o = oracle_from_workload(oracle, w)
+        o.set_particles(w.shape, w.radius, w.semi, w.density, pos, vel, omg, tri)
+        o.contact_forces(1.0)
+        po = _pairs_of(o.contacts())
+        assert pg <= po, pg - po
+        common += len(pg)
+        for i, j in sorted(po - pg):
+            d = pos[j] - pos[i]
+            d[0] -= 30.0 * np.round(d[0] / 30.0)
+            c = oracle.ellipsoid_contact(pos[i], tri[i], semi, pos[i] + d, tri[j], semi,
+                                         max_iter=w.params["ell_max_iter"], tol=w.params["ell_tol"])
+            assert c["rc"] == 1, (i, j, c)                       # not converged
+            assert oracle.pw_separated(pos[i], tri[i], semi, pos[i] + d, tri[j], semi) or \
+                _plane_separated(pos[i], tri[i], semi, pos[i] + d, tri[j], semi), (i, j)
+            listed.append((snap, i, j, round(c["delta"], 4)))
+    print(f"pairs in both: {common}; oracle-only (iteration not converged, proven disjoint): {listed}")
+    assert common > 20
+
+
+def _plane_separated(ri, Ri, si, rj, Rj, sj):
+    d = rj - ri
+    dist = np.linalg.norm(d)
+    n = d / dist
+    h = sum(np.linalg.norm(sv * (np.reshape(R, (3, 3)) @ n)) for R, sv in ((Ri, si), (Rj, sj)))
+    return h < dist * (1.0 - 1e-12)
+
+
+@pytest.mark.parametrize("fp32,orient", [(0, "triad"), (1, "triad"), (0, "quat"), (1, "quat")])
+def test_dem_ellipsoids_hertz(oracle, fp32, orient):
+    """Ellipsoid contacts (common-normal iteration, FP64 in both modes) with the Hertz law
+    and walls; orientations integrated by the triad update or by the quaternion option. The
+    kernel's screens are off (ell_screen 0), so both sides decide contacts by the iteration
+    alone and follow the same trajectory."""
+    w = _ellipsoid_pile(fp32, orient, 0)
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
     o.step(80)
