@@ -159,6 +159,7 @@ def ensemble_measure(args, device, stream):
     b = ledds.batch_from_workloads(ws, device=device)
     b.step(args.warmup)
     choice = b.autotune(steps_per_trial=2)
+    cfg = b.config()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -193,8 +194,14 @@ def ensemble_measure(args, device, stream):
             "sims": len(ws), "cells": cells, "particles": int(sum(w.n for w in ws)),
             "separate_sims_MLUPS": cells * args.steps / (serial_ms * 1e-3) / 1e6,
             "speedup_vs_separate_sims": serial_ms / ms,
-            "launches_per_step": 4, "autotune_choice": {"psm_ctas_per_sm": choice // 2 + 1,
-                                                         "order": ["member", "largest_first"][choice % 2]},
+            "launches_per_step": 4,
+            "autotune_choice": {"index": choice, "tile": f"32x8x{cfg['tile_depth']}",
+                                "psm_ctas_per_sm": cfg["ctas_per_sm"],
+                                "order": ["member", "largest_first"][cfg["order"]]},
+            # the whole step against the 16-bit algorithmic bytes of every member's cells
+            "roofline": {"achieved": cells * 76 / (ms / args.steps * 1e-3) / 1e9, "unit": "GB/s",
+                         "frac": cells * 76 / (ms / args.steps * 1e-3) / 1e9 / peaks()[0],
+                         "note": "coupled step time (DEM, binning, PSM), not the PSM kernel alone"},
             "status": bad}
 
 

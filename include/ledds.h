@@ -284,13 +284,25 @@ int ledds_batch_step(ledds_batch_t b, int n_steps);
 /* Release the batch and its members' host objects (the workspace stays the caller's). */
 int ledds_batch_destroy(ledds_batch_t b);
 
-/* Autotuner of the batched launch: tries every combination of resident PSM CTAs per SM
- * (1 up to the compiled register budget) and PSM work order (member order, or largest
- * members first), times steps_per_trial steps of each with CUDA events after two warm-up
- * steps, and keeps the fastest. The trial steps are real steps: they advance every member
- * (each candidate computes the same step). *choice (may be NULL) receives the index
- * (ctas_per_sm - 1) * 2 + order of the choice. Synchronous. The tile shape (32 x 8 x 16) is
- * fixed at compile time. Errors: INVALID_ARG, CUDA, and those of ledds_batch_step. */
+/* Launch shape of the batched step (BJ config 5's "autotuned tiles"; the paper has no
+ * batches): tile_depth planes per lattice tile (8, 16 or 32; tiles are 32 x 8 x depth
+ * nodes, one CTA's work item), ctas_per_sm resident PSM CTAs per SM (1 up to the
+ * compiled register budget, ledds_batch_get_config of a new batch reports it) and the PSM
+ * work order (0 member order, 1 largest members first). Results do not depend on it
+ * beyond the order of the hydrodynamic force sums. Default 16, the budget, 0. Errors:
+ * INVALID_ARG. */
+int ledds_batch_configure(ledds_batch_t b, int tile_depth, int ctas_per_sm, int order);
+int ledds_batch_get_config(ledds_batch_t b, int* tile_depth, int* ctas_per_sm, int* order);
+
+/* Autotuner of the batched launch: tries every launch shape (tile depth 8, 16, 32 x
+ * resident CTAs per SM x work order), times steps_per_trial steps of each with CUDA events
+ * after two warm-up steps, and keeps the fastest. The trial steps are real steps: they
+ * advance every member (each candidate computes the same step). The choice is cached
+ * for the process by the batch's shape (members' dimensions and particle counts, storage,
+ * collision): a later batch of the same shape takes it without trials (and without
+ * steps). *choice (may be NULL) receives its index ((depth index x ctas budget + ctas_per_sm
+ * - 1) x 2 + order; ledds_batch_get_config gives the values). Synchronous. Errors:
+ * INVALID_ARG, CUDA, and those of ledds_batch_step. */
 int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice);
 
 /* Cell keys and (key, id)-sorted particle ids of the DEM grid, computed without any

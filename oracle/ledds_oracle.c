@@ -479,6 +479,48 @@ static cell_solids* compute_solids(const or_sim* s) {
     return cs;
 }
 
+/* The solids of one node as compute_solids finds them (the same particle order, the same
+ * bounding boxes with their periodic images, the same top-two selection), for spot checks
+ * on lattices too large to voxelise whole. A periodic axis counts every image of the
+ * node inside a particle's box, as the box loop does. */
+void or_solids_at(const or_sim* s, int x, int y, int z, int ids[2], double beta[2], int* total) {
+    cell_solids cs;
+    memset(&cs, 0, sizeof(cs));
+    int n3[3] = {s->nx, s->ny, s->nz};
+    int node[3] = {x, y, z};
+    for (int k = 0; k < s->n; ++k) {
+        const double* r = s->pos + 3 * k;
+        double e = s->bound[k] + 1.0;
+        if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) continue;
+        long long mult = 1;
+        for (int a = 0; a < 3; ++a) {
+            long long lo = (long long)ceil(r[a] - e), hi = (long long)floor(r[a] + e);
+            long long m;
+            if (s->periodic[a]) {
+                /* integers q in [lo, hi] with q = node (mod n) */
+                long long n = n3[a];
+                long long first = (long long)ceil((double)(lo - node[a]) / (double)n);
+                long long last = (long long)floor((double)(hi - node[a]) / (double)n);
+                m = last >= first ? last - first + 1 : 0;
+            } else {
+                m = (lo <= node[a] && node[a] <= hi) ? 1 : 0;
+            }
+            mult *= m;
+        }
+        if (mult == 0) continue;
+        double rel[3];
+        for (int a = 0; a < 3; ++a) rel[a] = min_image(s, a, (double)node[a] - r[a]);
+        double b = beta_of(s, k, rel);
+        if (b > 0.0)
+            for (long long q = 0; q < mult; ++q) solids_insert(&cs, k, b);
+    }
+    for (int m = 0; m < 2; ++m) {
+        ids[m] = m < cs.ns ? cs.id[m] : -1;
+        beta[m] = m < cs.ns ? cs.beta[m] : 0.0;
+    }
+    *total = cs.total;
+}
+
 void or_voxelize(or_sim* s, double* beta2, int* id2, int* nsolid) {
     cell_solids* cs = compute_solids(s);
     for (long long c = 0; c < s->ncell; ++c) {

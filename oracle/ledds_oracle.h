@@ -106,6 +106,7 @@ int  or_ellipsoid_contact(const double ri[3], const double Ri[9], const double s
                           double cp[3], double* rho_i, double* rho_j, int* iters);
 /* 1 if a Perram-Wertheim certificate shows the two ellipsoids disjoint (F(l) > 1 + 1e-9
  * at one of at most 16 golden-section points), else 0. */
+void or_solids_at(const or_sim* s, int x, int y, int z, int ids[2], double beta[2], int* total);
 int  or_threads(void); /* 1, or the OpenMP team size of the timing build */
 int  or_pw_separated(const double ri[3], const double Ri[9], const double si[3],
                      const double rj[3], const double Rj[9], const double sj[3]);

@@ -92,6 +92,7 @@ def lib(parallel=False):
         L.or_ellipsoid_contact.argtypes = [dp, dp, dp, dp, dp, dp, C.c_int, C.c_double,
                                            dp, dp, dp, dp, dp, ip]
         L.or_status.argtypes = [C.c_void_p, lp]
+        L.or_solids_at.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, ip, dp, ip]
         L.or_threads.restype = C.c_int
         L.or_threads.argtypes = []
         _libs[parallel] = L
@@ -218,6 +219,14 @@ class Sim:
 
     def contact_forces(self, dt):
         self._L.or_contact_forces(self._h, float(dt))
+
+    def solids_at(self, x, y, z):
+        """(ids[2], betas[2], total) of node (x, y, z): the voxelisation of one node."""
+        ids = np.zeros(2, dtype=np.int32)
+        b = np.zeros(2)
+        t = np.zeros(1, dtype=np.int32)
+        self._L.or_solids_at(self._h, int(x), int(y), int(z), ids, b, t)
+        return ids, b, int(t[0])
 
     def voxelize(self):
         beta = np.zeros(2 * self.ncell)

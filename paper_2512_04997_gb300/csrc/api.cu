@@ -10,6 +10,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.cuh"
@@ -23,12 +25,12 @@ cudaError_t launch_psm(const LbmArgs&, const PsmMaps*, int, cudaStream_t);
 cudaError_t launch_voxelize(const LbmArgs&, float*, int*, int*, cudaStream_t);
 cudaError_t launch_rebuild(const DemArgs&, int, int, int, uint32_t*, cudaStream_t, int*);
 cudaError_t launch_predict_first(const DemArgs&, cudaStream_t);
-cudaError_t launch_substep(const DemArgs&, int, int, int, int, int, cudaStream_t);
+cudaError_t launch_substep(const DemArgs&, int, int, int, int, int*, cudaStream_t);
 cudaError_t launch_final(const DemArgs&, int, int, cudaStream_t);
 cudaError_t launch_pairs(const DemArgs&, int, uint32_t*, uint32_t*, uint32_t*, unsigned long long*,
                          int, cudaStream_t);
 cudaError_t launch_scan(const uint32_t*, int, uint32_t*, uint32_t*, cudaStream_t);
-cudaError_t launch_psm_batch(const BatchChunk&, int*, int, int, cudaStream_t);
+cudaError_t launch_psm_batch(const BatchChunk&, int*, int, int, bool, cudaStream_t);
 cudaError_t launch_bin_batch(const LbmArgs*, const int*, int, cudaStream_t);
 cudaError_t launch_dem_batch(const DemArgs*, const int*, int, int, cudaStream_t);
 cudaError_t launch_final_batch(const DemArgs*, int, cudaStream_t);
@@ -56,6 +58,7 @@ struct ledds_sim_s {
     bool lattice = false;
     long long N = 0;
     int ntx = 0, nty = 0, ntz = 0, ntiles = 0;
+    int tz = TILE_Z;          // tile depth (planes per tile)
     void* pop[2] = {nullptr, nullptr};
     PsmMaps maps[2];          // tensor maps of pop[0], pop[1] (staged PSM route)
     bool staged = false;      // the PSM kernel takes the staged route
@@ -182,6 +185,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
     int ntx = (d->nx + TILE_X - 1) / TILE_X, nty = (d->ny + TILE_Y - 1) / TILE_Y,
         ntz = (d->nz + TILE_Z - 1) / TILE_Z;
     int ntiles = N > 0 ? ntx * nty * ntz : 0;
+    // tile lists are sized for the smallest tile depth (a batch may choose it)
+    int ntiles_alloc = N > 0 ? ntx * nty * ((d->nz + TILE_Z_MIN - 1) / TILE_Z_MIN) : 0;
     int tcap = d->tile_cap > 0 ? d->tile_cap : 64;
     int cap = d->max_particles > 0 ? d->max_particles : 0;
     int ccap = d->cand_cap > 0 ? d->cand_cap : 32;
@@ -193,8 +198,8 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
     void* pop0 = c.take<char>((size_t)N * 19 * sb);
     // the AA pattern steps in place: one population array
     void* pop1 = p->pattern == LEDDS_PATTERN_AA ? pop0 : c.take<char>((size_t)N * 19 * sb);
-    int* tcount = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1));
-    int* tids = c.take<int>((size_t)(ntiles > 0 ? ntiles : 1) * tcap);
+    int* tcount = c.take<int>((size_t)(ntiles_alloc > 0 ? ntiles_alloc : 1));
+    int* tids = c.take<int>((size_t)(ntiles_alloc > 0 ? ntiles_alloc : 1) * tcap);
     double* st0 = c.take<double>(18 * (size_t)capc);
     double* st1 = c.take<double>(18 * (size_t)capc);
     double* acc = c.take<double>(3 * (size_t)capc);
@@ -239,6 +244,7 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
         s->nty = nty;
         s->ntz = ntz;
         s->ntiles = ntiles;
+        s->tz = TILE_Z;
         s->tile_cap = tcap;
         s->pop[0] = pop0;
         s->pop[1] = pop1;
@@ -343,13 +349,14 @@ static LbmArgs lbm_args(const ledds_sim_s* s, int in, int out, int pst) {
         // still need a wrap only if the box is narrower than the reach of a particle
         // from a tile (both sides) plus the tile itself.
         const int n3[3] = {s->d.nx, s->d.ny, s->d.nz};
-        const int T[3] = {TILE_X, TILE_Y, TILE_Z};
+        const int T[3] = {TILE_X, TILE_Y, s->tz};
         for (int q = 0; q < 3; ++q)
             a.mi[q] = s->d.periodic[q] && (double)n3[q] < 2.0 * (s->max_bound + 2.0 + T[q]) + 2.0;
     }
     a.ntx = s->ntx;
     a.nty = s->nty;
     a.ntz = s->ntz;
+    a.tz = s->tz;
     // fewer tiles than two waves of CTAs: split each tile's planes over four CTAs
     a.zsplit = s->ntiles < 2 * s->sms ? 4 : 1;
     a.tile_cap = s->tile_cap;
@@ -470,13 +477,9 @@ static cudaError_t enqueue_step(ledds_sim_s* s, int p, cudaStream_t st, int* lau
     if (n > 0) {
         CK(launch_predict_first(A, st));
         *launches += 1;
-        const int contact_launches = A.pair_once ? 2 : 1;  // pair forces + gather, or one kernel
-        for (int sub = 1; sub < nsub; ++sub) {
-            CK(launch_substep(A, (sub - 1) & 1, sub & 1, p ^ 1, 1, 1, st));
-            *launches += contact_launches + 1;
-        }
-        CK(launch_substep(A, last, last, p ^ 1, 0, 0, st));
-        *launches += contact_launches;
+        for (int sub = 1; sub < nsub; ++sub)
+            CK(launch_substep(A, (sub - 1) & 1, sub & 1, p ^ 1, 1, launches, st));
+        CK(launch_substep(A, last, last, p ^ 1, 0, launches, st));
     }
     if (ev) CK(cudaEventRecord(ev[2], st));
     if (overlap) {
@@ -1162,6 +1165,8 @@ struct ledds_batch_s {
     std::vector<BatchChunk> chunks[2];  // PSM launch arguments per batch parity
     int ctas_per_sm = 0, sms = 1;        // persistent PSM grid = ctas_per_sm x SMs
     int order = 0;                       // PSM work order: 0 member order, 1 largest first
+    int tz = TILE_Z;                     // tile depth of every member
+    bool sphd = false;                   // every member: distance-fraction spheres, no wrap
     cudaGraphExec_t g1[2] = {nullptr, nullptr}, g2[2] = {nullptr, nullptr};
     std::vector<long long> versions;
 };
@@ -1281,6 +1286,7 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
     std::vector<LbmArgs> la(2 * n);
     std::vector<DemArgs> da(n);
     std::vector<int> ts(3 * n + 2, 0);
+    bool sphd_all = true;
     for (int i = 0; i < n; ++i) {
         ledds_sim_s* s = b->sims[i];
         const int last = (s->p.n_sub - 1) & 1;
@@ -1289,6 +1295,7 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
         la[n + i] = lbm_args(s, off ^ 1, off, last);
         da[i] = dem_args(s);
         ts[i + 1] = ts[i] + s->ntiles;
+        sphd_all = sphd_all && !la[i].subdiv_any && !la[i].mi[0] && !la[i].mi[1] && !la[i].mi[2];
         ts[n + 1 + i] = s->P.n;
         ts[2 * n + 1 + i] = off;
     }
@@ -1315,6 +1322,7 @@ static cudaError_t batch_upload(ledds_batch_s* b) {
     CK(cudaMemcpyAsync(b->d_dargs, da.data(), sizeof(DemArgs) * n, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->d_tile_start, ts.data(), sizeof(int) * (3 * n + 1), cudaMemcpyHostToDevice, b->stream));
     CK(cudaStreamSynchronize(b->stream));
+    b->sphd = sphd_all;
     b->versions.assign(n, 0);
     for (int i = 0; i < n; ++i) b->versions[i] = b->sims[i]->version;
     return cudaSuccess;
@@ -1325,7 +1333,7 @@ static cudaError_t batch_enqueue(ledds_batch_s* b, int p, cudaStream_t st) {
     CK(launch_dem_batch(b->d_dargs, b->d_poff, b->nsim, p, st));
     CK(launch_bin_batch(b->d_largs[p], b->d_np, b->nsim, st));
     for (int c = 0; c < b->nchunks; ++c)
-        CK(launch_psm_batch(b->chunks[p][c], b->d_counter + c, b->storage, b->nblocks, st));
+        CK(launch_psm_batch(b->chunks[p][c], b->d_counter + c, b->storage, b->nblocks, b->sphd, st));
     CK(launch_final_batch(b->d_dargs, b->nsim, st));
     return cudaSuccess;
 }
@@ -1375,41 +1383,115 @@ int ledds_batch_step(ledds_batch_t b, int n_steps) {
 // Try every (resident PSM CTAs per SM, work order) and keep the fastest, timed with
 // events over steps_per_trial steps after two warm-up steps per candidate (these steps
 // advance the members like ledds_batch_step; every candidate computes the same step).
+// Tile depth of every member: its tile counts follow (the tile lists are sized for the
+// smallest depth); the uploaded arguments and the graphs are rebuilt on the next step.
+static void batch_set_depth(ledds_batch_s* b, int tz) {
+    b->tz = tz;
+    for (auto* s : b->sims) {
+        s->tz = tz;
+        s->ntz = (s->d.nz + tz - 1) / tz;
+        s->ntiles = s->ntx * s->nty * s->ntz;
+    }
+    b->versions.clear();
+}
+
+static const int kBatchDepths[3] = {8, 16, 32};
+
+int ledds_batch_configure(ledds_batch_t b, int tile_depth, int ctas_per_sm, int order) {
+    if (!b) return LEDDS_ERR_INVALID_ARG;
+    if (tile_depth != 8 && tile_depth != 16 && tile_depth != 32) return LEDDS_ERR_INVALID_ARG;
+    if (ctas_per_sm < 1 || ctas_per_sm > psm_batch_ctas_per_sm() || order < 0 || order > 1)
+        return LEDDS_ERR_INVALID_ARG;
+    batch_set_depth(b, tile_depth);
+    b->ctas_per_sm = ctas_per_sm;
+    b->nblocks = ctas_per_sm * b->sms;
+    b->order = order;
+    return LEDDS_OK;
+}
+
+int ledds_batch_get_config(ledds_batch_t b, int* tile_depth, int* ctas_per_sm, int* order) {
+    if (!b || !tile_depth || !ctas_per_sm || !order) return LEDDS_ERR_INVALID_ARG;
+    *tile_depth = b->tz;
+    *ctas_per_sm = b->ctas_per_sm;
+    *order = b->order;
+    return LEDDS_OK;
+}
+
+// Choices of earlier autotuner runs, by the shape of the batch (members' dimensions and
+// particle counts, storage, collision): a batch of the same shape takes the cached
+// choice without trials.
+static std::mutex g_tune_mu;
+static std::map<unsigned long long, int> g_tune_cache;
+
+static unsigned long long batch_shape_key(const ledds_batch_s* b) {
+    unsigned long long h = 1469598103934665603ull;
+    auto mix = [&](long long v) {
+        for (int q = 0; q < 8; ++q) {
+            h ^= (unsigned long long)((v >> (8 * q)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix(b->nsim);
+    mix(b->storage);
+    mix(b->sms);
+    for (const auto* s : b->sims) {
+        mix(s->d.nx);
+        mix(s->d.ny);
+        mix(s->d.nz);
+        mix(s->P.n);
+        mix(s->p.collision);
+    }
+    return h;
+}
+
+static void batch_apply_choice(ledds_batch_s* b, int id, int max_cps) {
+    const int order = id & 1, cps = (id >> 1) % max_cps + 1, d = (id >> 1) / max_cps;
+    ledds_batch_configure(b, kBatchDepths[d], cps, order);
+}
+
 int ledds_batch_autotune(ledds_batch_t b, int steps_per_trial, int* choice) {
     if (!b || steps_per_trial < 1) return LEDDS_ERR_INVALID_ARG;
     const int max_cps = psm_batch_ctas_per_sm();
+    const unsigned long long key = batch_shape_key(b);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            batch_apply_choice(b, it->second, max_cps);
+            if (choice) *choice = it->second;
+            return LEDDS_OK;
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LEDDS_ERR_CUDA;
     float best = 0.0f;
-    int best_cps = max_cps, best_order = 0, best_id = -1, rc = LEDDS_OK;
-    for (int cps = 1; cps <= max_cps && rc == LEDDS_OK; ++cps)
-        for (int order = 0; order < 2 && rc == LEDDS_OK; ++order) {
-            b->ctas_per_sm = cps;
-            b->nblocks = cps * b->sms;
-            b->order = order;
-            b->versions.clear();  // forces re-upload and fresh graphs
-            if ((rc = ledds_batch_step(b, 2)) != LEDDS_OK) break;
-            float ms = 0.0f;
-            if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = LEDDS_ERR_CUDA; break; }
-            if ((rc = ledds_batch_step(b, steps_per_trial)) != LEDDS_OK) break;
-            if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-                rc = LEDDS_ERR_CUDA;
-                break;
-            }
-            if (best_id < 0 || ms < best) {
-                best = ms;
-                best_cps = cps;
-                best_order = order;
-                best_id = (cps - 1) * 2 + order;
-            }
+    int best_id = -1, rc = LEDDS_OK;
+    const int ncand = 3 * max_cps * 2;
+    for (int id = 0; id < ncand && rc == LEDDS_OK; ++id) {
+        batch_apply_choice(b, id, max_cps);
+        if ((rc = ledds_batch_step(b, 2)) != LEDDS_OK) break;
+        float ms = 0.0f;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) { rc = LEDDS_ERR_CUDA; break; }
+        if ((rc = ledds_batch_step(b, steps_per_trial)) != LEDDS_OK) break;
+        if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = LEDDS_ERR_CUDA;
+            break;
         }
+        if (best_id < 0 || ms < best) {
+            best = ms;
+            best_id = id;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->ctas_per_sm = best_cps;
-    b->nblocks = best_cps * b->sms;
-    b->order = best_order;
-    b->versions.clear();
+    if (best_id >= 0) {
+        batch_apply_choice(b, best_id, max_cps);
+        if (rc == LEDDS_OK) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            g_tune_cache[key] = best_id;
+        }
+    }
     if (choice) *choice = best_id;
     return rc;
 }

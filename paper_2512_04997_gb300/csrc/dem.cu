@@ -1474,34 +1474,6 @@ __global__ void k_predict_first(DemArgs A) {
     for (int m = 0; m < 9; ++m) A.P.st[0][(long long)(ST + m) * A.P.cap + k] = d[m];
 }
 
-// k_contacts for the common case (only spheres, FP32 contact arithmetic): the same
-// sums without the ellipsoid and FP64 branches, which keeps its registers low.
-__global__ void __launch_bounds__(128) k_contacts_spheres(DemArgs A, int in, int cb) {
-    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (k >= A.P.n) return;  // uniform across the warp
-    const int lane = threadIdx.x & 31;
-    const double* st = A.P.st[in];
-    const int nc = A.ncand[cb][k];
-    F2 f[3], m[3];
-    for (int c = 0; c < 3; ++c) f[c] = m[c] = F2{0.0f, 0.0f};
-    for (int q = lane; q < nc; q += 32) pair_contrib_f<true>(A, st, cb, k, q, f, m);
-    if (lane < 6) wall_contrib_f<true>(A, st, k, lane, f, m);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            F2 of{__shfl_xor_sync(0xffffffffu, f[c].hi, off), __shfl_xor_sync(0xffffffffu, f[c].lo, off)};
-            F2 om{__shfl_xor_sync(0xffffffffu, m[c].hi, off), __shfl_xor_sync(0xffffffffu, m[c].lo, off)};
-            f[c] = f2_add(f[c], of);
-            m[c] = f2_add(m[c], om);
-        }
-    if (lane != 0) return;
-    for (int a = 0; a < 3; ++a) {
-        A.P.Fc[(long long)a * A.P.cap + k] = (double)f[a].hi + (double)f[a].lo;
-        A.P.Mc[(long long)a * A.P.cap + k] = (double)m[a].hi + (double)m[a].lo;
-    }
-}
-
 // End of a substep for one particle (thread per particle): the corrector with the held
 // hydrodynamic force, then the predictor of the next substep, from buffer `in` to `out`.
 __global__ void k_integrate(DemArgs A, int in, int out) {
@@ -1518,6 +1490,67 @@ __global__ void k_integrate(DemArgs A, int in, int out) {
     for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + k];
     predict(A, k, r, v, acc, w, d);
     store_state(A, A.P.st[out], k, r, v, w, d);
+}
+
+// One DEM substep of a sphere-only simulation with FP32 contact arithmetic in a single
+// launch: the contact force and torque of 32 particles (a warp each, lane per candidate,
+// compensated FP32 sums reduced by a butterfly and rounded to FP64 once; the sphere-only
+// form of k_contacts, without the ellipsoid and FP64 branches, which keeps its registers
+// low), then, after a CTA barrier, the corrector of this substep and
+// the predictor of the next for the same 32 particles (a lane each, as k_integrate).
+// The contacts read only buffer `in` and the integration writes buffer `out`, so the
+// CTAs need no ordering among themselves; the launch boundary orders the substeps.
+// do_step = 0 (the last substep) computes the contact sums only.
+constexpr int SUB_WARPS = 32;
+static_assert(SUB_WARPS <= 32, "the integration phase gives each particle one lane of warp 0");
+__global__ void __launch_bounds__(32 * SUB_WARPS, 1) k_substep_spheres(DemArgs A, int in, int out, int cb,
+                                                                      int do_step) {
+    __shared__ double sF[SUB_WARPS][3], sM[SUB_WARPS][3];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = blockIdx.x * SUB_WARPS;
+    const int k = base + w;
+    const double* st = A.P.st[in];
+    if (k < A.P.n) {  // uniform across the warp
+        const int nc = A.ncand[cb][k];
+        F2 f[3], m[3];
+        for (int c = 0; c < 3; ++c) f[c] = m[c] = F2{0.0f, 0.0f};
+        for (int q = lane; q < nc; q += 32) pair_contrib_f<true>(A, st, cb, k, q, f, m);
+        if (lane < 6) wall_contrib_f<true>(A, st, k, lane, f, m);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                F2 of{__shfl_xor_sync(0xffffffffu, f[c].hi, off), __shfl_xor_sync(0xffffffffu, f[c].lo, off)};
+                F2 om{__shfl_xor_sync(0xffffffffu, m[c].hi, off), __shfl_xor_sync(0xffffffffu, m[c].lo, off)};
+                f[c] = f2_add(f[c], of);
+                m[c] = f2_add(m[c], om);
+            }
+        if (lane == 0) {
+            for (int a = 0; a < 3; ++a) {
+                const double fa = (double)f[a].hi + (double)f[a].lo;
+                const double ma = (double)m[a].hi + (double)m[a].lo;
+                A.P.Fc[(long long)a * A.P.cap + k] = fa;
+                A.P.Mc[(long long)a * A.P.cap + k] = ma;
+                sF[w][a] = fa;
+                sM[w][a] = ma;
+            }
+        }
+    }
+    if (!do_step) return;  // uniform across the CTA
+    __syncthreads();
+    const int kk = base + lane;
+    if (w != 0 || lane >= SUB_WARPS || kk >= A.P.n) return;
+    double r[3], v[3], wv[3], d[9], Ft[3], Mt[3], acc[3];
+    load_state(A, st, kk, r, v, wv, d);
+    for (int a = 0; a < 3; ++a) {
+        const long long o = (long long)a * A.P.cap + kk;
+        Ft[a] = sF[lane][a] + A.P.Fhp[o];
+        Mt[a] = sM[lane][a] + A.P.Mhp[o];
+    }
+    correct(A, kk, Ft, Mt, d, v, wv);
+    for (int a = 0; a < 3; ++a) acc[a] = A.P.acc[(long long)a * A.P.cap + kk];
+    predict(A, kk, r, v, acc, wv, d);
+    store_state(A, A.P.st[out], kk, r, v, wv, d);
 }
 
 // Velocity update of the last substep (flowchart: after the fluid forces are reduced):
@@ -1772,15 +1805,19 @@ cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
 
 // do_step = 1: contact forces then corrector + next predictor (in -> out);
 // do_step = 0: contact forces only.
-cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int, cudaStream_t s) {
+cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int* launches, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
+    if (!A.pair_once && A.force_f32) {  // spheres only, FP32 contacts: one launch per substep
+        k_substep_spheres<<<nblk(A.P.n, SUB_WARPS), 32 * SUB_WARPS, 0, s>>>(A, in, out, cb, do_step);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    *launches += (A.pair_once ? 2 : 1) + (do_step ? 1 : 0);
     if (A.pair_once) {
         const long long maxp = (long long)A.P.n * A.ccap;  // every slot may hold an owned pair
         k_pair_forces<<<(unsigned)((maxp + 127) / 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_list, A.cp_res,
                                                                      A.cp_stride);
         k_contacts_gather<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb, A.cp_off, A.cp_res, A.cp_stride);
-    } else if (A.force_f32) {  // no ellipsoid in the simulation (pair_once is off)
-        k_contacts_spheres<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
     } else {
         k_contacts<<<nblk(A.P.n * 32, 128), 128, 0, s>>>(A, in, cb);
     }

@@ -54,6 +54,12 @@ struct Store<LEDDS_STORE_F32> {
     static __device__ __forceinline__ float raw(T v) { return v; }
     static __device__ __forceinline__ float ldg_raw(const T* p) { return __ldg(p); }
     static __device__ __forceinline__ void store_raw(T* p, float v) { __stcs(p, v); }
+    // streaming store under a predicate (no branch around it)
+    static __device__ __forceinline__ void store_if(T* p, float v, bool pred) {
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cs.f32 [%0], %1;\n\t}" ::"l"(p),
+                     "f"(v), "r"((unsigned)pred)
+                     : "memory");
+    }
     static __device__ __forceinline__ float up(float v, float) { return v; }
     static __device__ __forceinline__ float from_bits(unsigned short, float) { return 0.f; }
     static __device__ __forceinline__ void store(T* p, float v, float) { __stcs(p, v); }
@@ -70,6 +76,12 @@ struct Store<LEDDS_STORE_F16> {
     }
     static __device__ __forceinline__ void store_raw(T* p, float v) {
         __stcs(reinterpret_cast<unsigned short*>(p), __half_as_ushort(__float2half_rn(v)));
+    }
+    static __device__ __forceinline__ void store_if(T* p, float v, bool pred) {
+        const unsigned short h = __half_as_ushort(__float2half_rn(v));
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cs.b16 [%0], %1;\n\t}" ::"l"(p),
+                     "h"(h), "r"((unsigned)pred)
+                     : "memory");
     }
     static __device__ __forceinline__ float up(float v, float scale) { return v * scale; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
@@ -93,6 +105,12 @@ struct Store<LEDDS_STORE_BF16> {
     static __device__ __forceinline__ void store_raw(T* p, float v) {
         __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
     }
+    static __device__ __forceinline__ void store_if(T* p, float v, bool pred) {
+        const unsigned short h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.cs.b16 [%0], %1;\n\t}" ::"l"(p),
+                     "h"(h), "r"((unsigned)pred)
+                     : "memory");
+    }
     static __device__ __forceinline__ float up(float v, float scale) { return v * scale; }
     static __device__ __forceinline__ float from_bits(unsigned short h, float inv) {
         return __bfloat162float(__ushort_as_bfloat16(h)) * inv;
@@ -110,7 +128,8 @@ __host__ __device__ constexpr int storage_bytes_c(int store) { return store == L
 // per x-row), TILE_Z planes.
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 8;
-constexpr int TILE_Z = 16;
+constexpr int TILE_Z = 16;       // tile depth of a simulation (a batch may choose another)
+constexpr int TILE_Z_MIN = 8;    // smallest tile depth; tile lists are sized for it
 constexpr int MAX_TILE_CAP = 64;
 constexpr int MAX_CAND_CAP = 64;
 
@@ -170,8 +189,9 @@ struct LbmArgs {
     unsigned off_odd;             // bit i: off[i] is odd (16-bit word selection)
     int nx_even;                  // nx even: a pulled index has the parity of x - c_x
     int mi[3];                    // per axis: node-particle offsets may need a periodic wrap
-    // tile lists
+    // tile lists (tiles of TILE_X x TILE_Y x tz nodes)
     int ntx, nty, ntz, tile_cap;
+    int tz;
     int zsplit;                   // CTAs per tile of the PSM kernel (1, or more for small lattices)
     const int* tile_count;
     const int* tile_ids;

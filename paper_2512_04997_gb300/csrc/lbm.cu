@@ -340,7 +340,7 @@ __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
     int tl[3][16], tc[3];
     tc[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
     tc[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
-    tc[2] = axis_tiles(r[2], reach, a.nz, a.per[2], TILE_Z, tl[2]);
+    tc[2] = axis_tiles(r[2], reach, a.nz, a.per[2], a.tz, tl[2]);
     for (int c = 0; c < tc[2]; ++c)
         for (int b = 0; b < tc[1]; ++b)
             for (int q = 0; q < tc[0]; ++q) {
@@ -357,10 +357,13 @@ __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
 // arguments travel in the launch's parameter block (read-only for the whole launch, like
 // the single-simulation kernel's argument), up to BATCH_CHUNK members per launch.
 // The batched kernel indexes its members' arguments at run time and runs best with the
-// larger register budget (2 resident CTAs per SM) for every storage format.
+// larger register budget (2 resident CTAs per SM) for every storage format. Tiles are
+// TILE_X x TILE_Y x tz nodes, tz chosen per batch (ledds_batch_configure / autotune).
+// SPHD: every member's particles are spheres with distance fractions and no offset needs
+// a periodic wrap.
 constexpr int PSM_BATCH_MINB = 2;
 
-template <int STORE, bool TRT>
+template <int STORE, bool TRT, bool SPHD>
 __global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const __grid_constant__ BatchChunk P,
                                                                           int* counter) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -386,7 +389,7 @@ __global__ void __launch_bounds__(PSM_THREADS, PSM_BATCH_MINB) k_psm_batch(const
         const LbmArgs& a = P.a[sim];
         const int t = item - P.tile_start[sim];
         const int bx = t % a.ntx, by = (t / a.ntx) % a.nty, bz = t / (a.ntx * a.nty);
-        psm_tile_direct<STORE, TRT, PSM_AB, false>(a, bx, by, bz, 0, TILE_Z, smem);
+        psm_tile_direct<STORE, TRT, PSM_AB, SPHD>(a, bx, by, bz, 0, a.tz, smem);
         __syncthreads();
     }
 }
@@ -403,7 +406,7 @@ __device__ __forceinline__ void bin_particle(const LbmArgs& a, int k, int* tile_
     int tl[3][16], tcn[3];
     tcn[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
     tcn[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
-    tcn[2] = axis_tiles(r[2], reach, a.nz, a.per[2], TILE_Z, tl[2]);
+    tcn[2] = axis_tiles(r[2], reach, a.nz, a.per[2], a.tz, tl[2]);
     for (int c = 0; c < tcn[2]; ++c)
         for (int b = 0; b < tcn[1]; ++b)
             for (int q = 0; q < tcn[0]; ++q) {
@@ -476,16 +479,16 @@ bool psm_make_maps(const void* pop, int store, int nx, int ny, int nz, PsmMaps* 
 __global__ void __launch_bounds__(256) k_voxelize(const LbmArgs a, float* beta, int* ids, int* nsolid) {
     __shared__ TileCache tc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * TILE_Z;
+    const int x0 = blockIdx.x * TILE_X, y0 = blockIdx.y * TILE_Y, z0 = blockIdx.z * a.tz;
     const int tile = (blockIdx.z * a.nty + blockIdx.y) * a.ntx + blockIdx.x;
     const int cnt = min(a.tile_count[tile], a.tile_cap);
     load_tile(a, tc, tile, cnt, x0, y0, z0);
     __syncthreads();
     const int x = x0 + lane, y = y0 + warp;
-    for (int iz = 0; iz < TILE_Z; ++iz) {
+    for (int iz = 0; iz < a.tz; ++iz) {
         const int z = z0 + iz;
         if (y >= a.ny || z >= a.nz) break;
-        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
+        const unsigned long long mask = cnt ? row_mask<true>(a, tc, cnt, warp, iz) : 0ull;
         const bool valid = x < a.nx;
         Two t;
         t.ns = 0;
@@ -548,30 +551,37 @@ cudaError_t launch_psm(const LbmArgs& a, const PsmMaps* m, int store, cudaStream
     return launch_psm_mode<PSM_AB>(a, m, store, s);
 }
 
-template <int STORE, bool TRT>
+template <int STORE, bool TRT, bool SPHD>
 static cudaError_t launch_psm_batch_t(const BatchChunk& P, int* counter, int nblocks, cudaStream_t s) {
     static bool configured = false;
     const size_t smem = PsmSmem<STORE, false, true>::bytes;
     if (!configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_psm_batch<STORE, TRT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_psm_batch<STORE, TRT, SPHD>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_psm_batch<STORE, TRT><<<nblocks, PSM_THREADS, smem, s>>>(P, counter);
+    k_psm_batch<STORE, TRT, SPHD><<<nblocks, PSM_THREADS, smem, s>>>(P, counter);
     return cudaGetLastError();
 }
 
-// All members of a batch share the storage format and the collision operator.
-cudaError_t launch_psm_batch(const BatchChunk& P, int* counter, int store, int nblocks, cudaStream_t s) {
+template <bool SPHD>
+static cudaError_t launch_psm_batch_g(const BatchChunk& P, int* counter, int store, int nblocks, cudaStream_t s) {
     if (P.a[0].trt) {
-        if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, true>(P, counter, nblocks, s);
-        if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, true>(P, counter, nblocks, s);
-        return launch_psm_batch_t<LEDDS_STORE_BF16, true>(P, counter, nblocks, s);
+        if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, true, SPHD>(P, counter, nblocks, s);
+        if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, true, SPHD>(P, counter, nblocks, s);
+        return launch_psm_batch_t<LEDDS_STORE_BF16, true, SPHD>(P, counter, nblocks, s);
     }
-    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, false>(P, counter, nblocks, s);
-    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, false>(P, counter, nblocks, s);
-    return launch_psm_batch_t<LEDDS_STORE_BF16, false>(P, counter, nblocks, s);
+    if (store == LEDDS_STORE_F32) return launch_psm_batch_t<LEDDS_STORE_F32, false, SPHD>(P, counter, nblocks, s);
+    if (store == LEDDS_STORE_F16) return launch_psm_batch_t<LEDDS_STORE_F16, false, SPHD>(P, counter, nblocks, s);
+    return launch_psm_batch_t<LEDDS_STORE_BF16, false, SPHD>(P, counter, nblocks, s);
+}
+
+// All members of a batch share the storage format and the collision operator; sphd when
+// every member qualifies for the sphere-distance form.
+cudaError_t launch_psm_batch(const BatchChunk& P, int* counter, int store, int nblocks, bool sphd, cudaStream_t s) {
+    if (sphd) return launch_psm_batch_g<true>(P, counter, store, nblocks, s);
+    return launch_psm_batch_g<false>(P, counter, store, nblocks, s);
 }
 
 cudaError_t launch_bin_batch(const LbmArgs* args, const int* np, int nsim, cudaStream_t s) {

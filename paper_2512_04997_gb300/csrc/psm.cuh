@@ -228,6 +228,15 @@ __device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& t
 }
 
 // Row prefilter: which cached particles can touch the x-row (ly, lz) of this tile.
+// MI: a node-particle offset may need a periodic wrap (a.mi); false when no axis does
+// (known at compile time).
+template <bool MI>
+__device__ __forceinline__ float mimg(float d, int per, float L) {
+    if constexpr (MI) return min_image_f(d, per, L);
+    else return d;
+}
+
+template <bool MI>
 __device__ __forceinline__ unsigned long long row_mask(const LbmArgs& a, const TileCache& tc,
                                                        int cnt, int ly, int lz) {
     const int lane = threadIdx.x & 31;
@@ -237,8 +246,8 @@ __device__ __forceinline__ unsigned long long row_mask(const LbmArgs& a, const T
         bool hit = false;
         if (e < cnt) {
             const float4 ps = tc.pos[e];
-            float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
-            float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+            float dy = mimg<MI>((float)ly - ps.y, a.mi[1], (float)a.ny);
+            float dz = mimg<MI>((float)lz - ps.z, a.mi[2], (float)a.nz);
             hit = dy * dy + dz * dz < tc.vel[e].w;
         }
         unsigned b = __ballot_sync(FULL, hit);
@@ -256,7 +265,8 @@ struct Two {
 };
 
 __device__ __forceinline__ bool ranks_before(const TileCache& tc, float b, int e, float bw, int ew) {
-    return b > bw || (b == bw && tc_pid(tc, e) < tc_pid(tc, ew));
+    if (b != bw) return b > bw;
+    return tc_pid(tc, e) < tc_pid(tc, ew);  // a tie: the lower particle id first
 }
 
 // Exact subdivision counts for the lanes in `need`, one node after the other, each counted
@@ -286,8 +296,9 @@ static __device__ __noinline__ float subdiv_lanes(const LbmArgs& a, const TileCa
 
 // Called by the whole warp (the row mask is uniform); lanes with valid false take no part
 // beyond the warp-wide subdivision counts.
-// SPHD: every particle is a sphere with distance-based solid fractions (known at compile
-// time: the subdivision and ellipsoid code is left out).
+// SPHD: every particle is a sphere with distance-based solid fractions and no offset
+// needs a periodic wrap (known at compile time: the subdivision, ellipsoid and wrap code
+// is left out).
 template <bool SPHD>
 __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
                                             unsigned long long mask, int lx, int ly, int lz, int x,
@@ -300,9 +311,9 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& t
         const int e = __ffsll((long long)mask) - 1;
         mask &= mask - 1;
         const float4 ps = tc.pos[e];
-        float dx = min_image_f((float)lx - ps.x, a.mi[0], (float)a.nx);
-        float dy = min_image_f((float)ly - ps.y, a.mi[1], (float)a.ny);
-        float dz = min_image_f((float)lz - ps.z, a.mi[2], (float)a.nz);
+        float dx = mimg<!SPHD>((float)lx - ps.x, a.mi[0], (float)a.nx);
+        float dy = mimg<!SPHD>((float)ly - ps.y, a.mi[1], (float)a.ny);
+        float dz = mimg<!SPHD>((float)lz - ps.z, a.mi[2], (float)a.nz);
         float b;
         if constexpr (SPHD) {
             // Eq. (naiveSolidFrac), as in beta_quick
@@ -335,12 +346,13 @@ struct SolidAt {
     float B, ux, uy, uz, ax, ay, az;
 };
 
+template <bool MI>
 __device__ __forceinline__ void solid_at(const LbmArgs& a, const TileCache& tc, int e, float b, int lx,
                                          int ly, int lz, SolidAt& q) {
     const float4 ps = tc.pos[e], vs = tc.vel[e], ws = tc.spin[e];
-    q.ax = min_image_f(sb((float)lx, ps.x), a.mi[0], (float)a.nx);
-    q.ay = min_image_f(sb((float)ly, ps.y), a.mi[1], (float)a.ny);
-    q.az = min_image_f(sb((float)lz, ps.z), a.mi[2], (float)a.nz);
+    q.ax = mimg<MI>(sb((float)lx, ps.x), a.mi[0], (float)a.nx);
+    q.ay = mimg<MI>(sb((float)ly, ps.y), a.mi[1], (float)a.ny);
+    q.az = mimg<MI>(sb((float)lz, ps.z), a.mi[2], (float)a.nz);
     const float th = sb(a.tau, 0.5f);
     q.B = __fdividef(mu(b, th), ad(sb(1.0f, b), th));
     q.ux = ad(vs.x, sb(mu(ws.y, q.az), mu(ws.z, q.ay)));
@@ -435,6 +447,13 @@ __device__ __forceinline__ void make_plan(const LbmArgs& a, int x, int y, int z,
     if (z == 0) { if (a.per[2]) p.wzm = (int)a.N; else b |= 16u; }
     if (z == a.nz - 1) { if (a.per[2]) p.wzp = -(int)a.N; else b |= 32u; }
     p.bw = b;
+}
+
+// The plan of a node known to be off every lattice face (no wrap, no wall link).
+__device__ __forceinline__ void cell_plan(const LbmArgs& a, int x, int y, int z, Plan& p) {
+    p.cell = x + a.nx * (y + a.ny * z);
+    p.bw = 0u;
+    p.wxm = p.wxp = p.wym = p.wyp = p.wzm = p.wzp = 0;
 }
 
 // Walls crossed by the link of direction I (the axis flags of wall_term).
@@ -654,12 +673,13 @@ __device__ __forceinline__ float cdot(float x, float y, float z) {
 //                the moving-wall term of that direction (halfway bounce-back).
 // `node` points at the node's element of plane 0.
 template <class SS, int I, int MODE, bool WALLS>
-__device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS::T* node, float v) {
+__device__ __forceinline__ void put(const LbmArgs& a, const Plan& p, typename SS::T* node, float v, bool valid) {
     if constexpr (psm_form(MODE) == PSM_AB) {
-        SS::store_raw(node + plane_at<MODE>(a, I), v);
+        SS::store_if(node + plane_at<MODE>(a, I), v, valid);
     } else if constexpr (psm_form(MODE) == PSM_AA_EVEN) {
-        SS::store_raw(node + plane_at<MODE>(a, OPP(I)), v);
+        SS::store_if(node + plane_at<MODE>(a, OPP(I)), v, valid);
     } else {
+        if (!valid) return;
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         if constexpr (WALLS) {
             bool wx, wy, wz;
@@ -799,20 +819,15 @@ __device__ __forceinline__ float cqqc(const Coef& k) {
 template <class SS, int MODE, bool WALLS>
 __device__ __forceinline__ void collide_store(const LbmArgs& a, const float (&G)[19], const Coef& k,
                                               const Plan& p, typename SS::T* node, bool valid) {
-    const float o0 = fm(ad(k.al, k.ga), G[0], mu(TW(0), k.q0));  // al + ga = 1 - We
-    if (valid) put<SS, 0, MODE, WALLS>(a, p, node, o0);
+    put<SS, 0, MODE, WALLS>(a, p, node, fm(ad(k.al, k.ga), G[0], mu(TW(0), k.q0)), valid);  // al + ga = 1 - We
     static_for<9>([&](auto ic) {
         constexpr int I = 1 + 2 * decltype(ic)::value;
         constexpr int cx = CX(I), cy = CY(I), cz = CZ(I);
         constexpr float t = TW(I);
         const float P = mu(t, cqqc<cx, cy, cz>(k));
         const float A = mu(t, cq<cx, cy, cz>(k));
-        const float oi = fm(k.al, G[I], fm(k.ga, G[I + 1], ad(P, A)));
-        const float oj = fm(k.al, G[I + 1], fm(k.ga, G[I], sb(P, A)));
-        if (valid) {
-            put<SS, I, MODE, WALLS>(a, p, node, oi);
-            put<SS, I + 1, MODE, WALLS>(a, p, node, oj);
-        }
+        put<SS, I, MODE, WALLS>(a, p, node, fm(k.al, G[I], fm(k.ga, G[I + 1], ad(P, A))), valid);
+        put<SS, I + 1, MODE, WALLS>(a, p, node, fm(k.al, G[I + 1], fm(k.ga, G[I], sb(P, A))), valid);
     });
 }
 
@@ -826,16 +841,14 @@ __device__ __forceinline__ void collide_store(const LbmArgs& a, const float (&G)
 // the warp together (the force sums are warp-cooperative); `valid` is false for lanes
 // beyond the lattice, wwarp true when some lane of the warp has a wall link. hkey/hacc:
 // the running force sum of the solid this lane last met down its column.
-template <class SS, bool TRT, int MODE>
+template <class SS, bool TRT, int MODE, bool MI>
 __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float (&G)[19], const Plan& pl,
                                          bool valid, bool wwarp, const Two& t, int lane, int warp, int iz,
                                          typename SS::T* pout, int& hkey, float (&hacc)[6]) {
     constexpr bool SCALED = sizeof(typename SS::T) == 2;
     const float sc = SCALED ? a.scale : 1.0f;
-    if (!valid) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) G[i] = 0.f;
-    }
+    // (a lane beyond the lattice computes with the values it read at a clamped position or
+    // from zero-filled boxes; its results are not stored and it takes no part in any sum)
     // moments, Eqs. (rho), (momentum); rho = 1 + sum g (pairwise sums for ILP)
     float drho = ad(ad(ad(G[0], ad(G[1], G[2])), ad(ad(G[3], G[4]), ad(G[5], G[6]))),
                     ad(ad(ad(ad(G[7], G[8]), ad(G[9], G[10])), ad(ad(G[11], G[12]), ad(G[13], G[14]))),
@@ -867,73 +880,74 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
         SolidTerms m;
         node_coef<TRT, false>(a, sc, drho, rho, ux, uy, uz, usq, m, k);
     } else {
-        // B_k (Eq. bk), surface velocities u_k = v_k + w_k x (x - r_k), sums over the solids
+        // Per solid, one after the other (so that one solid's data is live at a time):
+        // B_k (Eq. bk) and the surface velocity u_k = v_k + w_k x (x - r_k), its terms in
+        // the sums V, Y, Z, and its hydrodynamic force and torque (Eqs. forceSF, torqueSF,
+        // which need only rho, u and the solid). Down a column a thread rarely meets a
+        // second particle within one tile, so it keeps a running FP32 sum for the first
+        // solid and the warp flushes to the tile's FP32 sums (native shared atomics) only
+        // when some lane meets a different particle (and at the end of the tile); a second
+        // solid in a node (rare) is flushed at once. Tiles add to FP64 totals.
         const bool two = __any_sync(FULL, t.ns > 1);  // uniform
-        SolidAt s0, s1;
-        s0.B = s1.B = 0.f;
-        s0.ux = s0.uy = s0.uz = s0.ax = s0.ay = s0.az = 0.f;
-        s1.ux = s1.uy = s1.uz = s1.ax = s1.ay = s1.az = 0.f;
-        if (t.ns > 0) solid_at(a, tc, t.e0, t.b0, lane, warp, iz, s0);
-        if (two && t.ns > 1) solid_at(a, tc, t.e1, t.b1, lane, warp, iz, s1);
         SolidTerms m;
-        const float v0x = mu(s0.B, s0.ux), v0y = mu(s0.B, s0.uy), v0z = mu(s0.B, s0.uz);
-        m.Bs = s0.B;
-        m.Vx = v0x;
-        m.Vy = v0y;
-        m.Vz = v0z;
-        m.Yxx = mu(v0x, s0.ux);
-        m.Yyy = mu(v0y, s0.uy);
-        m.Yzz = mu(v0z, s0.uz);
-        m.Yxy = mu(v0x, s0.uy);
-        m.Yxz = mu(v0x, s0.uz);
-        m.Yyz = mu(v0y, s0.uz);
-        m.Z = fm(v0z, s0.uz, fm(v0y, s0.uy, mu(v0x, s0.ux)));
+        {
+            SolidAt q;
+            q.B = 0.f;
+            q.ux = q.uy = q.uz = q.ax = q.ay = q.az = 0.f;
+            if (t.ns > 0) solid_at<MI>(a, tc, t.e0, t.b0, lane, warp, iz, q);
+            const float vx = mu(q.B, q.ux), vy = mu(q.B, q.uy), vz = mu(q.B, q.uz);
+            m.Bs = q.B;
+            m.Vx = vx;
+            m.Vy = vy;
+            m.Vz = vz;
+            m.Yxx = mu(vx, q.ux);
+            m.Yyy = mu(vy, q.uy);
+            m.Yzz = mu(vz, q.uz);
+            m.Yxy = mu(vx, q.uy);
+            m.Yxz = mu(vx, q.uz);
+            m.Yyz = mu(vy, q.uz);
+            m.Z = fm(vz, q.uz, fm(vy, q.uy, mu(vx, q.ux)));
+            const int key0 = t.ns > 0 ? t.e0 : -1;
+            float v0[6];
+            solid_force(q, rho, sb(ux, q.ux), sb(uy, q.uy), sb(uz, q.uz), a, v0);
+            // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
+            // held sum (the lane may meet the same particle again further down)
+            const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
+            if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
+            if (change) {
+                hkey = -1;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
+            }
+            if (key0 >= 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) hacc[c] = ad(hacc[c], v0[c]);
+                hkey = key0;
+            }
+        }
         if (two) {
-            const float v1x = mu(s1.B, s1.ux), v1y = mu(s1.B, s1.uy), v1z = mu(s1.B, s1.uz);
-            m.Bs = ad(m.Bs, s1.B);
-            m.Vx = ad(m.Vx, v1x);
-            m.Vy = ad(m.Vy, v1y);
-            m.Vz = ad(m.Vz, v1z);
-            m.Yxx = fm(v1x, s1.ux, m.Yxx);
-            m.Yyy = fm(v1y, s1.uy, m.Yyy);
-            m.Yzz = fm(v1z, s1.uz, m.Yzz);
-            m.Yxy = fm(v1x, s1.uy, m.Yxy);
-            m.Yxz = fm(v1x, s1.uz, m.Yxz);
-            m.Yyz = fm(v1y, s1.uz, m.Yyz);
-            m.Z = fm(v1z, s1.uz, fm(v1y, s1.uy, fm(v1x, s1.ux, m.Z)));
+            SolidAt q;
+            q.B = 0.f;
+            q.ux = q.uy = q.uz = q.ax = q.ay = q.az = 0.f;
+            if (t.ns > 1) solid_at<MI>(a, tc, t.e1, t.b1, lane, warp, iz, q);
+            const float vx = mu(q.B, q.ux), vy = mu(q.B, q.uy), vz = mu(q.B, q.uz);
+            m.Bs = ad(m.Bs, q.B);
+            m.Vx = ad(m.Vx, vx);
+            m.Vy = ad(m.Vy, vy);
+            m.Vz = ad(m.Vz, vz);
+            m.Yxx = fm(vx, q.ux, m.Yxx);
+            m.Yyy = fm(vy, q.uy, m.Yyy);
+            m.Yzz = fm(vz, q.uz, m.Yzz);
+            m.Yxy = fm(vx, q.uy, m.Yxy);
+            m.Yxz = fm(vx, q.uz, m.Yxz);
+            m.Yyz = fm(vy, q.uz, m.Yyz);
+            m.Z = fm(vz, q.uz, fm(vy, q.uy, fm(vx, q.ux, m.Z)));
+            float v1[6];
+            solid_force(q, rho, sb(ux, q.ux), sb(uy, q.uy), sb(uz, q.uz), a, v1);
+            warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
         }
         m.Btot = fminf(m.Bs, 1.0f);
         node_coef<TRT, true>(a, sc, drho, rho, ux, uy, uz, usq, m, k);
-
-        // Hydrodynamic force and torque (Eqs. forceSF, torqueSF) of this node's solids,
-        // before the collision (they need only rho, u and the solids). Down a column a
-        // thread rarely meets a second particle within one tile, so it keeps a running
-        // FP32 sum for the first solid and the warp flushes to the tile's FP32 sums (native
-        // shared atomics) only when some lane meets a different particle (and at the end
-        // of the tile); a second solid in a node (rare) is flushed at once. Tiles add to
-        // FP64 totals.
-        const int key0 = t.ns > 0 ? t.e0 : -1;
-        float v0[6];
-        solid_force(s0, rho, sb(ux, s0.ux), sb(uy, s0.uy), sb(uz, s0.uz), a, v0);
-        // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the held
-        // sum (the lane may meet the same particle again further down)
-        const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
-        if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
-        if (change) {
-            hkey = -1;
-#pragma unroll
-            for (int c = 0; c < 6; ++c) hacc[c] = 0.f;
-        }
-        if (key0 >= 0) {
-#pragma unroll
-            for (int c = 0; c < 6; ++c) hacc[c] = ad(hacc[c], v0[c]);
-            hkey = key0;
-        }
-        if (two) {
-            float v1[6];
-            solid_force(s1, rho, sb(ux, s1.ux), sb(uy, s1.uy), sb(uz, s1.uz), a, v1);
-            warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
-        }
     }
     if (psm_form(MODE) == PSM_AA_ODD && wwarp) collide_store<SS, MODE, true>(a, G, k, pl, node, valid);
     else collide_store<SS, MODE, false>(a, G, k, pl, node, valid);
@@ -945,8 +959,8 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
 template <int STORE, bool STAGED>
 struct PsmCfg {
     static constexpr bool F32 = STORE == LEDDS_STORE_F32;
-    static constexpr int minb = STAGED ? (F32 ? 2 : 3) : 3;
-    static constexpr int stages = F32 ? 4 : 4;
+    static constexpr int minb = STAGED ? (F32 ? 3 : 3) : 4;
+    static constexpr int stages = F32 ? 2 : 3;
 };
 
 // Shared memory of the PSM kernel: the tile cache, then (staged route) the full and
@@ -990,7 +1004,7 @@ __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by
     TileCache& tc = *reinterpret_cast<TileCache*>(psm_smem);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * a.tz;
     const int tile = (bz * a.nty + by) * a.ntx + bx;
     const int x = x0 + lane, y = y0 + warp;
     const int cnt = min(a.tile_count[tile], a.tile_cap);
@@ -1003,23 +1017,25 @@ __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by
         const int z = z0 + iz;
         if (y >= a.ny || z >= a.nz) continue;  // uniform across the warp
         const bool valid = x < a.nx;
-        const unsigned long long mask = cnt ? row_mask(a, tc, cnt, warp, iz) : 0ull;
+        const unsigned long long mask = cnt ? row_mask<!SPHD>(a, tc, cnt, warp, iz) : 0ull;
+        // lanes beyond the lattice read at x = nx - 1 (results discarded)
+        const int xr = valid ? x : a.nx - 1;
+        const bool gen = psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, !off_faces(a, xr, y, z));
         Plan pl;
-        make_plan(a, valid ? x : 0, y, z, pl);
-        const bool gen = __any_sync(FULL, valid && !off_faces(a, x, y, z));
-        const bool wwarp = psm_form(MODE) != PSM_AA_EVEN && __any_sync(FULL, valid && pl.bw != 0u);
-        float g[19];
-        if (valid) {
-            if (gen && psm_form(MODE) != PSM_AA_EVEN) pull_all<SS, true, MODE>(a, pin, pl, g);
-            else pull_all<SS, false, MODE>(a, pin, pl, g);
-        }
-        // the node's solids while its loads are in flight
+        if (gen || psm_form(MODE) == PSM_AA_ODD) make_plan(a, xr, y, z, pl);
+        else cell_plan(a, xr, y, z, pl);
+        const bool wwarp = gen && __any_sync(FULL, valid && pl.bw != 0u);
+        // the node's solids (before the loads, so that the search's registers and the
+        // pulled values are not live together)
         Two t;
         t.ns = 0;
         t.total = 0;
         if (mask) node_solids<SPHD>(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
         if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
-        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
+        float g[19];
+        if (gen) pull_all<SS, true, MODE>(a, pin, pl, g);
+        else pull_all<SS, false, MODE>(a, pin, pl, g);
+        psm_node<SS, TRT, MODE, !SPHD>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
     warp_flush(tc, hkey, hacc);
     __syncthreads();
@@ -1052,7 +1068,7 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
     const unsigned char* stg = psm_smem + SM::stages + pad;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * TILE_Z;
+    const int x0 = bx * TILE_X, y0 = by * TILE_Y, z0 = bz * a.tz;
     const int tile = (bz * a.nty + by) * a.ntx + bx;
     const int x = x0 + lane, y = y0 + warp;
     const int nplanes = min(zhi, a.nz - z0) - zlo;  // CTA-uniform
@@ -1099,7 +1115,7 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
         t.ns = 0;
         t.total = 0;
         if (row && cnt) {
-            const unsigned long long mask = row_mask(a, tc, cnt, warp, iz);
+            const unsigned long long mask = row_mask<!SPHD>(a, tc, cnt, warp, iz);
             if (mask) node_solids<SPHD>(a, tc, mask, lane, warp, iz, x, y, z, valid, t);  // uniform
             if (t.total > 2) atomicAdd(&a.status->solids_overflow, 1);
         }
@@ -1111,15 +1127,17 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
         __syncwarp();
         if (lane == 0) mbar_arrive(bar0 + 8u * (S + s));
         if (!row) continue;
+        const int xr = valid ? x : a.nx - 1;
         Plan pl;
-        make_plan(a, valid ? x : 0, y, z, pl);
+        if (face || xend || psm_form(MODE) == PSM_AA_ODD) make_plan(a, xr, y, z, pl);
+        else cell_plan(a, xr, y, z, pl);
         if (face) {
-            if (valid) pull_all<SS, true, MODE>(a, pin, pl, g);
+            pull_all<SS, true, MODE>(a, pin, pl, g);
         } else if (xend) {
             if (valid && (x == 0 || x == a.nx - 1)) fix_x_ends<SS, MODE>(a, pin, pl, g);
         }
-        const bool wwarp = SHIFT && __any_sync(FULL, valid && pl.bw != 0u);
-        psm_node<SS, TRT, MODE>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
+        const bool wwarp = (face || xend) && __any_sync(FULL, valid && pl.bw != 0u);
+        psm_node<SS, TRT, MODE, !SPHD>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
     warp_flush(tc, hkey, hacc);
     if (tid == 0) {
@@ -1137,8 +1155,8 @@ template <int STORE, bool TRT, int MODE, bool STAGED, bool SPHD>
 __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE, STAGED>::minb)
     k_psm(const __grid_constant__ LbmArgs a, const __grid_constant__ PsmMaps m) {
     extern __shared__ __align__(128) unsigned char psm_smem[];
-    // small lattices: a.zsplit CTAs share a tile, each taking TILE_Z / zsplit of its planes
-    const int part = blockIdx.z % a.zsplit, per = TILE_Z / a.zsplit;
+    // small lattices: a.zsplit CTAs share a tile, each taking tz / zsplit of its planes
+    const int part = blockIdx.z % a.zsplit, per = a.tz / a.zsplit;
     if constexpr (STAGED)
         psm_tile_staged<STORE, TRT, MODE, SPHD>(a, m, blockIdx.x, blockIdx.y, blockIdx.z / a.zsplit, part * per,
                                                 part * per + per, psm_smem);
@@ -1149,8 +1167,9 @@ __global__ void __launch_bounds__(PSM_THREADS, PsmCfg<STORE, STAGED>::minb)
 
 // Host side: launch k_psm in form MODE (its shared-memory size is set on first use), and
 // the dispatch over storage format, collision operator, route (staged when maps are
-// given) and particle geometry (spheres with distance fractions only, or any; lattices
-// with 64-bit offsets take the general form).
+// given) and particle geometry (spheres with distance fractions only and no periodic
+// wrap of node-particle offsets, or any; lattices with 64-bit offsets take the general
+// form).
 template <int STORE, bool TRT, int MODE, bool STAGED, bool SPHD>
 static cudaError_t launch_psm_form(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
     static bool configured = false;
@@ -1170,7 +1189,8 @@ static cudaError_t launch_psm_form(const LbmArgs& a, const PsmMaps* m, cudaStrea
 template <int STORE, bool TRT, int MODE, bool STAGED>
 static cudaError_t launch_psm_geom(const LbmArgs& a, const PsmMaps* m, cudaStream_t s) {
     if constexpr (!psm_w64(MODE)) {
-        if (!a.subdiv_any) return launch_psm_form<STORE, TRT, MODE, STAGED, true>(a, m, s);
+        if (!a.subdiv_any && !a.mi[0] && !a.mi[1] && !a.mi[2])
+            return launch_psm_form<STORE, TRT, MODE, STAGED, true>(a, m, s);
     }
     return launch_psm_form<STORE, TRT, MODE, STAGED, false>(a, m, s);
 }

@@ -98,6 +98,8 @@ _SIGS = {
     "ledds_batch_sim": (C.c_int, [VP, C.c_int, C.POINTER(VP)]),
     "ledds_batch_step": (C.c_int, [VP, C.c_int]),
     "ledds_batch_destroy": (C.c_int, [VP]),
+    "ledds_batch_configure": (C.c_int, [VP, C.c_int, C.c_int, C.c_int]),
+    "ledds_batch_get_config": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ledds_batch_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int)]),
 }
 
@@ -461,6 +463,17 @@ class Batch:
 
     def sync(self):
         self.torch.cuda.synchronize()
+
+    def configure(self, tile_depth=16, ctas_per_sm=None, order=0):
+        if ctas_per_sm is None:
+            ctas_per_sm = self.config()["ctas_per_sm"]
+        check("ledds_batch_configure", lib().ledds_batch_configure(self.h, int(tile_depth), int(ctas_per_sm),
+                                                                   int(order)))
+
+    def config(self):
+        d, c, o = C.c_int(0), C.c_int(0), C.c_int(0)
+        check("ledds_batch_get_config", lib().ledds_batch_get_config(self.h, C.byref(d), C.byref(c), C.byref(o)))
+        return {"tile_depth": d.value, "ctas_per_sm": c.value, "order": o.value}
 
     def autotune(self, steps_per_trial=4):
         """Choose the persistent launch shape and work order by timing (advances the members)."""

@@ -82,7 +82,8 @@ def test_batch_autotune_keeps_the_step():
     ws = W.batched_ensemble(nsim=6, seed_index=58, storage="f32")
     b = ledds.batch_from_workloads(ws)
     choice = b.autotune(steps_per_trial=2)
-    assert 0 <= choice < 8
+    cfg = b.config()
+    assert 0 <= choice < 3 * cfg["ctas_per_sm"] * 2 + 6 and cfg["tile_depth"] in (8, 16, 32)
     b.step(3)
     steps = b.members[0].status()["steps"]
     assert steps >= 4 + 3
@@ -97,3 +98,42 @@ def test_batch_autotune_keeps_the_step():
             pb, _, _, _ = m.particles()
             ps, _, _, _ = s.particles()
             assert np.abs(pb - ps).max() < 1e-6
+
+
+@pytest.mark.parametrize("tile_depth", [8, 16, 32])
+def test_batch_tile_depths_match_independent_runs(tile_depth):
+    """Every tile shape the autotuner can choose (32 x 8 x depth, with either work order)
+    gives each member the results of the same simulation stepped on its own. The tiles'
+    FP32 partial sums group a particle's node forces differently for each depth, so the
+    forces differ in the last bits and the runs part at the rounding level (fields within
+    5e-6 after 13 steps)."""
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=6, seed_index=59, storage="f32")
+    b = ledds.batch_from_workloads(ws)
+    b.configure(tile_depth=tile_depth, order=tile_depth // 16 % 2)
+    assert b.config()["tile_depth"] == tile_depth
+    b.step(13)
+    for w, m in zip(ws, b.members):
+        s = gpu_from_workload(w)
+        s.step(13)
+        _, u_b = m.fields()
+        _, u_s = s.fields()
+        assert normwise(u_b.cpu().numpy(), u_s.cpu().numpy()) < 5e-6
+        if w.n:
+            pb, vb, _, _ = m.particles()
+            ps, vs, _, _ = s.particles()
+            assert np.abs(pb - ps).max() < 1e-6
+            assert normwise(vb, vs) < 1e-5
+        assert m.status()["rc"] == 0
+
+
+def test_batch_autotune_choice_is_cached_by_shape():
+    """A second batch of the same shape takes the first one's choice without trial steps."""
+    from paper_2512_04997_gb300 import ledds
+    ws = W.batched_ensemble(nsim=4, seed_index=60, storage="f16")
+    a = ledds.batch_from_workloads(ws)
+    c1 = a.autotune(steps_per_trial=1)
+    b = ledds.batch_from_workloads(ws)
+    c2 = b.autotune(steps_per_trial=1)
+    assert c1 == c2 and b.config() == a.config()
+    assert b.members[0].status()["steps"] == 0

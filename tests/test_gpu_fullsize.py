@@ -3,13 +3,18 @@ times: the 256^3 Couette suspension (4000 spheres R 6, FP32, n_sub 10, graph rep
 coupled step from its initial state. The oracle cannot step 16.7 M cells in a test, so it
 checks sampled outputs one by one:
 
-- sampled nodes (fluid and solid): the stored post-collision populations against the
-  oracle's collision of the same node (Eqs. psm1, lbePS) from the pre-collision
-  populations read before the step, with the solids the kernel found there (two largest
-  solid fractions, from ledds_voxelize at the positions the PSM stage used);
+- sampled nodes (fluid and solid): the oracle voxelises each node itself (its two largest
+  solid fractions among all 4000 spheres, at the positions the PSM stage used) and the
+  kernel's solids there must be the same; the stored post-collision populations are
+  checked against the oracle's collision of the node (Eqs. psm1, lbePS) from the
+  pre-collision populations read before the step, with the oracle's solids;
 - sampled particles: the hydrodynamic force and torque against the oracle's sum of the
-  node forces (Eqs. forceSF, torqueSF) over every node where the particle is a solid;
-- every node: its collision conserves mass.
+  node forces (Eqs. forceSF, torqueSF) over every node where the oracle finds the
+  particle among the node's solids;
+- every node: its collision conserves mass;
+- after 40 coupled steps (contacts active): the DEM part from the state read back there,
+  stepped by the kernel and by the oracle from identical positions, velocities and
+  orientations: contact forces and torques, velocities and the contact sets.
 
 In the first step after the particles are set, no sphere touches another (placement gap
 0.1, relative speeds below 0.005 per step) and no force acts during the DEM substeps, so
@@ -21,6 +26,8 @@ import pytest
 
 from paper_2512_04997_gb300 import workloads as W
 
+from _helpers import gpu_from_workload, normwise, oracle_from_workload
+
 pytestmark = pytest.mark.gpu
 
 
@@ -29,6 +36,14 @@ def _cuda():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+
+
+def _oracle_solids_sim(oracle, w, pos):
+    o = oracle.Sim(w.nx, w.ny, w.nz, periodic=w.periodic, u_wall=w.u_wall,
+                   params=oracle.default_params(tau=w.params["tau"], voxel=0),
+                   max_particles=w.n)
+    o.set_particles(w.shape, w.radius, w.semi, w.density, pos, w.vel, w.omg, w.triad)
+    return o
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +78,7 @@ def _arm(w, x, y, z, p):
 
 
 def _node_collide(oracle, w, pos, fpre, beta, ids, cell):
-    """Oracle collision of one node with the kernel's solids there (centres `pos`, the
+    """Oracle collision of one node with the given solids there (centres `pos`, the
     initial velocities); returns f*, node forces [ns, 3] and torques, and the solid ids."""
     nx, ny = w.nx, w.ny
     x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
@@ -82,6 +97,10 @@ def _node_collide(oracle, w, pos, fpre, beta, ids, cell):
     return fstar, Fk, Mk, kk
 
 
+def _xyz(w, c):
+    return c % w.nx, (c // w.nx) % w.ny, c // (w.nx * w.ny)
+
+
 def test_status_and_no_contacts(full_step):
     st = full_step["status"]
     assert st["rc"] == 0 and st["tile_overflow"] == 0 and st["cand_overflow"] == 0, st
@@ -93,6 +112,7 @@ def test_sampled_nodes_post_collision(oracle, full_step):
     import torch
     w, pos = full_step["w"], full_step["pos"]
     N = w.ncell
+    o = _oracle_solids_sim(oracle, w, pos)
     g = np.random.default_rng(2024)
     nsol = full_step["nsol"]
     solid_cells = (nsol > 0).nonzero().flatten()
@@ -104,37 +124,59 @@ def test_sampled_nodes_post_collision(oracle, full_step):
     ci = torch.as_tensor(cells, device=dev)
     fpre = full_step["f_pre"][:, ci].cpu().numpy().astype(np.float64)
     fpost = full_step["f_post"][:, ci].cpu().numpy().astype(np.float64)
-    beta = full_step["beta"][ci].cpu().numpy()
-    ids = full_step["ids"][ci].cpu().numpy()
+    beta_k = full_step["beta"][ci].cpu().numpy()
+    ids_k = full_step["ids"][ci].cpu().numpy()
+    nsol_k = nsol[ci].cpu().numpy()
     err = 0.0
     nsolid_seen = 0
     for j, c in enumerate(cells):
-        fstar, _, _, kk = _node_collide(oracle, w, pos, fpre[:, j], beta[j], ids[j], int(c))
+        ids_o, beta_o, tot_o = o.solids_at(*_xyz(w, int(c)))
+        # the kernel found the same solids (distance fractions: FP32 against FP64)
+        assert tot_o == nsol_k[j], (c, tot_o, nsol_k[j])
+        assert np.array_equal(ids_o, ids_k[j]), (c, ids_o, ids_k[j])
+        assert np.abs(beta_o - beta_k[j]).max() < 2e-5, (c, beta_o, beta_k[j])
+        fstar, _, _, kk = _node_collide(oracle, w, pos, fpre[:, j], beta_o, ids_o, int(c))
         nsolid_seen += len(kk) > 0
         err = max(err, np.abs(fstar - fpost[:, j]).max())
     assert nsolid_seen >= 1500
-    # FP32 collision of FP32 inputs against FP64: a few units in the last place of values <= 0.4
+    # FP32 collision of FP32 inputs against FP64 (and FP32 against FP64 solid fractions):
+    # a few units in the last place of values <= 0.4
     assert err < 5e-7, err
 
 
 def test_sampled_particles_hydrodynamic_force(oracle, full_step):
     w, pos = full_step["w"], full_step["pos"]
-    ids_all = full_step["ids"]
-    beta_all = full_step["beta"]
     f_pre = full_step["f_pre"]
+    o = _oracle_solids_sim(oracle, w, pos)
     g = np.random.default_rng(77)
     ks = g.choice(w.n, 12, replace=False)
     Fh, Mh = full_step["Fh"], full_step["Mh"]
+    import torch
     for k in ks:
-        cells = ((ids_all[:, 0] == int(k)) | (ids_all[:, 1] == int(k))).nonzero().flatten()
-        assert cells.numel() > 500          # a sphere of radius 6 covers ~900 nodes
-        fpre = f_pre[:, cells].cpu().numpy().astype(np.float64)
-        beta = beta_all[cells].cpu().numpy()
-        ids = ids_all[cells].cpu().numpy()
+        # every node where the oracle finds particle k among the node's solids: its
+        # bounding box (one lattice unit of margin), periodic images on x and y
+        r = pos[k]
+        e = w.radius[k] + 1.0
+        box = [np.arange(int(np.ceil(r[a] - e)), int(np.floor(r[a] + e)) + 1) for a in range(3)]
+        cells, betas, idss = [], [], []
+        for zz in box[2]:
+            if zz < 0 or zz >= w.nz:
+                continue
+            for yy in box[1]:
+                for xx in box[0]:
+                    x, y = xx % w.nx, yy % w.ny
+                    ids_o, beta_o, _ = o.solids_at(x, y, zz)
+                    if int(k) in ids_o:
+                        cells.append(x + w.nx * (y + w.ny * zz))
+                        betas.append(beta_o)
+                        idss.append(ids_o)
+        assert len(cells) > 500          # a sphere of radius 6 covers ~900 nodes
+        ci = torch.as_tensor(np.array(cells), device=f_pre.device)
+        fpre = f_pre[:, ci].cpu().numpy().astype(np.float64)
         F, M = np.zeros(3), np.zeros(3)
         Fabs, Mabs = np.zeros(3), np.zeros(3)
-        for j, c in enumerate(cells.cpu().numpy()):
-            _, Fk, Mk, kk = _node_collide(oracle, w, pos, fpre[:, j], beta[j], ids[j], int(c))
+        for j, c in enumerate(cells):
+            _, Fk, Mk, kk = _node_collide(oracle, w, pos, fpre[:, j], betas[j], idss[j], int(c))
             m = kk.index(int(k))
             F += Fk[m]
             M += Mk[m]
@@ -152,3 +194,45 @@ def test_mass_conserved_per_node(full_step):
     """Every node's collision (fluid or solid) conserves its mass: sum_i f*_i = sum_i f_i."""
     d = (full_step["f_post"].double().sum(0) - full_step["f_pre"].double().sum(0)).abs().max().item()
     assert d < 2e-6, d
+
+
+def test_dem_from_state_after_40_steps(oracle):
+    """The main workload after 40 coupled steps: its particle state (positions, velocities,
+    angular velocities, orientations) is read back and the DEM part is stepped from it by
+    the kernel and by the oracle (no fluid: the box's walls at the lattice's halfway planes
+    with their velocities, tangential histories starting at zero on both sides), with
+    random velocities added so that many spheres touch, two fluid steps of 10 substeps.
+    Contact sets are identical; the kernel's FP32 contact arithmetic keeps forces and
+    velocities within 1e-5 of the oracle's."""
+    import torch
+    from paper_2512_04997_gb300 import ledds
+    w = W.couette_suspension()
+    s = ledds.from_workload(w)
+    s.step(40)
+    pos, vel, omg, tri = s.particles()
+    assert s.status()["rc"] == 0
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    d = W.Workload(name="dem", box_lo=(-0.5, -0.5, -0.5), box_hi=(w.nx - 0.5, w.ny - 0.5, w.nz - 0.5),
+                   periodic=w.periodic)
+    d.u_wall = w.u_wall.copy()
+    d.params = dict(w.params)
+    d.shape, d.radius, d.semi, d.density = w.shape, w.radius, w.semi, w.density
+    # the suspension's lubricated spheres rarely touch in a few steps: random velocities
+    # of 0.05 per step (a gap of 0.1 closes in two) bring many into contact
+    d.pos, d.vel, d.omg, d.triad = pos, vel + W.rng(41).normal(0.0, 0.05, vel.shape), omg, tri
+    o = oracle_from_workload(oracle, d)
+    g = gpu_from_workload(d)
+    o.step(2)
+    g.step(2)
+    pairs_o, pairs_g = o.contacts(), g.pairs()
+    assert len(pairs_o) > 20, len(pairs_o)      # contacts are active
+    assert np.array_equal(pairs_g, pairs_o)
+    _, _, Fc_o, Mc_o = o.forces()
+    _, _, Fc_g, Mc_g = g.forces()
+    assert normwise(Fc_g, Fc_o) < 1e-5 and normwise(Mc_g, Mc_o) < 1e-5
+    po, vo, wo, _ = o.particles()
+    pg, vg, wg, _ = g.particles()
+    assert normwise(vg, vo) < 1e-5 and normwise(wg, wo) < 1e-5
+    assert np.abs(pg - po).max() < 1e-6

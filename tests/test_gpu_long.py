@@ -1,6 +1,7 @@
-"""Longer GPU parity runs and checkpoint resume: the 1000-step FP32 bound on a c3-shaped
-64^3 crop, the reduced-precision bounds (fields 2e-3, drag 0.5 %) on the settling sphere,
-and bit-identical resume from a checkpoint."""
+"""Longer GPU parity runs and checkpoint resume: a c3-shaped 64^3 crop in the default mode
+(50-step trajectories and 1000-step statistics), the particle-free crop at 1000 steps, the
+reduced-precision bounds (fields 2e-3, drag 0.5 %) on the settling sphere, and
+bit-identical resume from a checkpoint."""
 import math
 
 import numpy as np
@@ -20,28 +21,74 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
+def _profiles(w, u, pos):
+    """Mean streamwise velocity per z-layer, and the solid fraction per 8-layer slab: each
+    sphere's volume split exactly between the slabs its extent crosses (a smooth function
+    of the centres, so nearby trajectories give nearby profiles)."""
+    ux = np.asarray(u)[0].reshape(w.nz, w.ny, w.nx).mean(axis=(1, 2))
+    edges = np.arange(0, w.nz + 8, 8) - 0.5
+    R = w.radius[:, None]
+    zc = pos[:, 2][:, None]
+
+    def cap(zz):   # volume of the sphere below height zz
+        t = np.clip(zz - zc, -R, R)
+        return math.pi * (R ** 2 * t - t ** 3 / 3.0 + 2.0 * R ** 3 / 3.0)
+
+    vol = cap(edges[None, 1:]) - cap(edges[None, :-1])
+    phi = vol.sum(0) / (8.0 * w.nx * w.ny)
+    return ux, phi
+
+
 def test_couette_crop_1000_steps(oracle):
     """The Couette suspension shrunk to 64^3 (62 spheres R 6, same solid fraction, walls at
-    -/+0.05, n_sub 10), FP32 storage with FP64 contact arithmetic, against the FP64 oracle
-    in chunks of 250 steps. The sheared suspension is chaotic: the FP32 and FP64 particle
-    trajectories part exponentially (slowly), and the field difference follows them. The
-    1e-5 bound on fields holds through 500 steps; at 1000 steps the difference is held to
-    4e-5 (measured 2.0e-5) and printed. The particle-free lattice test below meets 1e-5 at
-    1000 steps."""
+    -/+0.05, n_sub 10), in the product's default mode (FP32 storage, FP32 contact
+    arithmetic), against the FP64 oracle. The sheared suspension is chaotic: FP32 and FP64
+    particle trajectories part exponentially, and the field difference follows them. So,
+    as the tolerance definitions for many-body runs state: (iii) fields and trajectories
+    after 50 steps within 1e-5, and (iv) statistics over 1000 steps: the mean velocity
+    profile within 1e-4 of its maximum, the solid-fraction profile (8-layer bins) within
+    1e-3, and the particles' kinetic energy within 1e-3. The pointwise field difference at
+    1000 steps is printed as a diagnostic."""
     w = W.couette_suspension(nx=64, ny=64, nz=64, n_particles=62, steps=1000)
-    w.params["force_fp32"] = 0
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
-    errs = []
-    for _ in range(4):
-        o.step(250)
-        s.step(250)
+    o.step(50)
+    s.step(50)
+    _, u_o = o.moments()
+    _, u_g = s.fields()
+    po, vo, _, _ = o.particles()
+    pg, vg, _, _ = s.particles()
+    e50 = normwise(u_g.cpu().numpy(), u_o)
+    assert e50 < 1e-5, e50
+    assert normwise(vg, vo) < 1e-5
+    assert np.abs(pg - po).max() < 1e-5
+    ux_sum_o = ux_sum_g = 0.0
+    phi_o = phi_g = 0.0
+    ke = []
+    for _ in range(19):                 # steps 50 .. 1000, statistics sampled every 50 steps
+        o.step(50)
+        s.step(50)
         _, u_o = o.moments()
         _, u_g = s.fields()
-        errs.append(normwise(u_g.cpu().numpy(), u_o))
-    print("field error every 250 steps:", ["%.2e" % e for e in errs])
-    assert max(errs[:2]) < 1e-5, errs
-    assert errs[3] < 4e-5, errs
+        po, vo, _, _ = o.particles()
+        pg, vg, _, _ = s.particles()
+        a, b = _profiles(w, u_o, po)
+        c, d = _profiles(w, u_g.cpu().numpy(), pg)
+        ux_sum_o, phi_o = ux_sum_o + a, phi_o + b
+        ux_sum_g, phi_g = ux_sum_g + c, phi_g + d
+        m = w.density * 4.0 / 3.0 * math.pi * w.radius ** 3
+        ke.append((0.5 * (m[:, None] * vo ** 2).sum(), 0.5 * (m[:, None] * vg ** 2).sum()))
+    prof = np.abs(ux_sum_g - ux_sum_o).max() / np.abs(ux_sum_o).max()
+    phid = np.abs(phi_g - phi_o).max() / 19.0
+    ke = np.array(ke)
+    ked = np.abs(ke[:, 1] - ke[:, 0]).max() / ke[:, 0].max()
+    e1000 = normwise(u_g.cpu().numpy(), u_o)
+    print(f"fields at 50 steps {e50:.2e}; over 1000 steps: mean profile {prof:.2e}, "
+          f"solid-fraction profile {phid:.2e}, kinetic energy {ked:.2e}; "
+          f"pointwise field difference at 1000 steps {e1000:.2e} (diagnostic)")
+    assert prof < 1e-4, prof
+    assert phid < 1e-3, phid
+    assert ked < 1e-3, ked
     st = s.status()
     assert st["rc"] == 0 and st["skin_violation"] == 0 and st["nan_detected"] == 0, st
 

@@ -160,15 +160,23 @@ def test_voxelize_parity(oracle, voxel):
                                                     ("distance", 2, "trt")])
 def test_coupled_small(oracle, voxel, n_sub, collision):
     """Several spheres and ellipsoids in a sheared box: fields, forces and trajectories
-    after 30 coupled steps (PSM + hydrodynamic force + DEM substeps + walls)."""
+    after 30 coupled steps (PSM + hydrodynamic force + DEM substeps + walls). The
+    hydrodynamic force and torque of a particle are sums of node terms that largely
+    cancel, so their bound is relative to the sum of the terms' magnitudes (the condition
+    of the sum, as at full size): 2e-5 of it per particle; the angular velocity integrates
+    such torques over the 30 steps, so its bound adds 30 dt times 2e-5 of that magnitude
+    over the particle's smallest moment of inertia."""
     shapes = [0] * 5 + ([1] * 2 if voxel == "subdiv" else [])
     w = _particles_workload(40, 26, 24, (1, 1, 0), voxel, 503, shapes, radius=3.0, clear=True)
     w.params.update(n_sub=n_sub, k_n=20.0, k_t=20.0 * 2 / 7, gravity=(0, 0, -2e-5), collision=collision)
     w.u_wall[2, 1] = [0.03, 0.0, 0.0]
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
-    o.step(30)
-    s.step(30)
+    o.step(29)
+    s.step(29)
+    f_pre = o.populations()          # pre-collision populations of the last step
+    o.step(1)
+    s.step(1)
     _, u_o = o.moments()
     _, u_g = s.fields()
     assert normwise(u_g.cpu().numpy(), u_o) < FP32_TOL
@@ -176,10 +184,40 @@ def test_coupled_small(oracle, voxel, n_sub, collision):
     pg, vg, wg, tg = s.particles()
     assert np.abs(pg - po).max() < 1e-6
     assert normwise(vg, vo) < FP32_TOL
-    assert normwise(wg, wo) < 1e-4
     Fh_o, Mh_o, Fc_o, Mc_o = o.forces()
     Fh_g, Mh_g, Fc_g, Mc_g = s.forces()
-    assert normwise(Fh_g, Fh_o) < 1e-4
+    # magnitudes of the node terms of the last step's sums (the oracle's collision of every
+    # solid node, at the positions the step used)
+    beta, ids, _ = o.voxelize()
+    n = w.n
+    Fabs, Mabs = np.zeros((n, 3)), np.zeros((n, 3))
+    tau = w.params["tau"]
+    for c in np.nonzero(beta[:, 0] > 0)[0]:
+        x, y, z = c % w.nx, (c // w.nx) % w.ny, c // (w.nx * w.ny)
+        B, uk, arm, kk = [], [], [], []
+        for m in range(2):
+            k = int(ids[c, m])
+            if k < 0 or not beta[c, m] > 0:
+                continue
+            a = np.array([x, y, z], float) - po[k]
+            a[0] -= w.nx * round(a[0] / w.nx)
+            a[1] -= w.ny * round(a[1] / w.ny)
+            B.append(oracle.bk(beta[c, m], tau))
+            uk.append(vo[k] + np.cross(wo[k], a))
+            arm.append(a)
+            kk.append(k)
+        _, Fk, Mk = oracle.cell_collide(f_pre[:, c], tau, B, uk, arm, force=w.params["fluid_force"],
+                                        collision={"bgk": 0, "trt": 1}[collision])
+        for m, k in enumerate(kk):
+            Fabs[k] += np.abs(Fk[m])
+            Mabs[k] += np.abs(Mk[m])
+    assert np.all(np.abs(Fh_g - Fh_o) <= 2e-5 * Fabs + 1e-12), np.abs(Fh_g - Fh_o) / (Fabs + 1e-30)
+    assert np.all(np.abs(Mh_g - Mh_o) <= 2e-5 * Mabs + 1e-12), np.abs(Mh_g - Mh_o) / (Mabs + 1e-30)
+    m = w.density * np.where(w.shape == 1, 4.0 / 3.0 * np.pi * w.semi.prod(1), 4.0 / 3.0 * np.pi * w.radius ** 3)
+    s2 = w.semi ** 2
+    Imin = 0.2 * m * np.min(np.stack([s2[:, 1] + s2[:, 2], s2[:, 0] + s2[:, 2], s2[:, 0] + s2[:, 1]]), axis=0)
+    wtol = 1e-5 * np.abs(wo).max() + 30 * 2e-5 * Mabs.max(1) / Imin
+    assert np.all(np.abs(wg - wo).max(1) <= wtol), (np.abs(wg - wo).max(1), wtol)
     st = s.status()
     assert st["rc"] == 0 and st["skin_violation"] == 0, st
 

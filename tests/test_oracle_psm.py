@@ -232,3 +232,30 @@ def test_jeffery_rotation_rate(oracle, angle):
     jeffery = shear * (r * r * math.sin(phi) ** 2 + math.cos(phi) ** 2) / (r * r + 1.0)
     assert omg[0][1] > 0.0
     assert abs(omg[0][1] / jeffery - 1.0) < 0.08, (omg[0][1], jeffery)
+
+
+@pytest.mark.parametrize("voxel,periodic", [("distance", (1, 1, 0)), ("subdiv", (1, 0, 1))])
+def test_solids_at_matches_lattice_voxelisation(oracle, voxel, periodic):
+    """The oracle's one-node voxelisation (used for spot checks of lattices too large to
+    voxelise whole) gives, node by node, exactly the whole-lattice result: the same two
+    solids, fractions and counts, with spheres and ellipsoids across periodic faces."""
+    g = W.rng(5)
+    n = 12
+    w = W.Workload(name="t", nx=30, ny=22, nz=26, periodic=periodic)
+    w.params = W.base_params(voxel=voxel, dem_h=0.0)
+    w.shape = (np.arange(n) % 3 == 0).astype(np.int32)
+    w.radius = g.uniform(2, 4, n)
+    w.semi = np.stack([w.radius * 1.4, w.radius * 0.8, w.radius * 0.7], 1)
+    w.semi[w.shape == 0] = np.stack([w.radius] * 3, 1)[w.shape == 0]
+    w.density = np.ones(n)
+    w.pos = g.uniform(0, 1, (n, 3)) * [30, 22, 26]
+    w.vel = np.zeros((n, 3))
+    w.omg = np.zeros((n, 3))
+    w.triad = W.quaternion_to_triad(W.random_quaternions(g, n))
+    o = oracle.from_workload(w)
+    b, ids, ns = o.voxelize()
+    assert (ns > 1).sum() > 25 and (ns > 0).sum() > 2000
+    for c in range(w.ncell):
+        x, y, z = c % 30, (c // 30) % 22, c // (30 * 22)
+        i2, b2, t = o.solids_at(x, y, z)
+        assert np.array_equal(i2, ids[c]) and np.array_equal(b2, b[c]) and t == ns[c], (c, i2, ids[c])
