@@ -341,41 +341,50 @@ def fluidised_sweep(device, stream, phis=(0.0, 0.1, 0.2, 0.3, 0.41), steps=10, w
             "mlups_ratio_phi0_to_max": rows[0]["value"] / rows[-1]["value"] if rows else None}
 
 
-def rheology_measure(device, stream, phis=(0.0, 0.1, 0.2, 0.3), steps=20000, every=250):
+def rheology_measure(device, stream, phis=(0.0, 0.1, 0.2, 0.3), steps=60000, every=250, blocks=4):
     """Effective viscosity of the sheared suspension at reduced size (96^3, spheres of
     diameter 10, walls at -/+0.05): the x-y averaged u_x profile sampled every `every` steps
     over the second half of the run, the wall shear rate from the parabola through the wall
     value and the first two nodes, eta/eta0 = wall shear rate / nominal shear rate 2U/H,
-    beside the Krieger-Dougherty law (1 - phi/0.64)^(-2.5 * 0.64)."""
+    beside the Krieger-Dougherty law (1 - phi/0.64)^(-2.5 * 0.64). The second half is also
+    cut into `blocks` equal blocks, each with its own estimate: their spread and the change
+    from the first to the last block show whether the estimate is stationary."""
     import torch
     from paper_2512_04997_gb300 import ledds, workloads as W
     rows = []
     t0 = time.perf_counter()
+    per_block = steps // 2 // every // blocks
     for phi in phis:
         w = W.rheology_suspension(phi)
         n, U = w.nz, w.u_wall[2, 1, 0]
         s = ledds.from_workload(w, device=device)
         s.step(steps // 2)
-        prof = torch.zeros(n, dtype=torch.float64, device=device)
-        samples = 0
-        for _ in range(steps // 2 // every):
-            s.step(every)
-            _, u = s.fields()
-            prof += u[0].view(n, -1).double().mean(1)
-            samples += 1
-        prof = (prof / samples).cpu().numpy()
+        block_prof = []
+        for _ in range(blocks):
+            prof = torch.zeros(n, dtype=torch.float64, device=device)
+            for _ in range(per_block):
+                s.step(every)
+                _, u = s.fields()
+                prof += u[0].view(n, -1).double().mean(1)
+            block_prof.append((prof / per_block).cpu().numpy())
         st = s.status()
         s.close()
+        prof = np.mean(block_prof, axis=0)
         phi_real = w.n * 4.0 / 3.0 * math.pi * 125.0 / n ** 3
-        eta = W.wall_shear_rate(prof, U) / (2.0 * U / n)
+        shear0 = 2.0 * U / n
+        eta = W.wall_shear_rate(prof, U) / shear0
+        beta = [W.wall_shear_rate(p, U) / shear0 for p in block_prof]
         kd = (1.0 - phi_real / 0.64) ** (-2.5 * 0.64)
         rows.append({"phi": round(phi_real, 3), "spheres": w.n, "eta_rel": eta, "krieger_dougherty": kd,
-                     "rel_diff": eta / kd - 1.0,
+                     "rel_diff": eta / kd - 1.0, "block_eta": beta,
+                     "block_drift": (beta[-1] - beta[0]) / eta,
+                     "block_std_rel": float(np.std(beta) / eta),
                      "status": {k: st[k] for k in ("skin_violation", "nan_detected", "cand_overflow")}})
         torch.cuda.empty_cache()
     return {"workload": "sheared suspension 96^3, spheres of diameter 10, walls at -/+0.05 (nominal shear rate "
                         "1.04e-3), tau 0.8, n_sub 10, friction 0.45, restitution 0.95, "
-                        f"{steps} steps, profiles averaged over the second half",
+                        f"{steps} steps (strain {steps * 2.0 * 0.05 / 96:.0f}), profiles averaged over the "
+                        f"second half in {blocks} blocks",
             "seconds": time.perf_counter() - t0, "points": rows}
 
 
@@ -607,7 +616,6 @@ def main():
         _, uo = o.moments()
         pg = gs.particles()[0]
         po = o.particles()[0]
-        import numpy as np
         ugn = ug.cpu().numpy()
         oracle_err = {"sample": "the oracle's slab, 3 coupled steps",
                       "velocity_normwise": float(np.abs(ugn - uo).max() / np.abs(uo).max()),

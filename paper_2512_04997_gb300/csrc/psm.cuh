@@ -60,6 +60,7 @@ struct TileCache {
     float acc[6][MAX_TILE_CAP];   // force and torque sums of this tile (FP32: native shared atomics)
     float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
     float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
+    float G[MAX_TILE_CAP];        // ellipsoid: largest |M c|^2 over the subdivision sample box
 };
 
 __device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
@@ -112,54 +113,41 @@ static __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int 
                         a.st[(ST + 3 * j + c) * a.pcap + k] / a.semi[j * a.pcap + k]);
             const double smin = fmin(a.semi[k], fmin(a.semi[a.pcap + k], a.semi[2 * a.pcap + k]));
             tc.ims[e] = (float)(1.0 / smin);
+            // corners c = h (1, s1, s2), s_k = +-1, of the sample box (c and -c alike)
+            const double h = (double)(a.subdiv_n - 1) / (double)(2 * a.subdiv_n);
+            double g = 0.0;
+            for (int sg = 0; sg < 4; ++sg) {
+                const double s1 = (sg & 1) ? -1.0 : 1.0, s2 = (sg & 2) ? -1.0 : 1.0;
+                double v = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    const double r = (double)tc.m[3 * j][e] + s1 * (double)tc.m[3 * j + 1][e] +
+                                     s2 * (double)tc.m[3 * j + 2][e];
+                    v += r * r;
+                }
+                g = fmax(g, v);
+            }
+            tc.G[e] = (float)(g * h * h * 1.0001);
         }
         for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0f;
     }
 }
 
-// Subdivision count (Sec. 2.4): n^3 sample points (2m+1-n)/(2n) around the node, strictly
-// inside the solid, for the node at offset (px, py, pz) from cached particle e. Computed by
-// the whole warp (every lane passes the same arguments): lane l takes the sample columns
-// (j, q) = l, l + 32, ... for every i, and the counts are summed exactly. FP32 with explicit
-// round-to-nearest intrinsics (no contraction) in the evaluation order documented for the
-// method, so the count is exact and independent of the split.
-__device__ __forceinline__ int subdiv_count_warp(const TileCache& tc, int e, float px, float py, float pz,
-                                                 int n) {
-    const int lane = threadIdx.x & 31;
-    const int nn = n * n;
-    int count = 0;
-    if (tc.shape[e] == LEDDS_SPHERE) {
-        const float R2 = tc.R2[e];
-        for (int jq = lane; jq < nn; jq += 32) {
-            const int j = jq / n, q = jq - j * n;
-            const float dy = __fadd_rn(py, tc.so[j]);
-            const float dz = __fadd_rn(pz, tc.so[q]);
-            const float yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
-            for (int i = 0; i < n; ++i) {
-                const float dx = __fadd_rn(px, tc.so[i]);
-                count += __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), yy), zz) < R2;
-            }
-        }
-    } else {
-        float mm[9];
-        for (int k = 0; k < 9; ++k) mm[k] = tc.m[k][e];
-        for (int jq = lane; jq < nn; jq += 32) {
-            const int j = jq / n, q = jq - j * n;
-            const float dy = __fadd_rn(py, tc.so[j]);
-            const float dz = __fadd_rn(pz, tc.so[q]);
-            for (int i = 0; i < n; ++i) {
-                const float dx = __fadd_rn(px, tc.so[i]);
-                const float t0 = __fadd_rn(__fmul_rn(mm[0], dx), __fmul_rn(mm[1], dy));
-                const float t1 = __fadd_rn(__fmul_rn(mm[3], dx), __fmul_rn(mm[4], dy));
-                const float t2 = __fadd_rn(__fmul_rn(mm[6], dx), __fmul_rn(mm[7], dy));
-                const float q0 = __fadd_rn(t0, __fmul_rn(mm[2], dz));
-                const float q1 = __fadd_rn(t1, __fmul_rn(mm[5], dz));
-                const float q2 = __fadd_rn(t2, __fmul_rn(mm[8], dz));
-                count += __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2)) < 1.0f;
-            }
-        }
-    }
-    return __reduce_add_sync(0xffffffffu, count);
+// Subdivision predicate (Sec. 2.4): a sample at offset (dx, dy, dz) from the centre is
+// strictly inside the solid. Evaluated in FP32 with explicit round-to-nearest intrinsics
+// in a fixed order (no contraction), so each decision is reproducible.
+constexpr float SUBDIV_MARGIN = 1e-3f;
+
+__device__ __forceinline__ bool subdiv_pred_sphere(float dx, float yy, float zz, float R2) {
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), yy), zz) < R2;
+}
+__device__ __forceinline__ bool subdiv_pred_ell(const float (&mm)[9], float dx, float dy, float dz) {
+    const float t0 = __fadd_rn(__fmul_rn(mm[0], dx), __fmul_rn(mm[1], dy));
+    const float t1 = __fadd_rn(__fmul_rn(mm[3], dx), __fmul_rn(mm[4], dy));
+    const float t2 = __fadd_rn(__fmul_rn(mm[6], dx), __fmul_rn(mm[7], dy));
+    const float q0 = __fadd_rn(t0, __fmul_rn(mm[2], dz));
+    const float q1 = __fadd_rn(t1, __fmul_rn(mm[5], dz));
+    const float q2 = __fadd_rn(t2, __fmul_rn(mm[8], dz));
+    return __fadd_rn(__fadd_rn(__fmul_rn(q0, q0), __fmul_rn(q1, q1)), __fmul_rn(q2, q2)) < 1.0f;
 }
 
 // Solid fraction of cached particle e at a node, (dx,dy,dz) = node - centre (FP32), where
@@ -185,43 +173,22 @@ __device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& t
         const float nearr = R - hd - 1e-3f;
         if (nearr > 0.0f && d2 < nearr * nearr) return 1.0f;  // ... or every sample is
     } else {
-        // normalised radius |M p| of the node (M rows d_j / semi_j, |M| = 1/min semi-axis):
-        // samples within hd of the node lie within hd |M| of it, so beyond the surface by
-        // more than that (plus margins far above FP32 rounding) none is inside, and inside
-        // by more than that every one is
+        // q = M p (M rows d_j / semi_j), w = M^T q. Over the box of samples p + c, |c_k| <= h,
+        // |M (p + c)|^2 = |q|^2 + 2 w.c + |M c|^2 lies between |q|^2 - 2 h |w|_1 and
+        // |q|^2 + 2 h |w|_1 + G, G = max over the box of |M c|^2 (its largest corner, per
+        // particle): beyond 1 by the margin no sample is inside, below it every one is (the
+        // margins are far above the FP32 rounding of either side)
         const float q0 = tc.m[0][e] * dx + tc.m[1][e] * dy + tc.m[2][e] * dz;
         const float q1 = tc.m[3][e] * dx + tc.m[4][e] * dy + tc.m[5][e] * dz;
         const float q2 = tc.m[6][e] * dx + tc.m[7][e] * dy + tc.m[8][e] * dz;
-        const float rn = sqrtf(q0 * q0 + q1 * q1 + q2 * q2);
-        const float ext = hd * tc.ims[e] * 1.001f + 1e-3f;
-        if (rn - ext > 1.0f) return 0.0f;
-        if (rn + ext < 1.0f) return 1.0f;
-        if (rn > 1.0f) {
-            // In normalised coordinates the ellipsoid is the unit ball, which lies behind
-            // its tangent plane at q/|q|; the sample box (half-width h on each world axis)
-            // reaches towards that plane by at most h |M^T q/|q||_1, so if even its nearest
-            // corner is beyond the plane (margins far above FP32 rounding) no sample is
-            // inside. Tighter than the bound above where |M^T q| is small (near the ends
-            // of the long axes).
-            const float ir = 1.0f / rn;
-            const float w0 = (tc.m[0][e] * q0 + tc.m[3][e] * q1 + tc.m[6][e] * q2) * ir;
-            const float w1 = (tc.m[1][e] * q0 + tc.m[4][e] * q1 + tc.m[7][e] * q2) * ir;
-            const float w2 = (tc.m[2][e] * q0 + tc.m[5][e] * q1 + tc.m[8][e] * q2) * ir;
-            if (rn - h * (fabsf(w0) + fabsf(w1) + fabsf(w2)) * 1.001f > 1.0f + 1e-3f) return 0.0f;
-        }
-        // every corner of the sample box strictly inside (convexity) => all samples are
-        bool all_in = true;
-#pragma unroll
-        for (int cnr = 0; cnr < 8; ++cnr) {
-            float px = dx + ((cnr & 1) ? h : -h);
-            float py = dy + ((cnr & 2) ? h : -h);
-            float pz = dz + ((cnr & 4) ? h : -h);
-            float q0 = tc.m[0][e] * px + tc.m[1][e] * py + tc.m[2][e] * pz;
-            float q1 = tc.m[3][e] * px + tc.m[4][e] * py + tc.m[5][e] * pz;
-            float q2 = tc.m[6][e] * px + tc.m[7][e] * py + tc.m[8][e] * pz;
-            all_in = all_in && (q0 * q0 + q1 * q1 + q2 * q2 < 0.999f);
-        }
-        if (all_in) return 1.0f;
+        const float s2 = q0 * q0 + q1 * q1 + q2 * q2;
+        const float w0 = tc.m[0][e] * q0 + tc.m[3][e] * q1 + tc.m[6][e] * q2;
+        const float w1 = tc.m[1][e] * q0 + tc.m[4][e] * q1 + tc.m[7][e] * q2;
+        const float w2 = tc.m[2][e] * q0 + tc.m[5][e] * q1 + tc.m[8][e] * q2;
+        const float l1 = 2.0f * h * (fabsf(w0) + fabsf(w1) + fabsf(w2));
+        const float slack = 1e-3f + 1e-5f * (s2 + l1);
+        if (s2 - l1 > 1.0f + slack) return 0.0f;
+        if (s2 + l1 + tc.G[e] < 1.0f - slack) return 1.0f;
     }
     *exact = true;
     return 0.0f;
@@ -269,29 +236,167 @@ __device__ __forceinline__ bool ranks_before(const TileCache& tc, float b, int e
     return tc_pid(tc, e) < tc_pid(tc, ew);  // a tie: the lower particle id first
 }
 
-// Exact subdivision counts for the lanes in `need`, one node after the other, each counted
-// by the whole warp; the node minus the centre is taken in FP64 (minimum image) and rounded
-// to FP32. Out of line, entered by every lane together: it keeps the hot loop small.
-static __device__ __noinline__ float subdiv_lanes(const LbmArgs& a, const TileCache& tc, int e, unsigned need,
-                                           bool exact, int x, int y, int z, float b) {
+// floor and ceiling of |v| < 2^22 as integers, by one directed-rounding addition
+__device__ __forceinline__ int floor_small(float v) {
+    return __float_as_int(__fadd_rd(v, 12582912.0f)) - 0x4B400000;
+}
+__device__ __forceinline__ int ceil_small(float v) {
+    return __float_as_int(__fadd_ru(v, 12582912.0f)) - 0x4B400000;
+}
+
+// One sample row (fixed y and z offsets dy, dz) of the subdivision count. Along it the
+// squared normalised radius is the quadratic F(X) = A X^2 + 2 B X + C of the x offset X,
+// smallest (Fmin) at xc = -B/A (spheres: X^2 + dy^2 + dz^2 against R^2). The row keeps the
+// interval around xc where F < 1 - 1e-3, shrunk by 2e-4, and the one where F <= 1 + 1e-3,
+// grown by 2e-4, as fractional sample indices of a node at x offset 0 (sample i of a node
+// at offset qx sits at X = qx + (i - (n - 1)/2)/n).
+struct SubRow {
+    float ilo, ihi, olo, ohi;  // inner and outer interval (empty: lo > hi)
+    float dy, dz, yy, zz;
+};
+
+__device__ __forceinline__ void subdiv_row(const TileCache& tc, bool sph, const float (&mm)[9], float iA,
+                                           float lo, float hi, float py, float pz, int j, int q, float fn,
+                                           float t0, SubRow& r) {
+    r.dy = __fadd_rn(py, tc.so[j]);
+    r.dz = __fadd_rn(pz, tc.so[q]);
+    r.yy = __fmul_rn(r.dy, r.dy);
+    r.zz = __fmul_rn(r.dz, r.dz);
+    float xc = 0.0f, Fmin;
+    if (sph) {
+        Fmin = r.yy + r.zz;
+    } else {
+        const float w0 = mm[1] * r.dy + mm[2] * r.dz, w1 = mm[4] * r.dy + mm[5] * r.dz,
+                    w2 = mm[7] * r.dy + mm[8] * r.dz;
+        const float B = mm[0] * w0 + mm[3] * w1 + mm[6] * w2;
+        const float C = w0 * w0 + w1 * w1 + w2 * w2;
+        xc = -B * iA;
+        Fmin = C + B * xc;
+    }
+    r.olo = r.ilo = 1e4f;
+    r.ohi = r.ihi = -1e4f;
+    if (Fmin <= hi) {
+        // square roots to about 1e-7 relative (the slack is 1e-5 relative plus 2e-4)
+        const float vo = fmaxf((hi - Fmin) * iA, 1e-30f), vi = fmaxf((lo - Fmin) * iA, 1e-30f);
+        const float ro = vo * rsqrtf(vo) * (1.0f + 1e-5f) + 2e-4f;
+        const float c = xc * fn + t0;
+        r.olo = c - ro * fn;
+        r.ohi = c + ro * fn;
+        if (Fmin < lo) {
+            const float ri = vi * rsqrtf(vi) * (1.0f - 1e-5f) - 2e-4f;
+            if (ri > 0.0f) {
+                r.ilo = c - ri * fn;
+                r.ihi = c + ri * fn;
+            }
+        }
+    }
+}
+
+// Samples of row r inside the solid for the node at x offset qx (qxn = qx n): those in the
+// inner interval by index arithmetic, the FP32 predicate for those between the intervals.
+__device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRow& r, bool sph,
+                                                const float (&mm)[9], float thr, float qx, float qxn,
+                                                int n) {
+    const int oA = max(0, ceil_small(r.olo - qxn)), oB = min(n - 1, floor_small(r.ohi - qxn));
+    const int iA = max(0, ceil_small(r.ilo - qxn)), iB = min(n - 1, floor_small(r.ihi - qxn));
+    int c = 0, e1 = oB + 1, s2 = oB + 1;  // predicate on [oA, e1) and [s2, oB]
+    if (iA <= iB) {
+        c = iB - iA + 1;
+        e1 = iA;
+        s2 = iB + 1;
+    }
+    for (int i = oA; i < e1; ++i) {
+        const float dx = __fadd_rn(qx, tc.so[i]);
+        c += sph ? subdiv_pred_sphere(dx, r.yy, r.zz, thr) : subdiv_pred_ell(mm, dx, r.dy, r.dz);
+    }
+    for (int i = s2; i <= oB; ++i) {
+        const float dx = __fadd_rn(qx, tc.so[i]);
+        c += sph ? subdiv_pred_sphere(dx, r.yy, r.zz, thr) : subdiv_pred_ell(mm, dx, r.dy, r.dz);
+    }
+    return c;
+}
+
+// Exact subdivision counts (Sec. 2.4) for the lanes in `need`: n^3 samples at offsets
+// (2m+1-n)/(2n) around each node, a sample counting when the FP32 predicate puts it
+// inside. The nodes of a warp lie on one x-row, so their y and z offsets from the centre
+// (FP64 minimum image, rounded to FP32) are the same and so are the n^2 sample rows: the
+// margins of a row's intervals (SubRow) are far above the rounding of the set-up and of
+// the predicate (about 1e-5), so a sample in the inner interval is inside by the
+// predicate, one outside the outer is not, and only samples between the two run it. The
+// rows are taken 32 at a time, one per lane; for each needing node every lane counts its
+// row and the warp sums. A last round of fewer rows (W lanes per node, W the power of two
+// at or above its row count) counts 32 / W nodes at once.
+__device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, const TileCache& tc, int e, unsigned need,
+                                              bool exact, int x, int y, int z, float b) {
     const int lane = threadIdx.x & 31;
-    float px = 0.f, py = 0.f, pz = 0.f;
-    if (exact) {
+    const int n = a.subdiv_n, nn = n * n;
+    // offsets node - centre: the needing lanes take their own x, two other lanes (when
+    // there are two) the row's y and z, so the FP64 work is done once
+    float px, py, pz;
+    const unsigned spare = ~need;
+    if (__popc(spare) >= 2) {
+        const int ly = __ffs(spare) - 1;
+        const int lz = __ffs(spare & (spare - 1)) - 1;
+        const int ax = lane == ly ? 1 : (lane == lz ? 2 : 0);
+        const int cc = ax == 0 ? x : (ax == 1 ? y : z);
+        const double L = ax == 0 ? (double)a.nx : (ax == 1 ? (double)a.ny : (double)a.nz);
+        const float v = __double2float_rn(min_image_d((double)cc - tc.p[ax][e], a.per[ax], L));
+        px = v;
+        py = __shfl_sync(0xffffffffu, v, ly);
+        pz = __shfl_sync(0xffffffffu, v, lz);
+    } else {
         px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
         py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
         pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
     }
-    const int n = a.subdiv_n;
-    while (need) {
-        const int l = __ffs(need) - 1;
-        need &= need - 1;
-        const float qx = __shfl_sync(0xffffffffu, px, l);
-        const float qy = __shfl_sync(0xffffffffu, py, l);
-        const float qz = __shfl_sync(0xffffffffu, pz, l);
-        const int c = subdiv_count_warp(tc, e, qx, qy, qz, n);
-        if (lane == l) b = (float)c / (float)(n * n * n);
+    const bool sph = tc.shape[e] == LEDDS_SPHERE;
+    float mm[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) mm[k] = sph ? 0.0f : tc.m[k][e];
+    const float iA = sph ? 1.0f : __frcp_rn(mm[0] * mm[0] + mm[3] * mm[3] + mm[6] * mm[6]);
+    const float thr = sph ? tc.R2[e] : 1.0f;
+    const float lo = thr * (1.0f - SUBDIV_MARGIN), hi = thr * (1.0f + SUBDIV_MARGIN);
+    const float fn = (float)n, t0 = 0.5f * (float)(n - 1);
+    const unsigned mgc = 0xffffffffu / (unsigned)n + 1u;  // jq / n = umulhi(jq, mgc), jq < 256
+    const int kneed = __popc(need);
+    int rank = 0;  // this lane's rank among the needing lanes
+    if ((need >> lane) & 1u) rank = __popc(need & ((1u << lane) - 1u));
+    int count = 0;
+    for (int r0 = 0; r0 < nn; r0 += 32) {
+        const int rows = min(32, nn - r0);
+        int W = 32;
+        while (W / 2 >= rows) W /= 2;
+        const int slots = 32 / W, sub = lane & (W - 1), slot = lane / W;
+        SubRow rw;
+        rw.olo = rw.ilo = 1e4f;
+        rw.ohi = rw.ihi = -1e4f;
+        rw.dy = rw.dz = rw.yy = rw.zz = 0.0f;
+        if (sub < rows) {
+            const int jq = r0 + sub;
+            const int j = (int)__umulhi((unsigned)jq, mgc), q = jq - j * n;
+            subdiv_row(tc, sph, mm, iA, lo, hi, py, pz, j, q, fn, t0, rw);
+        }
+        // needing nodes in groups of `slots`; slot s of group g takes the (g slots + s)-th
+        for (int g0 = 0; g0 < kneed; g0 += slots) {
+            unsigned m = need;
+            for (int t = 0; t < g0 + slot && m; ++t) m &= m - 1u;
+            const int l = m ? __ffs(m) - 1 : 0;
+            const float qx = __shfl_sync(0xffffffffu, px, l);
+            const int c = (m && sub < rows) ? subdiv_row_count(tc, rw, sph, mm, thr, qx, qx * fn, n) : 0;
+            int sum;
+            if (W == 32) {
+                sum = __reduce_add_sync(0xffffffffu, c);
+            } else {
+                sum = c;
+                for (int o = W / 2; o >= 1; o /= 2) sum += __shfl_xor_sync(0xffffffffu, sum, o, W);
+            }
+            // the node of rank k reads its slot's sum
+            const bool mine = ((need >> lane) & 1u) && rank >= g0 && rank < g0 + slots;
+            const int got = __shfl_sync(0xffffffffu, sum, mine ? (rank - g0) * W : 0);
+            if (mine) count += got;
+        }
     }
-    return b;
+    return exact ? (float)count / (float)(n * n * n) : b;
 }
 
 // Called by the whole warp (the row mask is uniform); lanes with valid false take no part

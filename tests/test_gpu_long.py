@@ -1,7 +1,8 @@
 """Longer GPU parity runs and checkpoint resume: a c3-shaped 64^3 crop in the default mode
 (50-step trajectories and 1000-step statistics), the particle-free crop at 1000 steps, the
-reduced-precision bounds (fields 2e-3, drag 0.5 %) on the settling sphere, and
-bit-identical resume from a checkpoint."""
+reduced-precision bounds (fields 2e-3, drag 0.5 %) on the settling sphere and on crops
+of the two benchmark workloads against the oracle, the rheology workload on a 48^3 crop,
+and bit-identical resume from a checkpoint."""
 import math
 
 import numpy as np
@@ -130,6 +131,70 @@ def test_settling_sphere_reduced_precision(oracle, storage):
     print(f"{storage}: field error {err_u:.3e}, drag error {drag_err:.3e}")
     assert err_u < 2e-3, err_u
     assert drag_err < 5e-3, drag_err
+
+
+@pytest.mark.parametrize("storage", [
+    "f16",
+    pytest.param("bf16", marks=pytest.mark.xfail(
+        reason="BF16 keeps 8 significand bits; its field error against the FP64 oracle is above "
+               "2e-3 (the bound is not loosened)", strict=False)),
+])
+@pytest.mark.parametrize("case", ["couette_crop", "ellipsoid_crop"])
+def test_reduced_precision_crops_vs_oracle(oracle, storage, case):
+    """16-bit population storage against the FP64 oracle (not against FP32) on crops of the
+    two benchmark workloads: the 256^3 Couette suspension shrunk to 64^3 (62 spheres, 100
+    steps) and the sheared ellipsoid suspension shrunk to 48x48x32 (its density of (6, 2, 2)
+    ellipsoids, subdivision fractions, 20 steps: the oracle counts every sample). Fields
+    within 2e-3; the FP32 run's error is printed beside it."""
+    if case == "couette_crop":
+        w = W.couette_suspension(nx=64, ny=64, nz=64, n_particles=62, storage=storage)
+        steps = 100
+    else:
+        w = W.ellipsoid_shear(nx=48, ny=48, nz=32, n_particles=52, storage=storage)
+        steps = 20
+    o = oracle_from_workload(oracle, w)
+    s = gpu_from_workload(w)
+    r = gpu_from_workload(w, storage="f32")
+    o.step(steps)
+    s.step(steps)
+    r.step(steps)
+    _, u_o = o.moments()
+    e16 = normwise(s.fields()[1].cpu().numpy(), u_o)
+    e32 = normwise(r.fields()[1].cpu().numpy(), u_o)
+    print(f"{case} {storage}: field error against the oracle {e16:.2e} (FP32 storage {e32:.2e})")
+    assert e32 < 1e-5
+    assert e16 < 2e-3, e16
+
+
+def test_rheology_crop_vs_oracle(oracle):
+    """The rheology workload (spheres of diameter 10, walls at -/+0.05, solid fraction 0.2,
+    friction 0.45, restitution 0.95, n_sub 10) on a 48^3 crop for 300 steps against the
+    oracle: fields, particle velocities, the mean velocity profile and the wall shear rate
+    the viscosity estimate uses."""
+    w = W.rheology_suspension(0.2, n=48)
+    o = oracle_from_workload(oracle, w)
+    s = gpu_from_workload(w)
+    o.step(300)
+    s.step(300)
+    _, u_o = o.moments()
+    _, u_g = s.fields()
+    u_g = u_g.cpu().numpy()
+    assert normwise(u_g, u_o) < 1e-5
+    _, vo, _, _ = o.particles()
+    _, vg, _, _ = s.particles()
+    assert normwise(vg, vo) < 1e-5
+    # the wall shear rate is a short difference of near-wall mean velocities (about 0.05)
+    # that cancels to about 0.003: its error is bounded against the size of the terms it
+    # differences, not against its own value
+    n, U = w.nz, w.u_wall[2, 1, 0]
+    po = np.asarray(u_o)[0].reshape(n, -1).mean(1)
+    pg = u_g[0].reshape(n, -1).mean(1)
+    assert normwise(pg, po) < 1e-5
+    go, gg = W.wall_shear_rate(po, U), W.wall_shear_rate(pg, U)
+    scale = 0.5 * (3.0 * abs(po[0]) + abs(po[1]) / 3.0 + 3.0 * abs(po[-1]) + abs(po[-2]) / 3.0)
+    print(f"wall shear rate {gg:.6e} against {go:.6e} (terms {scale:.3e})")
+    assert abs(gg - go) < 1e-5 * scale, (gg, go, scale)
+    assert w.n > 30
 
 
 def _resume_case(w, steps_a, steps_b):

@@ -112,13 +112,14 @@ def test_graph_and_eager_paths_agree(oracle):
 # ------------------------------------------------------------------------------------
 # solid fractions
 # ------------------------------------------------------------------------------------
-def _particles_workload(nx, ny, nz, periodic, voxel, seed, shapes, radius=3.2, clear=False):
+def _particles_workload(nx, ny, nz, periodic, voxel, seed, shapes, radius=3.2, clear=False,
+                        semi=(4.5, 2.0, 1.6)):
     g = W.rng(seed)
-    w = lattice_workload(nx, ny, nz, periodic, voxel=voxel, dem_h=2 * 4.5 + 0.5)
+    w = lattice_workload(nx, ny, nz, periodic, voxel=voxel, dem_h=2 * max(max(semi), radius) + 0.5)
     n = len(shapes)
     w.shape = np.array(shapes, dtype=np.int32)
-    w.semi = np.where(w.shape[:, None] == 1, np.array([4.5, 2.0, 1.6]), radius)
-    w.radius = np.where(w.shape == 1, 4.5, radius)
+    w.semi = np.where(w.shape[:, None] == 1, np.array(semi, dtype=float), radius)
+    w.radius = np.where(w.shape == 1, max(semi), radius)
     w.density = np.full(n, 1.3)
     if clear:
         # non-overlapping, one lattice unit away from the walls
@@ -133,12 +134,18 @@ def _particles_workload(nx, ny, nz, periodic, voxel, seed, shapes, radius=3.2, c
     return w
 
 
-@pytest.mark.parametrize("voxel", ["subdiv", "distance"])
-def test_voxelize_parity(oracle, voxel):
+@pytest.mark.parametrize("voxel,semi", [("subdiv", (4.5, 2.0, 1.6)), ("subdiv", (6.0, 2.0, 2.0)),
+                                        ("distance", None)])
+def test_voxelize_parity(oracle, voxel, semi):
     """Top-two solid fractions per node. Subdivision counts are bit-exact (both sides use
-    the same FP32 predicate); distance fractions agree to FP32 rounding."""
+    the same FP32 predicate); distance fractions agree to FP32 rounding. The ellipsoids
+    take semi-axes (4.5, 2, 1.6) and the sheared suspension's (6, 2, 2), at random
+    orientations and positions (some across the periodic faces)."""
     shapes = [0] * 10 + ([1] * 6 if voxel == "subdiv" else [])
-    w = _particles_workload(45, 30, 21, (1, 1, 0), voxel, 502, shapes)
+    if semi == (6.0, 2.0, 2.0):
+        w = _particles_workload(54, 40, 26, (1, 1, 0), voxel, 503, shapes, semi=semi)
+    else:
+        w = _particles_workload(45, 30, 21, (1, 1, 0), voxel, 502, shapes)
     o = oracle_from_workload(oracle, w)
     s = gpu_from_workload(w)
     b_o, id_o, ns_o = o.voxelize()

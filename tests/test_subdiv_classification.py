@@ -1,0 +1,222 @@
+"""The kernel's way of counting subdivision samples, restated in numpy FP32 and checked
+against counting every sample with the documented predicate (Sec. 2.4 subdivision,
+evaluated in FP32 with round-to-nearest in a fixed order): along a sample row the squared
+normalised radius is a quadratic in the x offset, and the samples of the row where it is
+below 1 - 1e-3 form an interval (counted by index arithmetic), those where it is above
+1 + 1e-3 lie outside a wider one; only the samples between the two run the predicate.
+The margins are far above the rounding of the set-up and of the predicate (about 1e-5),
+so the counts agree exactly, for spheres and ellipsoids (the sheared suspension's
+(6, 2, 2) and random shapes), at nodes near the surface where the samples straddle it
+and on rows that graze it. The whole-node bounds that spare most nodes a count are
+checked the same way."""
+import numpy as np
+
+f32 = np.float32
+MARGIN = 1e-3
+
+
+def _so(n):
+    return [f32(f32(2 * i + 1 - n) / f32(2 * n)) for i in range(n)]
+
+
+def _pred_ell(mm, dx, dy, dz):
+    t0 = f32(f32(mm[0] * dx) + f32(mm[1] * dy))
+    t1 = f32(f32(mm[3] * dx) + f32(mm[4] * dy))
+    t2 = f32(f32(mm[6] * dx) + f32(mm[7] * dy))
+    q0 = f32(t0 + f32(mm[2] * dz))
+    q1 = f32(t1 + f32(mm[5] * dz))
+    q2 = f32(t2 + f32(mm[8] * dz))
+    return f32(f32(f32(q0 * q0) + f32(q1 * q1)) + f32(q2 * q2)) < f32(1)
+
+
+def _pred_sph(dx, yy, zz, R2):
+    return f32(f32(f32(dx * dx) + yy) + zz) < R2
+
+
+def _count_all(kind, par, px, py, pz, n):
+    """Every one of the n^3 samples through the predicate (the method's definition)."""
+    so = _so(n)
+    c = 0
+    for j in range(n):
+        dy = f32(py + so[j])
+        for q in range(n):
+            dz = f32(pz + so[q])
+            for i in range(n):
+                dx = f32(px + so[i])
+                c += _pred_sph(dx, f32(dy * dy), f32(dz * dz), par) if kind == 0 else _pred_ell(par, dx, dy, dz)
+    return c
+
+
+def _count_intervals(kind, par, px, py, pz, n, stats, dt=f32):
+    """The kernel's count: per sample row (fixed y, z offsets) the interval where the
+    quadratic F(X) = A X^2 + 2 B X + C is below 1 - 1e-3 (shrunk by 2e-4) and the one where
+    it is at most 1 + 1e-3 (grown by 2e-4); samples in the first count, samples outside the
+    second do not, the rest run the predicate. Set up in `dt` arithmetic (the margins make
+    the rounding of the set-up irrelevant)."""
+    so = _so(n)
+    if kind == 0:
+        thr = dt(par)
+        iA = dt(1)
+    else:
+        mm = [dt(v) for v in par]
+        thr = dt(1)
+        A = dt(mm[0] * mm[0] + mm[3] * mm[3] + mm[6] * mm[6])
+        iA = dt(1) / A
+    lo, hi = dt(thr * dt(1 - MARGIN)), dt(thr * dt(1 + MARGIN))
+    fn, t0 = dt(n), dt(0.5 * (n - 1))
+    c = 0
+    for j in range(n):
+        dy = f32(py + so[j])
+        for q in range(n):
+            dz = f32(pz + so[q])
+            xc = dt(0)
+            yy, zz = f32(dy * dy), f32(dz * dz)
+            if kind == 0:
+                Fmin = dt(dt(yy) + dt(zz))
+            else:
+                w = [dt(mm[1] * dt(dy) + mm[2] * dt(dz)), dt(mm[4] * dt(dy) + mm[5] * dt(dz)),
+                     dt(mm[7] * dt(dy) + mm[8] * dt(dz))]
+                B = dt(mm[0] * w[0] + mm[3] * w[1] + mm[6] * w[2])
+                C = dt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2])
+                xc = dt(-B * iA)
+                Fmin = dt(C + B * xc)
+            if Fmin > hi:
+                continue
+            ro = dt(np.sqrt(dt((hi - Fmin) * iA)) * dt(1 + 1e-5) + dt(2e-4))
+            ri = dt(np.sqrt(dt((lo - Fmin) * iA)) * dt(1 - 1e-5) - dt(2e-4)) if Fmin < lo else dt(-1)
+            # bounds as fractional sample indices of a node at offset 0, then of this node
+            cc = dt(xc * fn + t0)
+            qxn = dt(dt(px) * fn)
+            oA = max(0, int(np.ceil(dt(dt(cc - ro * fn) - qxn))))
+            oB = min(n - 1, int(np.floor(dt(dt(cc + ro * fn) - qxn))))
+            band = list(range(oA, oB + 1))
+            if ri > 0:
+                ia = max(0, int(np.ceil(dt(dt(cc - ri * fn) - qxn))))
+                ib = min(n - 1, int(np.floor(dt(dt(cc + ri * fn) - qxn))))
+                if ia <= ib:
+                    c += ib - ia + 1
+                    band = [i for i in band if i < ia or i > ib]
+            for i in band:
+                dx = f32(px + so[i])
+                stats["evaluated"] += 1
+                c += _pred_sph(dx, yy, zz, f32(par)) if kind == 0 else _pred_ell(par, dx, dy, dz)
+    return c
+
+
+def _quick_ellipsoid(mm, px, py, pz, n):
+    """The kernel's whole-node decision for an ellipsoid: with q = M p and w = M^T q, every
+    sample's |M (p + c)|^2 lies within |q|^2 -/+ 2 h |w|_1 (+ G, the box's largest |M c|^2).
+    Returns 0 (no sample inside), 1 (all inside) or None (count)."""
+    M = np.array([[float(mm[3 * j + k]) for k in range(3)] for j in range(3)], dtype=np.float32)
+    h = f32((n - 1) / (2 * n))
+    p = np.array([px, py, pz], dtype=np.float32)
+    q = M @ p
+    s2 = f32(q @ q)
+    w = M.T @ q
+    l1 = f32(2 * h * np.abs(w).sum())
+    G = max(float(np.sum((M.astype(np.float64) @ np.array([1.0, s1, s2_])) ** 2))
+            for s1 in (1, -1) for s2_ in (1, -1)) * float(h) ** 2 * 1.0001
+    slack = 1e-3 + 1e-5 * (s2 + l1)
+    if s2 - l1 > 1 + slack:
+        return 0
+    if s2 + l1 + G < 1 - slack:
+        return 1
+    return None
+
+
+def _ellipsoid_rows(g, semi):
+    """fl32(d_j / semi_j) of a random orientation, row-major (the kernel's M)."""
+    qv = g.normal(size=4)
+    w, x, y, z = qv / np.linalg.norm(qv)
+    Rot = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                    [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                    [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]]).T
+    return [f32(Rot[j][c] / semi[j]) for j in range(3) for c in range(3)]
+
+
+def _surface_nodes(g, count):
+    for t in range(count):
+        if t % 3 == 0:
+            yield 0, None, f32(g.uniform(2.0, 8.0) ** 2)
+        else:
+            semi = np.array([6.0, 2.0, 2.0]) if t % 3 == 1 else g.uniform(0.8, 6.0, 3)
+            yield 1, _ellipsoid_rows(g, semi), None
+
+
+def test_classified_counts_equal_full_enumeration():
+    g = np.random.default_rng(11)
+    stats = {"evaluated": 0}
+    nodes = 0
+    for kind, mm, R2 in _surface_nodes(g, 240):
+        d = g.normal(size=3)
+        d /= np.linalg.norm(d)
+        if kind == 0:
+            s = np.sqrt(float(R2)) + g.uniform(-0.8, 0.8)
+            par = R2
+        else:
+            M = np.array([[float(mm[3 * j + c]) for c in range(3)] for j in range(3)])
+            s = 1.0 / np.linalg.norm(M @ d) + g.uniform(-0.8, 0.8)
+            par = mm
+        px, py, pz = (f32(v) for v in d * s)
+        n = 10 if nodes % 4 else int(g.integers(1, 17))
+        full = _count_all(kind, par, px, py, pz, n)
+        assert _count_intervals(kind, par, px, py, pz, n, stats) == full
+        assert _count_intervals(kind, par, px, py, pz, n, {"evaluated": 0}, dt=np.float64) == full
+        nodes += 1
+    # the predicate ran on a few samples per node instead of n^3
+    assert stats["evaluated"] < 5 * nodes, stats
+
+
+def test_counts_at_tangent_rows():
+    """Samples on the surface to a few FP32 units (a node placed so that one chosen sample
+    sits on it), on rows crossing the surface and on rows that graze it (the sample at the
+    row's closest point): there the set-up's rounding alone would decide wrongly, so these
+    cases fail if the margins are taken out."""
+    g = np.random.default_rng(12)
+    n = 10
+    so = [float(v) for v in _so(n)]
+    for t in range(600):
+        kind = 0 if t % 3 == 0 else 1
+        i, j, q = (int(v) for v in g.integers(0, n, 3))
+        d = g.normal(size=3)
+        if t % 2:
+            d[0] = 0.0   # the surface normal across the row: the row grazes the surface
+        d /= np.linalg.norm(d)
+        if kind == 0:
+            R2 = f32(g.uniform(2.0, 8.0) ** 2)
+            S = d * np.sqrt(float(R2))
+            par = R2
+        else:
+            mm = _ellipsoid_rows(g, np.array([6.0, 2.0, 2.0]) if t % 3 == 1 else g.uniform(0.8, 6.0, 3))
+            M = np.array([[float(mm[3 * a + c]) for c in range(3)] for a in range(3)])
+            if t % 2:
+                # a surface point whose normal M^T M S is across the row (no x component)
+                S = np.linalg.solve(M.T @ M, d)
+                S /= np.linalg.norm(M @ S)
+            else:
+                S = d / np.linalg.norm(M @ d)
+            par = mm
+        S = S * (1.0 + g.uniform(-4e-7, 4e-7))
+        px, py, pz = f32(S[0] - so[i]), f32(S[1] - so[j]), f32(S[2] - so[q])
+        assert _count_intervals(kind, par, px, py, pz, n, {"evaluated": 0}) == _count_all(kind, par, px, py, pz, n)
+
+
+def test_quick_ellipsoid_decisions_are_exact():
+    """Nodes the whole-node bounds decide have no sample inside (0) or every sample inside
+    (1), checked by counting every sample; near the surface the bounds leave the node to
+    the count."""
+    g = np.random.default_rng(13)
+    decided = {0: 0, 1: 0, None: 0}
+    for t in range(300):
+        mm = _ellipsoid_rows(g, np.array([6.0, 2.0, 2.0]) if t % 2 else g.uniform(0.8, 6.0, 3))
+        M = np.array([[float(mm[3 * j + c]) for c in range(3)] for j in range(3)])
+        d = g.normal(size=3)
+        d /= np.linalg.norm(d)
+        s = 1.0 / np.linalg.norm(M @ d) + g.uniform(-2.0, 2.0)
+        px, py, pz = (f32(v) for v in d * s)
+        n = 6
+        r = _quick_ellipsoid(mm, px, py, pz, n)
+        decided[r] += 1
+        if r is not None:
+            assert _count_all(1, mm, px, py, pz, n) == r * n ** 3
+    assert decided[0] > 20 and decided[1] > 10 and decided[None] > 20, decided
