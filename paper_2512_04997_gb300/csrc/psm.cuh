@@ -61,6 +61,8 @@ struct TileCache {
     float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
     float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
     float G[MAX_TILE_CAP];        // ellipsoid: largest |M c|^2 over the subdivision sample box
+    float spx[TILE_Y][32];        // subdivision counts: x offsets of a warp's nodes
+    int scnt[TILE_Y][32];         // subdivision counts: samples decided by the predicate
 };
 
 __device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
@@ -323,12 +325,15 @@ __device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRo
 // margins of a row's intervals (SubRow) are far above the rounding of the set-up and of
 // the predicate (about 1e-5), so a sample in the inner interval is inside by the
 // predicate, one outside the outer is not, and only samples between the two run it. The
-// rows are taken 32 at a time, one per lane; for each needing node every lane counts its
-// row and the warp sums. A last round of fewer rows (W lanes per node, W the power of two
-// at or above its row count) counts 32 / W nodes at once.
-__device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, const TileCache& tc, int e, unsigned need,
+// rows are taken 32 at a time, one per lane. The samples of the needing nodes Lmin..Lmax
+// lie on one grid along x (node L's sample i is the (L - Lmin) n + i-th), so a lane maps
+// its row's intervals onto that grid once, runs the predicate on the few samples between
+// them (adding hits to the node's shared counter), and the warp sums each needing node's
+// overlap with the inner interval. Where the nodes' offsets do not lie on one grid (they
+// would take different periodic images: tiny periodic boxes) each node is counted alone.
+__device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, TileCache& tc, int e, unsigned need,
                                               bool exact, int x, int y, int z, float b) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.subdiv_n, nn = n * n;
     // offsets node - centre: the needing lanes take their own x, two other lanes (when
     // there are two) the row's y and z, so the FP64 work is done once
@@ -357,44 +362,75 @@ __device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, const TileCache&
     const float thr = sph ? tc.R2[e] : 1.0f;
     const float lo = thr * (1.0f - SUBDIV_MARGIN), hi = thr * (1.0f + SUBDIV_MARGIN);
     const float fn = (float)n, t0 = 0.5f * (float)(n - 1);
-    const unsigned mgc = 0xffffffffu / (unsigned)n + 1u;  // jq / n = umulhi(jq, mgc), jq < 256
-    const int kneed = __popc(need);
-    int rank = 0;  // this lane's rank among the needing lanes
-    if ((need >> lane) & 1u) rank = __popc(need & ((1u << lane) - 1u));
+    const unsigned mgc = 0xffffffffu / (unsigned)n + 1u;  // v / n = umulhi(v, mgc) for v < 2^16
+    const bool mine = (need >> lane) & 1u;
+    const int Lmin = __ffs(need) - 1, Lmax = 31 - __clz(need);
+    const float p0 = __shfl_sync(0xffffffffu, px, Lmin);  // x offset of node Lmin
+    const bool grid = __all_sync(0xffffffffu, !mine || fabsf(px - p0 - (float)(lane - Lmin)) < 1e-3f);
+    const float bn = p0 * fn;                  // node Lmin's first sample at grid index 0
+    const int S = (Lmax - Lmin + 1) * n;       // grid samples
     int count = 0;
+    if (grid) {
+        tc.spx[warp][lane] = px;
+        tc.scnt[warp][lane] = 0;
+        __syncwarp();
+    }
     for (int r0 = 0; r0 < nn; r0 += 32) {
-        const int rows = min(32, nn - r0);
-        int W = 32;
-        while (W / 2 >= rows) W /= 2;
-        const int slots = 32 / W, sub = lane & (W - 1), slot = lane / W;
+        const int jq = r0 + lane;
         SubRow rw;
         rw.olo = rw.ilo = 1e4f;
         rw.ohi = rw.ihi = -1e4f;
         rw.dy = rw.dz = rw.yy = rw.zz = 0.0f;
-        if (sub < rows) {
-            const int jq = r0 + sub;
+        if (jq < nn) {
             const int j = (int)__umulhi((unsigned)jq, mgc), q = jq - j * n;
             subdiv_row(tc, sph, mm, iA, lo, hi, py, pz, j, q, fn, t0, rw);
         }
-        // needing nodes in groups of `slots`; slot s of group g takes the (g slots + s)-th
-        for (int g0 = 0; g0 < kneed; g0 += slots) {
-            unsigned m = need;
-            for (int t = 0; t < g0 + slot && m; ++t) m &= m - 1u;
-            const int l = m ? __ffs(m) - 1 : 0;
-            const float qx = __shfl_sync(0xffffffffu, px, l);
-            const int c = (m && sub < rows) ? subdiv_row_count(tc, rw, sph, mm, thr, qx, qx * fn, n) : 0;
-            int sum;
-            if (W == 32) {
-                sum = __reduce_add_sync(0xffffffffu, c);
+        if (grid) {
+            const int oA = max(0, ceil_small(rw.olo - bn)), oB = min(S - 1, floor_small(rw.ohi - bn));
+            int gA = max(0, ceil_small(rw.ilo - bn)), gB = min(S - 1, floor_small(rw.ihi - bn));
+            int e1 = oB + 1, s2 = oB + 1;  // predicate on [oA, e1) and [s2, oB]
+            if (gA <= gB) {
+                e1 = gA;
+                s2 = gB + 1;
             } else {
-                sum = c;
-                for (int o = W / 2; o >= 1; o /= 2) sum += __shfl_xor_sync(0xffffffffu, sum, o, W);
+                gA = 0;
+                gB = -1;
             }
-            // the node of rank k reads its slot's sum
-            const bool mine = ((need >> lane) & 1u) && rank >= g0 && rank < g0 + slots;
-            const int got = __shfl_sync(0xffffffffu, sum, mine ? (rank - g0) * W : 0);
-            if (mine) count += got;
+            for (int g = oA; g <= oB; ++g) {
+                if (g == e1) g = s2;
+                if (g > oB) break;
+                const int k = (int)__umulhi((unsigned)g, mgc), L = Lmin + k;
+                if ((need >> L) & 1u) {
+                    const float dx = __fadd_rn(tc.spx[warp][L], tc.so[g - k * n]);
+                    if (sph ? subdiv_pred_sphere(dx, rw.yy, rw.zz, thr) : subdiv_pred_ell(mm, dx, rw.dy, rw.dz))
+                        atomicAdd(&tc.scnt[warp][L], 1);
+                }
+            }
+            unsigned todo = need;
+            while (todo) {
+                const int L = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const int w0 = (L - Lmin) * n;
+                const int ov = max(0, min(gB, w0 + n - 1) - max(gA, w0) + 1);
+                const int sum = __reduce_add_sync(0xffffffffu, ov);
+                if (lane == L) count += sum;
+            }
+        } else {
+            unsigned todo = need;
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const float qx = __shfl_sync(0xffffffffu, px, l);
+                const int c = jq < nn ? subdiv_row_count(tc, rw, sph, mm, thr, qx, qx * fn, n) : 0;
+                const int sum = __reduce_add_sync(0xffffffffu, c);
+                if (lane == l) count += sum;
+            }
         }
+    }
+    if (grid) {
+        __syncwarp();
+        count += tc.scnt[warp][lane];
+        __syncwarp();  // the counters are reused by this warp's next call
     }
     return exact ? (float)count / (float)(n * n * n) : b;
 }
@@ -405,7 +441,7 @@ __device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, const TileCache&
 // needs a periodic wrap (known at compile time: the subdivision, ellipsoid and wrap code
 // is left out).
 template <bool SPHD>
-__device__ __forceinline__ void node_solids(const LbmArgs& a, const TileCache& tc,
+__device__ __forceinline__ void node_solids(const LbmArgs& a, TileCache& tc,
                                             unsigned long long mask, int lx, int ly, int lz, int x,
                                             int y, int z, bool valid, Two& t) {
     t.ns = 0;

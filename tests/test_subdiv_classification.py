@@ -8,7 +8,8 @@ The margins are far above the rounding of the set-up and of the predicate (about
 so the counts agree exactly, for spheres and ellipsoids (the sheared suspension's
 (6, 2, 2) and random shapes), at nodes near the surface where the samples straddle it
 and on rows that graze it. The whole-node bounds that spare most nodes a count are
-checked the same way."""
+checked the same way, and so is the kernel's count for a warp's row of nodes at once (the
+needing nodes' samples mapped onto one grid along x)."""
 import numpy as np
 
 f32 = np.float32
@@ -220,3 +221,100 @@ def test_quick_ellipsoid_decisions_are_exact():
         if r is not None:
             assert _count_all(1, mm, px, py, pz, n) == r * n ** 3
     assert decided[0] > 20 and decided[1] > 10 and decided[None] > 20, decided
+
+
+def _row_setup(kind, par, py, pz, j, q, n, dt=f32):
+    """Per-row set-up shared by a warp's nodes: the intervals as fractional sample indices
+    of a node at x offset 0 (None when the row cannot reach inside)."""
+    so = _so(n)
+    dy, dz = f32(py + so[j]), f32(pz + so[q])
+    yy, zz = f32(dy * dy), f32(dz * dz)
+    fn, t0 = dt(n), dt(0.5 * (n - 1))
+    if kind == 0:
+        thr, iA, xc = dt(par), dt(1), dt(0)
+        Fmin = dt(dt(yy) + dt(zz))
+    else:
+        mm = [dt(v) for v in par]
+        thr = dt(1)
+        iA = dt(1) / dt(mm[0] * mm[0] + mm[3] * mm[3] + mm[6] * mm[6])
+        w = [dt(mm[1] * dt(dy) + mm[2] * dt(dz)), dt(mm[4] * dt(dy) + mm[5] * dt(dz)),
+             dt(mm[7] * dt(dy) + mm[8] * dt(dz))]
+        B = dt(mm[0] * w[0] + mm[3] * w[1] + mm[6] * w[2])
+        C = dt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2])
+        xc = dt(-B * iA)
+        Fmin = dt(C + B * xc)
+    lo, hi = dt(thr * dt(1 - MARGIN)), dt(thr * dt(1 + MARGIN))
+    if Fmin > hi:
+        return None
+    ro = dt(np.sqrt(dt((hi - Fmin) * iA)) * dt(1 + 1e-5) + dt(2e-4))
+    ri = dt(np.sqrt(dt((lo - Fmin) * iA)) * dt(1 - 1e-5) - dt(2e-4)) if Fmin < lo else dt(-1)
+    cc = dt(xc * fn + t0)
+    inner = (dt(cc - ri * fn), dt(cc + ri * fn)) if ri > 0 else None
+    return dict(outer=(dt(cc - ro * fn), dt(cc + ro * fn)), inner=inner, dy=dy, dz=dz, yy=yy, zz=zz)
+
+
+def _count_row_of_nodes(kind, par, px, need, py, pz, n):
+    """The kernel's count for the needing nodes of one x-row: node L's sample i is grid
+    sample (L - Lmin) n + i; each sample row's intervals are mapped onto the grid once, the
+    samples between them run the predicate, the inner interval's overlap with each node's
+    n grid samples is its count."""
+    so = _so(n)
+    L0, L1 = min(need), max(need)
+    bn = f32(px[L0] * f32(n))
+    S = (L1 - L0 + 1) * n
+    cnt = {L: 0 for L in need}
+    for j in range(n):
+        for q in range(n):
+            r = _row_setup(kind, par, py, pz, j, q, n)
+            if r is None:
+                continue
+            oA = max(0, int(np.ceil(f32(r["outer"][0] - bn))))
+            oB = min(S - 1, int(np.floor(f32(r["outer"][1] - bn))))
+            gA, gB = 0, -1
+            if r["inner"] is not None:
+                gA = max(0, int(np.ceil(f32(r["inner"][0] - bn))))
+                gB = min(S - 1, int(np.floor(f32(r["inner"][1] - bn))))
+            for g in range(oA, oB + 1):
+                if gA <= g <= gB:
+                    continue
+                L, i = L0 + g // n, g % n
+                if L in cnt:
+                    dx = f32(px[L] + so[i])
+                    cnt[L] += _pred_sph(dx, r["yy"], r["zz"], f32(par)) if kind == 0 else \
+                        _pred_ell(par, dx, r["dy"], r["dz"])
+            for L in cnt:
+                w0 = (L - L0) * n
+                cnt[L] += max(0, min(gB, w0 + n - 1) - max(gA, w0) + 1)
+    return cnt
+
+
+def test_row_of_nodes_on_one_grid():
+    """x-rows of 32 nodes (FP64 centre, offsets rounded to FP32 as the kernel does) through
+    spheres and ellipsoids, the nodes whose samples straddle the surface counted at once:
+    every count equals full enumeration."""
+    g = np.random.default_rng(14)
+    n = 10
+    rows = 0
+    for t in range(36):
+        kind = 0 if t % 3 == 0 else 1
+        if kind == 0:
+            par = f32(g.uniform(2.0, 7.0) ** 2)
+            reach = float(np.sqrt(float(par)))
+        else:
+            semi = np.array([6.0, 2.0, 2.0]) if t % 3 == 1 else g.uniform(0.8, 6.0, 3)
+            par = _ellipsoid_rows(g, semi)
+            reach = float(max(semi))
+        p = np.array([g.uniform(100.0, 300.0), g.uniform(0.0, 200.0), g.uniform(0.0, 100.0)])
+        x0 = int(np.floor(p[0])) - 16
+        y = int(np.floor(p[1] + g.uniform(-0.8, 0.8) * reach))
+        z = int(np.floor(p[2] + g.uniform(-0.8, 0.8) * reach))
+        px = [f32(float(x0 + L) - p[0]) for L in range(32)]
+        py, pz = f32(float(y) - p[1]), f32(float(z) - p[2])
+        full = [_count_all(kind, par, px[L], py, pz, n) for L in range(32)]
+        need = [L for L in range(32) if 0 < full[L] < n ** 3]
+        if not need:
+            continue
+        got = _count_row_of_nodes(kind, par, px, need, py, pz, n)
+        assert all(got[L] == full[L] for L in need), (t, [(L, got[L], full[L]) for L in need])
+        rows += 1
+    assert rows > 20
