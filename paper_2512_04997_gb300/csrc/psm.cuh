@@ -63,7 +63,6 @@ struct TileCache {
     float G[MAX_TILE_CAP];        // ellipsoid: largest |M c|^2 over the subdivision sample box
     float spx[TILE_Y][32];        // subdivision counts: x offsets of a warp's nodes
     int scnt[TILE_Y][32];         // subdivision counts: samples decided by the predicate
-    int srow[TILE_Y][32];         // subdivision counts: first row and first z index per y index
 };
 
 __device__ __forceinline__ int tc_pid(const TileCache& tc, int e) { return __float_as_int(tc.spin[e].w); }
@@ -247,66 +246,40 @@ __device__ __forceinline__ int ceil_small(float v) {
     return __float_as_int(__fadd_ru(v, 12582912.0f)) - 0x4B400000;
 }
 
-// The squared normalised radius of a sample at offsets (X, dy, dz) from the centre,
-// |M (X, dy, dz)|^2 = A X^2 + 2 X (b1 dy + b2 dz) + C(dy, dz) (spheres: X^2 + dy^2 + dz^2
-// against R^2). Along a sample row (fixed dy, dz) it is smallest at xc = x1 dy + x2 dz,
-// where it is Fmin = f11 dy^2 + 2 f12 dy dz + f22 dz^2 (the Schur complement of M^T M).
-struct SubQuad {
-    float iA, x1, x2, f11, f12, f22, if22;
-};
-
-__device__ __forceinline__ SubQuad subdiv_quad(const float (&mm)[9]) {
-    SubQuad Q;
-    float m[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) m[k][c] = mm[3 * k + c];
-    const float A = m[0][0] * m[0][0] + m[1][0] * m[1][0] + m[2][0] * m[2][0];
-    const float b1 = m[0][0] * m[0][1] + m[1][0] * m[1][1] + m[2][0] * m[2][1];
-    const float b2 = m[0][0] * m[0][2] + m[1][0] * m[1][2] + m[2][0] * m[2][2];
-    const float c11 = m[0][1] * m[0][1] + m[1][1] * m[1][1] + m[2][1] * m[2][1];
-    const float c12 = m[0][1] * m[0][2] + m[1][1] * m[1][2] + m[2][1] * m[2][2];
-    const float c22 = m[0][2] * m[0][2] + m[1][2] * m[1][2] + m[2][2] * m[2][2];
-    Q.iA = 1.0f / A;
-    Q.x1 = -b1 * Q.iA;
-    Q.x2 = -b2 * Q.iA;
-    Q.f11 = c11 + b1 * Q.x1;
-    Q.f12 = c12 + b1 * Q.x2;
-    Q.f22 = c22 + b2 * Q.x2;
-    Q.if22 = 1.0f / Q.f22;
-    return Q;
-}
-
-// One sample row (fixed y and z offsets dy, dz) of the subdivision count: the interval
-// around xc where the squared normalised radius is below 1 - 1e-3, shrunk by 2e-4, and the
-// one where it is at most 1 + 1e-3, grown by 2e-4 (1 replaced by R^2 for spheres), as
-// fractional sample indices of a node at x offset 0 (sample i of a node at offset qx sits
-// at X = qx + (i - (n - 1)/2)/n).
+// One sample row (fixed y and z offsets dy, dz) of the subdivision count. Along it the
+// squared normalised radius is the quadratic F(X) = A X^2 + 2 B X + C of the x offset X,
+// smallest (Fmin) at xc = -B/A (spheres: X^2 + dy^2 + dz^2 against R^2). The row keeps the
+// interval around xc where F < 1 - 1e-3, shrunk by 2e-4, and the one where F <= 1 + 1e-3,
+// grown by 2e-4, as fractional sample indices of a node at x offset 0 (sample i of a node
+// at offset qx sits at X = qx + (i - (n - 1)/2)/n).
 struct SubRow {
     float ilo, ihi, olo, ohi;  // inner and outer interval (empty: lo > hi)
     float dy, dz, yy, zz;
 };
 
-template <bool SPH>
-__device__ __forceinline__ void subdiv_row(const TileCache& tc, const SubQuad& Q, float lo, float hi, float py,
-                                           float pz, int j, int q, float fn, float t0, SubRow& r) {
+__device__ __forceinline__ void subdiv_row(const TileCache& tc, bool sph, const float (&mm)[9], float iA,
+                                           float lo, float hi, float py, float pz, int j, int q, float fn,
+                                           float t0, SubRow& r) {
     r.dy = __fadd_rn(py, tc.so[j]);
     r.dz = __fadd_rn(pz, tc.so[q]);
+    r.yy = __fmul_rn(r.dy, r.dy);
+    r.zz = __fmul_rn(r.dz, r.dz);
     float xc = 0.0f, Fmin;
-    if constexpr (SPH) {
-        r.yy = __fmul_rn(r.dy, r.dy);
-        r.zz = __fmul_rn(r.dz, r.dz);
+    if (sph) {
         Fmin = r.yy + r.zz;
     } else {
-        xc = Q.x1 * r.dy + Q.x2 * r.dz;
-        Fmin = r.dy * (Q.f11 * r.dy + 2.0f * Q.f12 * r.dz) + Q.f22 * r.dz * r.dz;
+        const float w0 = mm[1] * r.dy + mm[2] * r.dz, w1 = mm[4] * r.dy + mm[5] * r.dz,
+                    w2 = mm[7] * r.dy + mm[8] * r.dz;
+        const float B = mm[0] * w0 + mm[3] * w1 + mm[6] * w2;
+        const float C = w0 * w0 + w1 * w1 + w2 * w2;
+        xc = -B * iA;
+        Fmin = C + B * xc;
     }
     r.olo = r.ilo = 1e4f;
     r.ohi = r.ihi = -1e4f;
     if (Fmin <= hi) {
         // square roots to about 1e-7 relative (the slack is 1e-5 relative plus 2e-4)
-        const float vo = fmaxf((hi - Fmin) * Q.iA, 1e-30f), vi = fmaxf((lo - Fmin) * Q.iA, 1e-30f);
+        const float vo = fmaxf((hi - Fmin) * iA, 1e-30f), vi = fmaxf((lo - Fmin) * iA, 1e-30f);
         const float ro = vo * rsqrtf(vo) * (1.0f + 1e-5f) + 2e-4f;
         const float c = xc * fn + t0;
         r.olo = c - ro * fn;
@@ -323,9 +296,9 @@ __device__ __forceinline__ void subdiv_row(const TileCache& tc, const SubQuad& Q
 
 // Samples of row r inside the solid for the node at x offset qx (qxn = qx n): those in the
 // inner interval by index arithmetic, the FP32 predicate for those between the intervals.
-template <bool SPH>
-__device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRow& r, const float (&mm)[9],
-                                                float thr, float qx, float qxn, int n) {
+__device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRow& r, bool sph,
+                                                const float (&mm)[9], float thr, float qx, float qxn,
+                                                int n) {
     const int oA = max(0, ceil_small(r.olo - qxn)), oB = min(n - 1, floor_small(r.ohi - qxn));
     const int iA = max(0, ceil_small(r.ilo - qxn)), iB = min(n - 1, floor_small(r.ihi - qxn));
     int c = 0, e1 = oB + 1, s2 = oB + 1;  // predicate on [oA, e1) and [s2, oB]
@@ -334,12 +307,13 @@ __device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRo
         e1 = iA;
         s2 = iB + 1;
     }
-    for (int i = oA; i <= oB; ++i) {
-        if (i == e1) i = s2;
-        if (i > oB) break;
+    for (int i = oA; i < e1; ++i) {
         const float dx = __fadd_rn(qx, tc.so[i]);
-        if constexpr (SPH) c += subdiv_pred_sphere(dx, r.yy, r.zz, thr);
-        else c += subdiv_pred_ell(mm, dx, r.dy, r.dz);
+        c += sph ? subdiv_pred_sphere(dx, r.yy, r.zz, thr) : subdiv_pred_ell(mm, dx, r.dy, r.dz);
+    }
+    for (int i = s2; i <= oB; ++i) {
+        const float dx = __fadd_rn(qx, tc.so[i]);
+        c += sph ? subdiv_pred_sphere(dx, r.yy, r.zz, thr) : subdiv_pred_ell(mm, dx, r.dy, r.dz);
     }
     return c;
 }
@@ -347,90 +321,69 @@ __device__ __forceinline__ int subdiv_row_count(const TileCache& tc, const SubRo
 // Exact subdivision counts (Sec. 2.4) for the lanes in `need`: n^3 samples at offsets
 // (2m+1-n)/(2n) around each node, a sample counting when the FP32 predicate puts it
 // inside. The nodes of a warp lie on one x-row, so their y and z offsets from the centre
-// (px per lane; py, pz: FP64 minimum image, rounded to FP32) are the same and so are the
-// n^2 sample rows. Only rows whose smallest squared radius can be within 2e-3 of the
-// surface are taken (for each y offset the z range from the quadratic Fmin, one index
-// wider on each side; the others have no sample inside), 32 at a time, one per lane. The
+// (FP64 minimum image, rounded to FP32) are the same and so are the n^2 sample rows: the
 // margins of a row's intervals (SubRow) are far above the rounding of the set-up and of
 // the predicate (about 1e-5), so a sample in the inner interval is inside by the
 // predicate, one outside the outer is not, and only samples between the two run it. The
-// samples of the needing nodes Lmin..Lmax lie on one grid along x (node L's sample i is
-// the (L - Lmin) n + i-th), so a lane maps its row's intervals onto that grid once, runs
-// the predicate on the few samples between them (adding hits to the node's shared
-// counter), and the warp sums each needing node's overlap with the inner interval. Where
-// the nodes' offsets do not lie on one grid (they would take different periodic images:
-// tiny periodic boxes) each node is counted alone.
-template <bool SPH>
-__device__ __forceinline__ int subdiv_counts(const LbmArgs& a, TileCache& tc, int e, unsigned need, float px,
-                                             float py, float pz) {
+// rows are taken 32 at a time, one per lane. The samples of the needing nodes Lmin..Lmax
+// lie on one grid along x (node L's sample i is the (L - Lmin) n + i-th), so a lane maps
+// its row's intervals onto that grid once, runs the predicate on the few samples between
+// them (adding hits to the node's shared counter), and the warp sums each needing node's
+// overlap with the inner interval. Where the nodes' offsets do not lie on one grid (they
+// would take different periodic images: tiny periodic boxes) each node is counted alone.
+__device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, TileCache& tc, int e, unsigned need,
+                                              bool exact, int x, int y, int z, float b) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = a.subdiv_n;
-    float mm[9];
-    SubQuad Q;
-    float thr;
-    if constexpr (SPH) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) mm[k] = 0.0f;
-        Q = SubQuad{1.0f, 0.0f, 0.0f, 1.0f, 0.0f, 1.0f, 1.0f};
-        thr = tc.R2[e];
+    const int n = a.subdiv_n, nn = n * n;
+    // offsets node - centre: the needing lanes take their own x, two other lanes (when
+    // there are two) the row's y and z, so the FP64 work is done once
+    float px, py, pz;
+    const unsigned spare = ~need;
+    if (__popc(spare) >= 2) {
+        const int ly = __ffs(spare) - 1;
+        const int lz = __ffs(spare & (spare - 1)) - 1;
+        const int ax = lane == ly ? 1 : (lane == lz ? 2 : 0);
+        const int cc = ax == 0 ? x : (ax == 1 ? y : z);
+        const double L = ax == 0 ? (double)a.nx : (ax == 1 ? (double)a.ny : (double)a.nz);
+        const float v = __double2float_rn(min_image_d((double)cc - tc.p[ax][e], a.per[ax], L));
+        px = v;
+        py = __shfl_sync(0xffffffffu, v, ly);
+        pz = __shfl_sync(0xffffffffu, v, lz);
     } else {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) mm[k] = tc.m[k][e];
-        Q = subdiv_quad(mm);
-        thr = 1.0f;
+        px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
+        py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
+        pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
     }
+    const bool sph = tc.shape[e] == LEDDS_SPHERE;
+    float mm[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) mm[k] = sph ? 0.0f : tc.m[k][e];
+    const float iA = sph ? 1.0f : __frcp_rn(mm[0] * mm[0] + mm[3] * mm[3] + mm[6] * mm[6]);
+    const float thr = sph ? tc.R2[e] : 1.0f;
     const float lo = thr * (1.0f - SUBDIV_MARGIN), hi = thr * (1.0f + SUBDIV_MARGIN);
     const float fn = (float)n, t0 = 0.5f * (float)(n - 1);
-    // rows per y offset j (lane j): the z range where Fmin <= thr (1 + 2e-3)
-    int qa = 0, nq = 0;
-    if (lane < n) {
-        const float dy = __fadd_rn(py, tc.so[lane]);
-        const float bq = Q.f12 * dy, cq = Q.f11 * dy * dy - thr * (1.0f + 2.0f * SUBDIV_MARGIN);
-        const float disc = bq * bq - Q.f22 * cq;
-        if (disc >= 0.0f) {
-            const float sd = sqrtf(disc);
-            const float zl = (-bq - sd) * Q.if22, zh = (-bq + sd) * Q.if22;
-            qa = max(0, floor_small((zl - pz) * fn + t0) - 1);
-            const int qb = min(n - 1, ceil_small((zh - pz) * fn + t0) + 1);
-            nq = max(0, qb - qa + 1);
-        }
-    }
-    int start = nq;  // inclusive scan over j, then exclusive
-#pragma unroll
-    for (int o = 1; o < 16; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, start, o);
-        if (lane >= o) start += v;
-    }
-    const int R = __shfl_sync(0xffffffffu, start, 15);
-    start -= nq;
+    const unsigned mgc = 0xffffffffu / (unsigned)n + 1u;  // v / n = umulhi(v, mgc) for v < 2^16
     const bool mine = (need >> lane) & 1u;
     const int Lmin = __ffs(need) - 1, Lmax = 31 - __clz(need);
     const float p0 = __shfl_sync(0xffffffffu, px, Lmin);  // x offset of node Lmin
     const bool grid = __all_sync(0xffffffffu, !mine || fabsf(px - p0 - (float)(lane - Lmin)) < 1e-3f);
     const float bn = p0 * fn;                  // node Lmin's first sample at grid index 0
     const int S = (Lmax - Lmin + 1) * n;       // grid samples
-    const unsigned mgc = 0xffffffffu / (unsigned)n + 1u;  // v / n = umulhi(v, mgc) for v < 2^16
-    if (lane < 16) {
-        tc.srow[warp][lane] = lane < n ? start : R;
-        tc.srow[warp][16 + lane] = qa;
-    }
-    tc.spx[warp][lane] = px;
-    tc.scnt[warp][lane] = 0;
-    __syncwarp();
     int count = 0;
-    for (int r0 = 0; r0 < R; r0 += 32) {
-        const int rr = r0 + lane;
+    if (grid) {
+        tc.spx[warp][lane] = px;
+        tc.scnt[warp][lane] = 0;
+        __syncwarp();
+    }
+    for (int r0 = 0; r0 < nn; r0 += 32) {
+        const int jq = r0 + lane;
         SubRow rw;
         rw.olo = rw.ilo = 1e4f;
         rw.ohi = rw.ihi = -1e4f;
         rw.dy = rw.dz = rw.yy = rw.zz = 0.0f;
-        if (rr < R) {
-            int j = 0;  // the last y offset whose rows start at or before rr
-#pragma unroll
-            for (int st = 8; st >= 1; st >>= 1)
-                if (j + st < n && tc.srow[warp][j + st] <= rr) j += st;
-            const int q = tc.srow[warp][16 + j] + rr - tc.srow[warp][j];
-            subdiv_row<SPH>(tc, Q, lo, hi, py, pz, j, q, fn, t0, rw);
+        if (jq < nn) {
+            const int j = (int)__umulhi((unsigned)jq, mgc), q = jq - j * n;
+            subdiv_row(tc, sph, mm, iA, lo, hi, py, pz, j, q, fn, t0, rw);
         }
         if (grid) {
             const int oA = max(0, ceil_small(rw.olo - bn)), oB = min(S - 1, floor_small(rw.ohi - bn));
@@ -449,10 +402,8 @@ __device__ __forceinline__ int subdiv_counts(const LbmArgs& a, TileCache& tc, in
                 const int k = (int)__umulhi((unsigned)g, mgc), L = Lmin + k;
                 if ((need >> L) & 1u) {
                     const float dx = __fadd_rn(tc.spx[warp][L], tc.so[g - k * n]);
-                    bool in;
-                    if constexpr (SPH) in = subdiv_pred_sphere(dx, rw.yy, rw.zz, thr);
-                    else in = subdiv_pred_ell(mm, dx, rw.dy, rw.dz);
-                    if (in) atomicAdd(&tc.scnt[warp][L], 1);
+                    if (sph ? subdiv_pred_sphere(dx, rw.yy, rw.zz, thr) : subdiv_pred_ell(mm, dx, rw.dy, rw.dz))
+                        atomicAdd(&tc.scnt[warp][L], 1);
                 }
             }
             unsigned todo = need;
@@ -470,45 +421,18 @@ __device__ __forceinline__ int subdiv_counts(const LbmArgs& a, TileCache& tc, in
                 const int l = __ffs(todo) - 1;
                 todo &= todo - 1u;
                 const float qx = __shfl_sync(0xffffffffu, px, l);
-                const int c = rr < R ? subdiv_row_count<SPH>(tc, rw, mm, thr, qx, qx * fn, n) : 0;
+                const int c = jq < nn ? subdiv_row_count(tc, rw, sph, mm, thr, qx, qx * fn, n) : 0;
                 const int sum = __reduce_add_sync(0xffffffffu, c);
                 if (lane == l) count += sum;
             }
         }
     }
-    __syncwarp();
-    count += tc.scnt[warp][lane];
-    __syncwarp();  // the shared rows and counters are reused by this warp's next call
-    return count;
-}
-
-// Subdivision fractions for the lanes in `need` (see subdiv_counts); the others keep b.
-// The offsets node - centre: the needing lanes take their own x, two other lanes (when
-// there are two) the row's y and z, so the FP64 work is done once.
-__device__ __forceinline__ float subdiv_lanes(const LbmArgs& a, TileCache& tc, int e, unsigned need,
-                                              bool exact, int x, int y, int z, float b) {
-    const int lane = threadIdx.x & 31;
-    float px, py, pz;
-    const unsigned spare = ~need;
-    if (__popc(spare) >= 2) {
-        const int ly = __ffs(spare) - 1;
-        const int lz = __ffs(spare & (spare - 1)) - 1;
-        const int ax = lane == ly ? 1 : (lane == lz ? 2 : 0);
-        const int cc = ax == 0 ? x : (ax == 1 ? y : z);
-        const double L = ax == 0 ? (double)a.nx : (ax == 1 ? (double)a.ny : (double)a.nz);
-        const float v = __double2float_rn(min_image_d((double)cc - tc.p[ax][e], a.per[ax], L));
-        px = v;
-        py = __shfl_sync(0xffffffffu, v, ly);
-        pz = __shfl_sync(0xffffffffu, v, lz);
-    } else {
-        px = __double2float_rn(min_image_d((double)x - tc.p[0][e], a.per[0], (double)a.nx));
-        py = __double2float_rn(min_image_d((double)y - tc.p[1][e], a.per[1], (double)a.ny));
-        pz = __double2float_rn(min_image_d((double)z - tc.p[2][e], a.per[2], (double)a.nz));
+    if (grid) {
+        __syncwarp();
+        count += tc.scnt[warp][lane];
+        __syncwarp();  // the counters are reused by this warp's next call
     }
-    const int n = a.subdiv_n;
-    const int c = tc.shape[e] == LEDDS_SPHERE ? subdiv_counts<true>(a, tc, e, need, px, py, pz)
-                                              : subdiv_counts<false>(a, tc, e, need, px, py, pz);
-    return exact ? (float)c / (float)(n * n * n) : b;
+    return exact ? (float)count / (float)(n * n * n) : b;
 }
 
 // Called by the whole warp (the row mask is uniform); lanes with valid false take no part

@@ -253,43 +253,12 @@ def _row_setup(kind, par, py, pz, j, q, n, dt=f32):
     return dict(outer=(dt(cc - ro * fn), dt(cc + ro * fn)), inner=inner, dy=dy, dz=dz, yy=yy, zz=zz)
 
 
-def _shadow_rows(kind, par, py, pz, n):
-    """The rows the kernel sets up: for each y index j the z range where the row minimum
-    Fmin(dy, dz) = f11 dy^2 + 2 f12 dy dz + f22 dz^2 (the Schur complement of M^T M) is at
-    most 1 + 2e-3 (R^2 (1 + 2e-3) for spheres), one index wider on each side."""
-    so = _so(n)
-    fn, t0 = f32(n), f32(0.5 * (n - 1))
-    if kind == 0:
-        f11, f12, f22, thr = f32(1), f32(0), f32(1), f32(par)
-    else:
-        m = np.array([[f32(par[3 * k + c]) for c in range(3)] for k in range(3)], dtype=np.float32)
-        Q = m.T @ m
-        iA = f32(1) / Q[0, 0]
-        x1, x2 = f32(-Q[0, 1] * iA), f32(-Q[0, 2] * iA)
-        f11, f12, f22 = f32(Q[1, 1] + Q[0, 1] * x1), f32(Q[1, 2] + Q[0, 1] * x2), f32(Q[2, 2] + Q[0, 2] * x2)
-        thr = f32(1)
-    rows = set()
-    for j in range(n):
-        dy = f32(py + so[j])
-        bq, cq = f32(f12 * dy), f32(f11 * dy * dy - thr * f32(1 + 2 * MARGIN))
-        disc = f32(bq * bq - f22 * cq)
-        if disc < 0:
-            continue
-        sd = f32(np.sqrt(disc))
-        zl, zh = f32((-bq - sd) / f22), f32((-bq + sd) / f22)
-        qa = max(0, int(np.floor(f32(f32(zl - pz) * fn + t0))) - 1)
-        qb = min(n - 1, int(np.ceil(f32(f32(zh - pz) * fn + t0))) + 1)
-        rows.update((j, q) for q in range(qa, qb + 1))
-    return rows
-
-
 def _count_row_of_nodes(kind, par, px, need, py, pz, n):
-    """The kernel's count for the needing nodes of one x-row: only the rows within the
-    shadow are set up; node L's sample i is grid sample (L - Lmin) n + i; each row's
-    intervals are mapped onto the grid once, the samples between them run the predicate,
-    the inner interval's overlap with each node's n grid samples is its count."""
+    """The kernel's count for the needing nodes of one x-row: node L's sample i is grid
+    sample (L - Lmin) n + i; each sample row's intervals are mapped onto the grid once, the
+    samples between them run the predicate, the inner interval's overlap with each node's
+    n grid samples is its count."""
     so = _so(n)
-    shadow = _shadow_rows(kind, par, py, pz, n)
     L0, L1 = min(need), max(need)
     bn = f32(px[L0] * f32(n))
     S = (L1 - L0 + 1) * n
@@ -299,7 +268,6 @@ def _count_row_of_nodes(kind, par, px, need, py, pz, n):
             r = _row_setup(kind, par, py, pz, j, q, n)
             if r is None:
                 continue
-            assert (j, q) in shadow, (j, q)   # a row that reaches the surface is set up
             oA = max(0, int(np.ceil(f32(r["outer"][0] - bn))))
             oB = min(S - 1, int(np.floor(f32(r["outer"][1] - bn))))
             gA, gB = 0, -1
