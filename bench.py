@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ensemble-only", action="store_true",
                     help="time only the batched 64-simulation ensemble (one JSON line)")
+    ap.add_argument("--ellipsoid-only", type=int, default=0, metavar="NX",
+                    help="time only the sheared ellipsoid suspension, shrunk to NX x NX x NX/2 at "
+                         "its particle density (384: the full workload; one JSON line)")
     ap.add_argument("--long", type=int, default=500,
                     help="steps of each of the three runs whose median the line also reports")
     ap.add_argument("--edge", type=int, default=256,
@@ -261,21 +264,25 @@ def granular_measure(device, stream, steps=10000, sample=100):
             "status": {k: st[k] for k in ("cand_overflow", "skin_violation", "nan_detected")}}
 
 
-def ellipsoid_measure(args, device, stream):
+def ellipsoid_measure(args, device, stream, nx=384, storages=("f32", "bf16")):
     """Prolate ellipsoids (semi-axes 6, 2, 2) in shear, 384x384x192, 2e4 particles at
     random orientations, subdivision solid fractions, common-normal contacts, n_sub 10:
     MLUPS with FP32 and BF16 storage on the same workload, BF16 field error against FP32,
-    and the event-timed stage split of each."""
+    and the event-timed stage split of each. nx < 384: the box nx x nx x nx/2 at the same
+    particle density."""
     import torch
     from paper_2512_04997_gb300 import ledds, workloads as W
     t0 = time.perf_counter()
-    w = W.ellipsoid_shear()
+    if nx == 384:
+        w = W.ellipsoid_shear()
+    else:
+        w = W.ellipsoid_shear(nx=nx, ny=nx, nz=nx // 2, n_particles=int(round(20000 * (nx / 384.0) ** 3)))
     gen_s = time.perf_counter() - t0
     out = {"workload": f"{w.name}: semi-axes (6,2,2), random orientations, shear rate 1e-4, "
                        "subdivision fractions, common-normal contacts, n_sub 10",
            "generate_s": gen_s, "cells": w.ncell, "particles": w.n}
     u_ref = None
-    for sto in ("f32", "bf16"):
+    for sto in storages:
         s = ledds.from_workload(w, device=device, storage=sto)
         s.step(args.warmup)
         torch.cuda.synchronize()
@@ -303,7 +310,8 @@ def ellipsoid_measure(args, device, stream):
         s.close()
         del s
         torch.cuda.empty_cache()
-    out["bf16_speedup_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
+    if "bf16" in out and "f32" in out:
+        out["bf16_speedup_vs_f32"] = out["bf16"]["value"] / out["f32"]["value"]
     return out
 
 
@@ -483,6 +491,12 @@ def main():
         ens = ensemble_measure(args, f"cuda:{local}", torch.cuda.current_stream())
         if rank == 0:
             print(json.dumps({"ensemble": ens, "steps": args.steps, "warmup": args.warmup}), flush=True)
+        return
+    if args.ellipsoid_only:
+        ell = ellipsoid_measure(args, f"cuda:{local}", torch.cuda.current_stream(), nx=args.ellipsoid_only,
+                                storages=(args.storage,))
+        if rank == 0:
+            print(json.dumps({"ellipsoid_shear": ell, "steps": args.steps, "warmup": args.warmup}), flush=True)
         return
     w = main_workload(args)
     N = w.ncell
