@@ -23,6 +23,13 @@ __device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_r
 __device__ __forceinline__ float mu(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float ad(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sb(float a, float b) { return __fsub_rn(a, b); }
+// Square root by the hardware approximation (relative error about 2^-23, exact at 0): the
+// distance solid fraction (R + R_c - d) / (2 R_c) needs no correctly rounded root.
+__device__ __forceinline__ float sqrt_apx(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Moving-wall correction 6 t_i (c_i . u_w) (rho_w = 1) for a link that crossed walls;
 // with walls on two axes the wall of the higher axis (z, then y, then x) is used. The
@@ -162,7 +169,7 @@ __device__ __forceinline__ float beta_quick(const LbmArgs& a, const TileCache& t
     *exact = false;
     if (sh == LEDDS_SPHERE && a.voxel == LEDDS_VOXEL_DISTANCE) {
         // Eq. (naiveSolidFrac): (R + R_c - d) / (2 R_c), clamped
-        const float dsc = sb(ad(R, a.Rc), __fsqrt_rn(d2));
+        const float dsc = sb(ad(R, a.Rc), sqrt_apx(d2));
         return fminf(fmaxf(mu(dsc, a.inv2Rc), 0.0f), 1.0f);
     }
     const int n = a.subdiv_n;
@@ -459,7 +466,7 @@ __device__ __forceinline__ void node_solids(const LbmArgs& a, TileCache& tc,
         if constexpr (SPHD) {
             // Eq. (naiveSolidFrac), as in beta_quick
             const float d2 = fm(dz, dz, fm(dy, dy, mu(dx, dx)));
-            const float dsc = sb(ad(ps.w, a.Rc), __fsqrt_rn(d2));
+            const float dsc = sb(ad(ps.w, a.Rc), sqrt_apx(d2));
             b = valid ? fminf(fmaxf(mu(dsc, a.inv2Rc), 0.0f), 1.0f) : 0.0f;
         } else {
             bool exact = false;
@@ -520,7 +527,9 @@ __device__ __forceinline__ void solid_force(const SolidAt& q, float rho, float d
 
 // Warp-aggregated addition of per-lane (key, 6 values) into the tile accumulators: one
 // butterfly per distinct key present in the warp (lanes with key < 0 take no part).
-static __device__ __noinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
+// Inlined in the sphere kernel (no call frame), out of line in the general kernel (whose
+// register budget it would otherwise strain): warp_flush<true> / warp_flush<false>.
+__device__ __forceinline__ void warp_flush_body(TileCache& tc, int key, const float val[6]) {
     const int lane = threadIdx.x & 31;
     unsigned pending = __ballot_sync(FULL, key >= 0);
     while (pending) {
@@ -539,6 +548,14 @@ static __device__ __noinline__ void warp_flush(TileCache& tc, int key, const flo
             for (int c = 0; c < 6; ++c) atomicAdd(&tc.acc[c][kk], v[c]);
         pending &= ~__ballot_sync(FULL, mine);
     }
+}
+static __device__ __noinline__ void warp_flush_call(TileCache& tc, int key, const float val[6]) {
+    warp_flush_body(tc, key, val);
+}
+template <bool INL>
+__device__ __forceinline__ void warp_flush(TileCache& tc, int key, const float val[6]) {
+    if constexpr (INL) warp_flush_body(tc, key, val);
+    else warp_flush_call(tc, key, val);
 }
 
 
@@ -1054,7 +1071,7 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
             // invariant: hacc is zero whenever hkey < 0; a node without solid keeps the
             // held sum (the lane may meet the same particle again further down)
             const bool change = hkey >= 0 && key0 >= 0 && key0 != hkey;
-            if (__any_sync(FULL, change)) warp_flush(tc, change ? hkey : -1, hacc);
+            if (__any_sync(FULL, change)) warp_flush<!MI>(tc, change ? hkey : -1, hacc);
             if (change) {
                 hkey = -1;
 #pragma unroll
@@ -1085,7 +1102,7 @@ __device__ __forceinline__ void psm_node(const LbmArgs& a, TileCache& tc, float 
             m.Z = fm(vz, q.uz, fm(vy, q.uy, fm(vx, q.ux, m.Z)));
             float v1[6];
             solid_force(q, rho, sb(ux, q.ux), sb(uy, q.uy), sb(uz, q.uz), a, v1);
-            warp_flush(tc, t.ns > 1 ? t.e1 : -1, v1);
+            warp_flush<!MI>(tc, t.ns > 1 ? t.e1 : -1, v1);
         }
         m.Btot = fminf(m.Bs, 1.0f);
         node_coef<TRT, true>(a, sc, drho, rho, ux, uy, uz, usq, m, k);
@@ -1178,7 +1195,7 @@ __device__ __forceinline__ void psm_tile_direct(const LbmArgs& a, int bx, int by
         else pull_all<SS, false, MODE>(a, pin, pl, g);
         psm_node<SS, TRT, MODE, !SPHD>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
-    warp_flush(tc, hkey, hacc);
+    warp_flush<SPHD>(tc, hkey, hacc);
     __syncthreads();
     tile_sums_out(a, tc, cnt);
 }
@@ -1280,7 +1297,7 @@ __device__ __forceinline__ void psm_tile_staged(const LbmArgs& a, const PsmMaps&
         const bool wwarp = (face || xend) && __any_sync(FULL, valid && pl.bw != 0u);
         psm_node<SS, TRT, MODE, !SPHD>(a, tc, g, pl, valid, wwarp, t, lane, warp, iz, pout, hkey, hacc);
     }
-    warp_flush(tc, hkey, hacc);
+    warp_flush<SPHD>(tc, hkey, hacc);
     if (tid == 0) {
         // after a timeout: wait (bounded) for the copies still in flight into this CTA's
         // shared memory before the CTA ends
