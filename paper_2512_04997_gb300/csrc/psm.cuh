@@ -68,6 +68,7 @@ struct TileCache {
     float so[16];                 // subdivision sample offsets (2m + 1 - n)/(2n)
     float ims[MAX_TILE_CAP];      // ellipsoid: 1 / smallest semi-axis (norm of the m rows)
     float G[MAX_TILE_CAP];        // ellipsoid: largest |M c|^2 over the subdivision sample box
+    float4 sdw[MAX_TILE_CAP];     // ellipsoid: y-z shadow f11, 2 f12, f22 and its grown bound
     float spx[TILE_Y][32];        // subdivision counts: x offsets of a warp's nodes
     int scnt[TILE_Y][32];         // subdivision counts: samples decided by the predicate
 };
@@ -136,6 +137,26 @@ static __device__ void load_tile(const LbmArgs& a, TileCache& tc, int tile, int 
                 g = fmax(g, v);
             }
             tc.G[e] = (float)(g * h * h * 1.0001);
+            // Shadow on the y-z plane: the smallest |M (X, dy, dz)|^2 over X is the Schur
+            // complement quadratic f11 dy^2 + 2 f12 dy dz + f22 dz^2 of M^T M. A node's
+            // samples lie within h sqrt(2) of the row (ly, lz) in y-z, and the square root
+            // of the quadratic grows by at most 1/smallest semi-axis per unit distance, so a
+            // row whose value is at least (1 + h sqrt(2) / s_min)^2 (with margins) has no
+            // sample inside at any of its nodes.
+            double Q[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    double v = 0.0;
+                    for (int j = 0; j < 3; ++j) v += (double)tc.m[3 * j + r][e] * (double)tc.m[3 * j + c][e];
+                    Q[r][c] = v;
+                }
+            const double f11 = Q[1][1] - Q[0][1] * Q[0][1] / Q[0][0];
+            const double f12 = Q[1][2] - Q[0][1] * Q[0][2] / Q[0][0];
+            const double f22 = Q[2][2] - Q[0][2] * Q[0][2] / Q[0][0];
+            const double grow = 1.0 + (h * 1.41421356237 + 1e-3) / smin + 1e-3;
+            tc.sdw[e] = make_float4((float)f11, (float)(2.0 * f12), (float)f22, (float)(grow * grow * 1.001));
+        } else {
+            tc.sdw[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         for (int c = 0; c < 6; ++c) tc.acc[c][e] = 0.0f;
     }
@@ -225,6 +246,12 @@ __device__ __forceinline__ unsigned long long row_mask(const LbmArgs& a, const T
             float dy = mimg<MI>((float)ly - ps.y, a.mi[1], (float)a.ny);
             float dz = mimg<MI>((float)lz - ps.z, a.mi[2], (float)a.nz);
             hit = dy * dy + dz * dz < tc.vel[e].w;
+            if constexpr (MI) {
+                // an ellipsoid: its shadow on the y-z plane, grown to cover the samples of
+                // the row's nodes (sdw.w 0: not an ellipsoid)
+                const float4 sd = tc.sdw[e];
+                hit = hit && (sd.w == 0.0f || fm(sd.x * dy, dy, fm(sd.y * dy, dz, mu(sd.z * dz, dz))) < sd.w);
+            }
         }
         unsigned b = __ballot_sync(FULL, hit);
         mask |= (unsigned long long)b << base;
