@@ -14,6 +14,7 @@
 // members compute bit-identical forces and tangential histories and the per-particle
 // sums of Table 1 need neither atomics nor a second sort.
 #include <math.h>
+#include <algorithm>
 
 #include "internal.cuh"
 
@@ -1501,13 +1502,14 @@ __global__ void k_integrate(DemArgs A, int in, int out) {
 // The contacts read only buffer `in` and the integration writes buffer `out`, so the
 // CTAs need no ordering among themselves; the launch boundary orders the substeps.
 // do_step = 0 (the last substep) computes the contact sums only.
-constexpr int SUB_WARPS = 32;
+constexpr int SUB_WARPS = 32;  // most warps (particles) per CTA; the launch picks fewer
 static_assert(SUB_WARPS <= 32, "the integration phase gives each particle one lane of warp 0");
 __global__ void __launch_bounds__(32 * SUB_WARPS, 1) k_substep_spheres(DemArgs A, int in, int out, int cb,
                                                                       int do_step) {
     __shared__ double sF[SUB_WARPS][3], sM[SUB_WARPS][3];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int base = blockIdx.x * SUB_WARPS;
+    const int wpc = blockDim.x >> 5;  // particles of this CTA
+    const int base = blockIdx.x * wpc;
     const int k = base + w;
     const double* st = A.P.st[in];
     if (k < A.P.n) {  // uniform across the warp
@@ -1539,7 +1541,7 @@ __global__ void __launch_bounds__(32 * SUB_WARPS, 1) k_substep_spheres(DemArgs A
     if (!do_step) return;  // uniform across the CTA
     __syncthreads();
     const int kk = base + lane;
-    if (w != 0 || lane >= SUB_WARPS || kk >= A.P.n) return;
+    if (w != 0 || lane >= wpc || kk >= A.P.n) return;
     double r[3], v[3], wv[3], d[9], Ft[3], Mt[3], acc[3];
     load_state(A, st, kk, r, v, wv, d);
     for (int a = 0; a < 3; ++a) {
@@ -1808,7 +1810,13 @@ cudaError_t launch_predict_first(const DemArgs& A, cudaStream_t s) {
 cudaError_t launch_substep(const DemArgs& A, int in, int out, int cb, int do_step, int* launches, cudaStream_t s) {
     if (A.P.n <= 0) return cudaSuccess;
     if (!A.pair_once && A.force_f32) {  // spheres only, FP32 contacts: one launch per substep
-        k_substep_spheres<<<nblk(A.P.n, SUB_WARPS), 32 * SUB_WARPS, 0, s>>>(A, in, out, cb, do_step);
+        // particles per CTA: spread over every SM (the contact arithmetic loads the SM's FP64
+        // pipe in proportion to its particles), at most SUB_WARPS
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int wpc = std::min(SUB_WARPS, std::max(1, (A.P.n + nsm - 1) / std::max(nsm, 1)));
+        k_substep_spheres<<<nblk(A.P.n, wpc), 32 * wpc, 0, s>>>(A, in, out, cb, do_step);
         *launches += 1;
         return cudaGetLastError();
     }
