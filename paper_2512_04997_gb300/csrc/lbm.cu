@@ -302,53 +302,69 @@ __global__ void k_read(const LbmArgs a, float* rho_out, float* u_out, float* f_o
 // fraction can reach (node range r +- reach, periodic wrap).
 // ------------------------------------------------------------------------------------
 
+// The tiles (of T nodes) along one axis that the node range [ceil(r - reach),
+// floor(r + reach)] meets, clipped to the lattice or wrapped on a periodic axis: one or two
+// contiguous runs, at most 16 tiles.
 __device__ __forceinline__ int axis_tiles(double r, float reach, int n, int per, int T, int* out) {
     // a particle far outside the lattice (or not finite) reaches no tile
     if (!(r > -2.0 * n && r < 3.0 * n)) return 0;
     int lo = (int)ceil(r - (double)reach);
     int hi = (int)floor(r + (double)reach);
-    int cnt = 0, last = -1;
-    for (int q = lo; q <= hi; ++q) {
-        int qw = q;
-        if (per) {
-            qw %= n;
-            if (qw < 0) qw += n;
-        } else if (q < 0 || q >= n) {
-            continue;
-        }
-        int t = qw / T;
-        if (t != last && cnt < 16) {
-            bool dup = false;
-            for (int m = 0; m < cnt; ++m) dup |= (out[m] == t);
-            if (!dup) out[cnt++] = t;
-            last = t;
+    if (lo > hi) return 0;  // no node within reach
+    const int nt = (n + T - 1) / T;
+    int cnt = 0;
+    auto run = [&](int t0, int t1) {
+        for (int t = t0; t <= t1 && cnt < 16; ++t) out[cnt++] = t;
+    };
+    if (!per) {
+        lo = max(lo, 0);
+        hi = min(hi, n - 1);
+        if (lo <= hi) run(lo / T, hi / T);
+    } else if (hi - lo + 1 >= n) {
+        run(0, nt - 1);
+    } else {
+        int lw = lo % n;
+        if (lw < 0) lw += n;
+        const int hw = lw + (hi - lo);
+        if (hw < n) {
+            run(lw / T, hw / T);
+        } else {
+            const int a0 = lw / T, b1 = (hw - n) / T;  // [a0, nt - 1] and [0, b1]
+            if (b1 >= a0) {
+                run(0, nt - 1);  // the two runs meet: every tile
+            } else {
+                run(a0, nt - 1);
+                run(0, b1);
+            }
         }
     }
     return cnt;
 }
 
+// One warp per particle: the lanes append its id to the tiles' lists in parallel.
 __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;  // uniform across the warp
     double r[3] = {a.st[(SP + 0) * a.pcap + k], a.st[(SP + 1) * a.pcap + k],
                    a.st[(SP + 2) * a.pcap + k]};
     float reach = reach_of(a, a.shape[k], a.radius[k], a.bound[k]);
     if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) {
-        atomicAdd(&a.status->nan_detected, 1);
+        if (lane == 0) atomicAdd(&a.status->nan_detected, 1);
         return;
     }
     int tl[3][16], tc[3];
     tc[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
     tc[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
     tc[2] = axis_tiles(r[2], reach, a.nz, a.per[2], a.tz, tl[2]);
-    for (int c = 0; c < tc[2]; ++c)
-        for (int b = 0; b < tc[1]; ++b)
-            for (int q = 0; q < tc[0]; ++q) {
-                int t = (tl[2][c] * a.nty + tl[1][b]) * a.ntx + tl[0][q];
-                int slot = atomicAdd(&tile_count[t], 1);
-                if (slot < a.tile_cap) tile_ids[(long long)t * a.tile_cap + slot] = k;
-                else atomicAdd(&a.status->tile_overflow, 1);
-            }
+    const int n01 = tc[0] * tc[1], total = n01 * tc[2];
+    for (int m = lane; m < total; m += 32) {
+        const int c = m / n01, rem = m - c * n01, b = rem / tc[0], q = rem - b * tc[0];
+        const int t = (tl[2][c] * a.nty + tl[1][b]) * a.ntx + tl[0][q];
+        const int slot = atomicAdd(&tile_count[t], 1);
+        if (slot < a.tile_cap) tile_ids[(long long)t * a.tile_cap + slot] = k;
+        else atomicAdd(&a.status->tile_overflow, 1);
+    }
 }
 
 
@@ -541,7 +557,7 @@ cudaError_t launch_read(const LbmArgs& a, int store, float* rho, float* u, float
 
 cudaError_t launch_bin(const LbmArgs& a, int n, int* tile_count, int* tile_ids, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    k_bin<<<(n + 127) / 128, 128, 0, s>>>(a, n, tile_count, tile_ids);
+    k_bin<<<(unsigned)(((long long)n * 32 + 127) / 128), 128, 0, s>>>(a, n, tile_count, tile_ids);
     return cudaGetLastError();
 }
 
