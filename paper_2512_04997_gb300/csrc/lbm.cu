@@ -304,41 +304,60 @@ __global__ void k_read(const LbmArgs a, float* rho_out, float* u_out, float* f_o
 
 // The tiles (of T nodes) along one axis that the node range [ceil(r - reach),
 // floor(r + reach)] meets, clipped to the lattice or wrapped on a periodic axis: one or two
-// contiguous runs, at most 16 tiles.
-__device__ __forceinline__ int axis_tiles(double r, float reach, int n, int per, int T, int* out) {
+// contiguous runs s0 .. s0 + n0 - 1 and s1 .. s1 + n1 - 1, at most 16 tiles in all.
+struct AxisRuns {
+    int s0, n0, s1, n1;
+    __device__ int count() const { return n0 + n1; }
+    __device__ int tile(int m) const { return m < n0 ? s0 + m : s1 + (m - n0); }
+};
+
+__device__ __forceinline__ AxisRuns axis_runs(double r, float reach, int n, int per, int T) {
+    AxisRuns R{0, 0, 0, 0};
     // a particle far outside the lattice (or not finite) reaches no tile
-    if (!(r > -2.0 * n && r < 3.0 * n)) return 0;
+    if (!(r > -2.0 * n && r < 3.0 * n)) return R;
     int lo = (int)ceil(r - (double)reach);
     int hi = (int)floor(r + (double)reach);
-    if (lo > hi) return 0;  // no node within reach
+    if (lo > hi) return R;  // no node within reach
     const int nt = (n + T - 1) / T;
-    int cnt = 0;
-    auto run = [&](int t0, int t1) {
-        for (int t = t0; t <= t1 && cnt < 16; ++t) out[cnt++] = t;
-    };
+    int t0 = 0, t1 = -1, u0 = 0, u1 = -1;  // runs [t0, t1] and [u0, u1]
     if (!per) {
         lo = max(lo, 0);
         hi = min(hi, n - 1);
-        if (lo <= hi) run(lo / T, hi / T);
+        if (lo <= hi) {
+            t0 = lo / T;
+            t1 = hi / T;
+        }
     } else if (hi - lo + 1 >= n) {
-        run(0, nt - 1);
+        t1 = nt - 1;
     } else {
         int lw = lo % n;
         if (lw < 0) lw += n;
         const int hw = lw + (hi - lo);
         if (hw < n) {
-            run(lw / T, hw / T);
+            t0 = lw / T;
+            t1 = hw / T;
         } else {
             const int a0 = lw / T, b1 = (hw - n) / T;  // [a0, nt - 1] and [0, b1]
             if (b1 >= a0) {
-                run(0, nt - 1);  // the two runs meet: every tile
+                t1 = nt - 1;  // the two runs meet: every tile
             } else {
-                run(a0, nt - 1);
-                run(0, b1);
+                t0 = a0;
+                t1 = nt - 1;
+                u1 = b1;
             }
         }
     }
-    return cnt;
+    R.s0 = t0;
+    R.n0 = min(16, max(0, t1 - t0 + 1));
+    R.s1 = u0;
+    R.n1 = min(16 - R.n0, max(0, u1 - u0 + 1));
+    return R;
+}
+
+__device__ __forceinline__ int axis_tiles(double r, float reach, int n, int per, int T, int* out) {
+    const AxisRuns R = axis_runs(r, reach, n, per, T);
+    for (int m = 0; m < R.count(); ++m) out[m] = R.tile(m);
+    return R.count();
 }
 
 // One warp per particle: the lanes append its id to the tiles' lists in parallel.
@@ -353,14 +372,13 @@ __global__ void k_bin(const LbmArgs a, int n, int* tile_count, int* tile_ids) {
         if (lane == 0) atomicAdd(&a.status->nan_detected, 1);
         return;
     }
-    int tl[3][16], tc[3];
-    tc[0] = axis_tiles(r[0], reach, a.nx, a.per[0], TILE_X, tl[0]);
-    tc[1] = axis_tiles(r[1], reach, a.ny, a.per[1], TILE_Y, tl[1]);
-    tc[2] = axis_tiles(r[2], reach, a.nz, a.per[2], a.tz, tl[2]);
-    const int n01 = tc[0] * tc[1], total = n01 * tc[2];
+    const AxisRuns X = axis_runs(r[0], reach, a.nx, a.per[0], TILE_X);
+    const AxisRuns Y = axis_runs(r[1], reach, a.ny, a.per[1], TILE_Y);
+    const AxisRuns Z = axis_runs(r[2], reach, a.nz, a.per[2], a.tz);
+    const int cx = X.count(), n01 = cx * Y.count(), total = n01 * Z.count();
     for (int m = lane; m < total; m += 32) {
-        const int c = m / n01, rem = m - c * n01, b = rem / tc[0], q = rem - b * tc[0];
-        const int t = (tl[2][c] * a.nty + tl[1][b]) * a.ntx + tl[0][q];
+        const int c = m / n01, rem = m - c * n01, b = rem / cx, q = rem - b * cx;
+        const int t = (Z.tile(c) * a.nty + Y.tile(b)) * a.ntx + X.tile(q);
         const int slot = atomicAdd(&tile_count[t], 1);
         if (slot < a.tile_cap) tile_ids[(long long)t * a.tile_cap + slot] = k;
         else atomicAdd(&a.status->tile_overflow, 1);
