@@ -101,10 +101,12 @@ typedef struct {
     int index64;             /* 1: 64-bit population offsets in the PSM kernel; 0: only when  */
                              /* 19 nx ny nz >= 2^31 (lattices of more than 1.1e8 nodes up to  */
                              /* 2^31 nodes use them automatically; batch members cannot)      */
-    int psm_route;           /* PSM kernel loads: 0 staged by the tensor copy engine (TMA) where */
+    int psm_route;           /* PSM kernel loads: 2 staged by the tensor copy engine (TMA) where */
                              /* the lattice suits it (rows a multiple of 16 bytes, nx >= 40   */
                              /* (FP32) / 48 (16-bit), ny >= 8), else direct; 1 always direct  */
-                             /* per-thread loads. Both give identical results.                 */
+                             /* per-thread loads; 0 (default) automatic: staged for FP32      */
+                             /* storage, direct for 16-bit storage (the faster of the two on  */
+                             /* GB300 for each). All give identical results.                  */
     int ell_screen;          /* 1 (default): before the common-normal iteration, two exact    */
                              /* tests of disjointness (separating plane across the centre line, */
                              /* Perram-Wertheim certificate) skip pairs that cannot touch; 0:   */

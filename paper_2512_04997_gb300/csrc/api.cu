@@ -145,7 +145,7 @@ static int check_args(const ledds_dims* d, const ledds_params* p) {
     if (p->orient < 0 || p->orient > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->pattern < 0 || p->pattern > 1) return LEDDS_ERR_INVALID_ARG;
     if (p->index64 < 0 || p->index64 > 1) return LEDDS_ERR_INVALID_ARG;
-    if (p->psm_route < 0 || p->psm_route > 1) return LEDDS_ERR_INVALID_ARG;
+    if (p->psm_route < 0 || p->psm_route > 2) return LEDDS_ERR_INVALID_ARG;
     if (p->ell_screen < 0 || p->ell_screen > 1) return LEDDS_ERR_INVALID_ARG;
     if (!lat) {
         for (int a = 0; a < 3; ++a)
@@ -248,7 +248,10 @@ static size_t layout(ledds_sim_s* s, const ledds_dims* d, const ledds_params* p,
         s->tile_cap = tcap;
         s->pop[0] = pop0;
         s->pop[1] = pop1;
-        s->staged = N > 0 && p->psm_route == 0 &&
+        // route 0 (automatic): staged for FP32, where it is faster; the 16-bit kernels are
+        // bound by instruction issue and the per-thread loads are faster for them
+        const bool want_staged = p->psm_route == 2 || (p->psm_route == 0 && p->storage == LEDDS_STORE_F32);
+        s->staged = N > 0 && want_staged &&
                     psm_make_maps(pop0, p->storage, d->nx, d->ny, d->nz, &s->maps[0]) &&
                     psm_make_maps(pop1, p->storage, d->nx, d->ny, d->nz, &s->maps[1]);
         s->tile_count = tcount;

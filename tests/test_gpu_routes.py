@@ -77,7 +77,7 @@ def test_staged_route_matches_direct_bitwise(oracle, periodic, walls, pattern, s
     """Lattice only: bit-identical populations after 1, 3 and 7 steps (both AA forms)."""
     w = _suspension(periodic, walls, storage, pattern, n=0)
     f0 = random_populations(oracle, W.rng(77), w.nx, w.ny, w.nz)
-    st = gpu_from_workload(w, populations=f0)
+    st = gpu_from_workload(w, populations=f0, psm_route=2)
     dr = gpu_from_workload(w, populations=f0, psm_route=1)
     assert st.status()["psm_staged"] == 1
     assert dr.status()["psm_staged"] == 0
@@ -101,7 +101,7 @@ def test_staged_route_matches_direct_with_particles(oracle, periodic, walls, pat
     in either order) to a few units."""
     w = _suspension(periodic, walls, storage, pattern)
     f0 = random_populations(oracle, W.rng(77), w.nx, w.ny, w.nz)
-    st = gpu_from_workload(w, populations=f0)
+    st = gpu_from_workload(w, populations=f0, psm_route=2)
     dr = gpu_from_workload(w, populations=f0, psm_route=1)
     st.step(1)
     dr.step(1)
@@ -145,7 +145,7 @@ def test_wide_offsets_staged_matches_direct(oracle):
     """64-bit population offsets (forced) on the staged route equal the direct route."""
     w = _suspension((1, 1, 0), "z", "f32", "ab", size=(64, 16, 20), n=0)
     f0 = random_populations(oracle, W.rng(79), w.nx, w.ny, w.nz)
-    st = gpu_from_workload(w, populations=f0, index64=1)
+    st = gpu_from_workload(w, populations=f0, index64=1, psm_route=2)
     dr = gpu_from_workload(w, populations=f0, index64=1, psm_route=1)
     st.step(3)
     dr.step(3)
@@ -154,8 +154,12 @@ def test_wide_offsets_staged_matches_direct(oracle):
 
 def test_unsuited_lattice_takes_direct_route(oracle):
     """Rows that are not a multiple of 16 bytes (nx = 50 in 16-bit storage) or narrower
-    than a wide box take the direct route."""
+    than a wide box take the direct route even where staging is asked for; the automatic
+    choice stages FP32 storage and pulls 16-bit storage per thread."""
     for size, storage in [((50, 16, 16), "f16"), ((36, 16, 16), "f32")]:
         w = _suspension((1, 1, 1), None, storage, "ab", size=size, n=0)
-        s = gpu_from_workload(w)
+        s = gpu_from_workload(w, psm_route=2)
         assert s.status()["psm_staged"] == 0
+    for storage, staged in [("f32", 1), ("f16", 0), ("bf16", 0)]:
+        w = _suspension((1, 1, 1), None, storage, "ab", size=(64, 16, 16), n=0)
+        assert gpu_from_workload(w).status()["psm_staged"] == staged
