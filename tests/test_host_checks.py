@@ -24,7 +24,8 @@ BAD_PARAMS = [
     dict(voxel=2), dict(subdiv_n=0), dict(subdiv_n=17), dict(law=2), dict(n_sub=0),
     dict(skin=-0.1), dict(dem_h=0.0), dict(dem_h=float("nan")), dict(collision=2),
     dict(collision=-1), dict(force_fp32=2), dict(orient=2), dict(orient=-1), dict(pattern=2),
-    dict(pattern=-1), dict(index64=2),
+    dict(pattern=-1), dict(index64=2), dict(psm_route=3), dict(psm_route=-1), dict(ell_screen=2),
+    dict(ell_screen=-1),
 ]
 
 
