@@ -318,3 +318,52 @@ def test_row_of_nodes_on_one_grid():
         assert all(got[L] == full[L] for L in need), (t, [(L, got[L], full[L]) for L in need])
         rows += 1
     assert rows > 20
+
+
+def test_row_shadow_prefilter_keeps_every_touching_row():
+    """The row prefilter for ellipsoids: a row of nodes (fixed y, z offsets from the centre)
+    is dropped when the smallest squared normalised radius over x, the Schur complement
+    quadratic f11 dy^2 + 2 f12 dy dz + f22 dz^2 of M^T M, is at least (1 + (h sqrt(2) +
+    1e-3)/s_min + 1e-3)^2 x 1.001. Rows near that bound, for the (6, 2, 2) shape and random
+    shapes: a dropped row has no sample inside at any node along x (every sample of the
+    nodes within reach checked with the predicate), and most rows near the shadow's rim are
+    dropped where the bounding circle would keep them."""
+    g = np.random.default_rng(15)
+    n = 10
+    so = [float(v) for v in _so(n)]
+    h = (n - 1) / (2 * n)
+    dropped = kept_circle = 0
+    for t in range(60):
+        semi = np.array([6.0, 2.0, 2.0]) if t % 2 else g.uniform(0.8, 6.0, 3)
+        mm = _ellipsoid_rows(g, semi)
+        M = np.array([[float(mm[3 * a + c]) for c in range(3)] for a in range(3)])
+        Q = M.T @ M
+        f11 = Q[1, 1] - Q[0, 1] ** 2 / Q[0, 0]
+        f12 = Q[1, 2] - Q[0, 1] * Q[0, 2] / Q[0, 0]
+        f22 = Q[2, 2] - Q[0, 2] ** 2 / Q[0, 0]
+        grow = 1.0 + (h * np.sqrt(2.0) + 1e-3) / semi.min() + 1e-3
+        bound = grow * grow * 1.001
+        reach = semi.max() + 0.8661 + 1e-3
+        for _ in range(40):
+            ang = g.uniform(0, 2 * np.pi)
+            # a row offset near the grown shadow's rim in a random direction
+            e = np.array([np.cos(ang), np.sin(ang)])
+            F1 = f11 * e[0] ** 2 + 2 * f12 * e[0] * e[1] + f22 * e[1] ** 2
+            rho = np.sqrt(bound / F1) * g.uniform(0.9, 1.3)
+            dy, dz = rho * e
+            F = f11 * dy * dy + 2 * f12 * dy * dz + f22 * dz * dz
+            if F < bound:
+                continue
+            dropped += 1
+            kept_circle += dy * dy + dz * dz < reach * reach
+            # every node along x within reach: no sample inside (the predicate on arrays,
+            # same FP32 operations in the same order)
+            px = (np.arange(-int(reach) - 1, int(reach) + 2) + g.uniform(-0.5, 0.5)).astype(np.float32)
+            sx = (px[:, None] + np.asarray(so, np.float32)[None, :]).reshape(-1, 1, 1)
+            sy = (f32(dy) + np.asarray(so, np.float32)).reshape(1, -1, 1)
+            sz = (f32(dz) + np.asarray(so, np.float32)).reshape(1, 1, -1)
+            m32 = [f32(v) for v in mm]
+            q = [(m32[3 * a] * sx + m32[3 * a + 1] * sy) + m32[3 * a + 2] * sz for a in range(3)]
+            r2 = (q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]
+            assert r2.dtype == np.float32 and not (r2 < f32(1)).any(), (t, dy, dz)
+    assert dropped > 500 and kept_circle > 0.5 * dropped, (dropped, kept_circle)
